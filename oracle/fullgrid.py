@@ -1,0 +1,66 @@
+"""Brute-force full-grid solution of the stabilized semi-implicit step -- oracle pin.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Eq. AC-discrete-semi-stable-K solved directly on the tensor-product C-FEM space, with no
+separation of variables: the D-dimensional mass and stiffness are assembled as Kronecker
+products of the 1D matrices (``N~(x, y) = N~_x(x) N~_y(y)``), ``K = c_t M + c_k K_grad`` and
+``Q = c_t M u^k - L M w(u^k)`` (nonlinear term under the nodal rule, so its integral is
+``M`` times the nodal values of ``w``), then one dense solve.  Used only on tiny grids to
+check ``oracle.ctd``, whose greedy separated solution must approach this one as the mode
+budget and tolerances tighten (Section 3.2: CTD converges to the CFE solution).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .ctd import Operators, Problem, w_of_u
+
+
+def kron_all(mats):
+    out = mats[0]
+    for m in mats[1:]:
+        out = sp.kron(out, m, format="csr")
+    return out
+
+
+def operators_full(prob: Problem, ops: Operators):
+    """Full-grid mass ``M = (x)_d M_d`` and gradient operator
+    ``K_grad = sum_d M_0 (x) .. K_d .. (x) M_{D-1}`` (row-major node ordering)."""
+    D = prob.dim
+    Mfull = kron_all([ops.M[d] for d in range(D)])
+    Kfull = None
+    for d in range(D):
+        mats = [ops.K[e] if e == d else ops.M[e] for e in range(D)]
+        term = kron_all(mats)
+        Kfull = term if Kfull is None else Kfull + term
+    return Mfull, Kfull
+
+
+def step(prob: Problem, ops: Operators, u_k: np.ndarray) -> np.ndarray:
+    """``u^{k+1}`` on the full grid from nodal values ``u_k`` (D-way array)."""
+    Mfull, Kfull = operators_full(prob, ops)
+    uk = u_k.reshape(-1)
+    Ksys = (prob.c_t * Mfull + prob.c_k * Kfull).toarray()
+    Q = prob.c_t * (Mfull @ uk) - prob.L * (Mfull @ w_of_u(uk, prob.a0))
+    return np.linalg.solve(Ksys, Q).reshape(u_k.shape)
+
+
+def energy(prob: Problem, ops: Operators, u: np.ndarray) -> float:
+    """Same discrete energy as ``ctd.energy`` but from full-grid values."""
+    Mfull, Kfull = operators_full(prob, ops)
+    uv = u.reshape(-1)
+    bulk = float(Mfull.diagonal() @ (prob.a0 * (uv ** 2 - 1.0) ** 2))
+    return bulk + 0.5 * prob.kappa * float(uv @ (Kfull @ uv))
+
+
+def galerkin_functional(prob: Problem, ops: Operators, u_k: np.ndarray, u: np.ndarray) -> float:
+    """``J(u) = 1/2 u^T K u - u^T Q`` of the step from ``u_k``; each ALS half-sweep is an
+    exact minimisation of ``J`` over one factor, so ``J`` cannot increase."""
+    Mfull, Kfull = operators_full(prob, ops)
+    uk = u_k.reshape(-1)
+    uv = u.reshape(-1)
+    Q = prob.c_t * (Mfull @ uk) - prob.L * (Mfull @ w_of_u(uk, prob.a0))
+    Kv = prob.c_t * (Mfull @ uv) + prob.c_k * (Kfull @ uv)
+    return 0.5 * float(uv @ Kv) - float(uv @ Q)

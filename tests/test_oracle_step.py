@@ -1,0 +1,212 @@
+"""Pins for the oracle's CTD step (Section 3.3, Eq. KxQx, App. D) and energy (Eq.
+energylaw, App. A) against a brute-force full-grid solve, closed forms and invariants."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import cfem, ctd, fullgrid, splitmix
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def make_problem(dim=2, n=10, s=1, p=1, eps=0.05, S=2.0, dt=0.01, **kw):
+    args = dict(dim=dim, n=(n,) * dim, length=(1.0,) * dim, s=s, p=p, a=12.0, L=1.0,
+                kappa=eps ** 2, a0=0.25, alpha=S, dt=dt, M_max=20, I_max=50, tol_als=1e-8,
+                tol_enrich=1e-4, seed=0)
+    args.update(kw)
+    return ctd.Problem(**args)
+
+
+def test_splitmix_published_vectors():
+    # Reference outputs of the SplitMix64 generator for seeds 0 and 1234567.
+    r = workloads.SplitMix64Stream(1234567)
+    assert [r.next_u64() for _ in range(3)] == [6457827717110365317, 3203168211198807973,
+                                                9817491932198370423]
+    assert workloads.SplitMix64Stream(0).next_u64() == 0xE220A8397B1DCDAF
+    # the oracle's counter form uses the same finaliser
+    assert splitmix.mix64(0) == 0xE220A8397B1DCDAF
+    v = splitmix.mode_init_vector(7, 3, 2, 1, 50)
+    assert np.all((v >= 0.5) & (v < 1.5))
+
+
+def test_rel_change_equals_brute_force_tensor_norm():
+    rng = np.random.default_rng(0)
+    for D in (2, 3):
+        new = [rng.standard_normal(5 + d) for d in range(D)]
+        old = [x + 1e-3 * rng.standard_normal(x.shape) for x in new]
+
+        def full(f):
+            T = f[0]
+            for y in f[1:]:
+                T = np.multiply.outer(T, y)
+            return T
+        ref = np.linalg.norm(full(new) - full(old)) / np.linalg.norm(full(new))
+        assert ctd.rel_change(new, old) == pytest.approx(ref, rel=1e-10)
+
+
+@pytest.mark.parametrize("dim,n,s,p,tol,bound", [(2, 8, 1, 1, 1e-12, 1e-10), (2, 7, 2, 2, 1e-12, 1e-10),
+                                                  (3, 4, 1, 1, 1e-10, 1e-6)])
+def test_ctd_converges_to_full_grid_solution(dim, n, s, p, tol, bound):
+    prob = make_problem(dim=dim, n=n, s=s, p=p, M_max=n ** (dim - 1) * 4, I_max=3000,
+                        tol_als=tol, tol_enrich=1e-15)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 3, 4, 11, amp=0.8)
+    B, st = ctd.step(prob, ops, A, 0)
+    U1 = fullgrid.step(prob, ops, ctd.reconstruct(A))
+    err = np.linalg.norm(ctd.reconstruct(B) - U1) / np.linalg.norm(U1)
+    assert err < bound
+
+
+def test_more_modes_approach_full_grid_monotonically():
+    # Section 4.1 / Fig. ctd_m: the CTD solution approaches CFE as modes are added.
+    prob = make_problem(n=12, I_max=400, tol_als=1e-12, tol_enrich=0.0)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 4, 4, 3, amp=0.8)
+    U1 = fullgrid.step(prob, ops, ctd.reconstruct(A))
+    errs = []
+    for M in (1, 2, 4, 8):
+        prob.fixed_modes = M
+        prob.fixed_als_iters = 0
+        prob.M_max = M
+        B, _ = ctd.step(prob, ops, A, 0)
+        errs.append(np.linalg.norm(ctd.reconstruct(B) - U1) / np.linalg.norm(U1))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+
+
+def test_linear_separable_eigenpair_is_reproduced_exactly():
+    # a0 = 0 removes w; an initial condition phi_x (x) phi_y made of generalised
+    # eigenvectors (K phi = lambda M phi) decays by c_t / (c_t + c_k (lx + ly)) in one mode.
+    prob = make_problem(n=14, s=2, p=2, a0=0.0, kappa=0.01, tol_als=1e-12)
+    ops = ctd.build_operators(prob)
+    import scipy.linalg as sla
+    lam, vecs = [], []
+    for d, idx in ((0, 2), (1, 3)):
+        ev, V = sla.eigh(ops.K[d].toarray(), np.diag(ops.omega[d]))
+        lam.append(ev[idx])
+        vecs.append(V[:, idx])
+    A = [vecs[0][:, None], vecs[1][:, None]]
+    B, st = ctd.step(prob, ops, A, 0)
+    factor = prob.c_t / (prob.c_t + prob.c_k * (lam[0] + lam[1]))
+    assert st["modes"] == 1
+    ref = factor * np.outer(vecs[0], vecs[1])
+    assert np.max(np.abs(ctd.reconstruct(B) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("c", [0.3, -0.7, 1.0])
+def test_constant_state_follows_scalar_recursion(c):
+    # K 1 = 0 and partition of unity: a constant stays constant with
+    # u^{k+1} = u^k - L w(u^k) / c_t  (Eq. AC-discrete-semi-stable-K on constants).
+    prob = make_problem(dim=2, n=11, s=2, p=2)
+    ops = ctd.build_operators(prob)
+    A = [np.full((11, 1), abs(c) ** 0.5), np.full((11, 1), math.copysign(abs(c) ** 0.5, c))]
+    u = c
+    for k in range(5):
+        A, st = ctd.step(prob, ops, A, k)
+        u = u - prob.L * 4 * prob.a0 * (u ** 3 - u) / prob.c_t
+        assert st["modes"] == 1
+        assert np.max(np.abs(ctd.reconstruct(A) - u)) < 1e-12
+
+
+def test_stationary_tanh_profile_stays_put():
+    # u = tanh((x - 1/2) / (sqrt(2) eps)) solves eps^2 u'' = u^3 - u; one mode, small drift.
+    eps, n = 0.05, 81
+    prob = make_problem(n=n, s=2, p=2, eps=eps, dt=0.01)
+    ops = ctd.build_operators(prob)
+    A = workloads.tanh_mode(prob.n, prob.length, eps)
+    U0 = ctd.reconstruct(A)
+    for k in range(30):
+        A, st = ctd.step(prob, ops, A, k)
+        assert st["modes"] == 1
+    h = 1.0 / (n - 1)
+    assert np.max(np.abs(ctd.reconstruct(A) - U0)) < 2.0 * (h / eps) ** 2
+
+
+def test_energy_routes_agree_and_constant_energy():
+    prob = make_problem(n=9, s=2, p=2)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 2, 3, 5, amp=0.9)
+    assert ctd.energy(prob, ops, A) == pytest.approx(
+        fullgrid.energy(prob, ops, ctd.reconstruct(A)), rel=1e-13)
+    A = [np.full((9, 1), 0.5), np.full((9, 1), 0.5)]
+    assert ctd.energy(prob, ops, A) == pytest.approx(prob.a0 * (0.25 ** 2 - 1) ** 2, rel=1e-13)
+
+
+def test_paper_stabiliser_satisfies_bound():
+    # Section 2.5 / App. A: alpha >= max(w')/2 with w' = 4 a0 (3u^2 - 1), u in [-1, 1].
+    g = json.load(open(GOLDEN))["stabiliser_case_2d"]
+    u = np.linspace(-1, 1, 2001)
+    wprime = 4 * g["a0"] * (3 * u ** 2 - 1)
+    assert g["alpha"] >= wprime.max() / 2
+    assert wprime.max() / 2 == pytest.approx(40.0)
+
+
+def test_full_grid_energy_law_holds_for_any_dt():
+    # Theorem of App. A on the full-grid scheme with the nodal rule: E non-increasing for
+    # S >= max(w')/2 = 1 (eps form), even for a large dt.
+    for dt in (0.01, 1.0):
+        prob = make_problem(n=10, s=1, p=1, S=1.0, dt=dt, eps=0.08)
+        ops = ctd.build_operators(prob)
+        U = ctd.reconstruct(workloads.cosine_modes(prob.n, prob.length, 3, 4, 2, amp=0.9))
+        E = fullgrid.energy(prob, ops, U)
+        for k in range(15):
+            U = fullgrid.step(prob, ops, U)
+            E1 = fullgrid.energy(prob, ops, U)
+            assert E1 <= E + 1e-14 * abs(E)
+            E = E1
+
+
+def test_ctd_energy_non_increasing_on_small_run():
+    prob = make_problem(n=32, s=1, p=1, eps=0.05, dt=0.01)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 4, 4, 0)
+    E = ctd.energy(prob, ops, A)
+    for k in range(10):
+        A, st = ctd.step(prob, ops, A, k)
+        E1 = ctd.energy(prob, ops, A)
+        assert E1 <= E + 1e-10 * abs(E)
+        E = E1
+
+
+def test_half_sweeps_never_increase_the_galerkin_functional():
+    # Each half-sweep minimises J(u) = 1/2 u^T K u - u^T Q exactly over one factor.
+    prob = make_problem(n=10, s=1, p=1, M_max=3)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 3, 4, 9, amp=0.8)
+    Uk = ctd.reconstruct(A)
+    tr = []
+    B, st = ctd.step(prob, ops, A, 0, trace=tr)
+    # rebuild u after each half-sweep: committed modes so far + current trial mode
+    committed = [np.zeros((10, 0)), np.zeros((10, 0))]
+    last_J = None
+    count = 0
+    for (m, it, x, v) in tr:
+        if m > count:   # modes < m are committed (same values as B's columns)
+            committed = [B[d][:, :m] for d in range(2)]
+            count = m
+            last_J = None
+        u = ctd.reconstruct(committed) + np.outer(v[0], v[1])
+        if x == 0:      # after the x-solve v is a full iterate
+            J = fullgrid.galerkin_functional(prob, ops, Uk, u)
+            if last_J is not None:
+                assert J <= last_J + 1e-13 * abs(last_J)
+            last_J = J
+
+
+def test_zero_initial_condition_gives_zero_solution():
+    prob = make_problem(n=8)
+    ops = ctd.build_operators(prob)
+    A = [np.zeros((8, 2)), np.zeros((8, 2))]
+    B, st = ctd.step(prob, ops, A, 0)
+    assert st["modes"] == 0 and not st["capped"]
+
+
+def test_mode_cap_sets_capped_flag():
+    prob = make_problem(n=12, M_max=1, tol_enrich=0.0)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 3, 4, 1)
+    B, st = ctd.step(prob, ops, A, 0)
+    assert st["modes"] == 1 and st["capped"]
