@@ -1,0 +1,156 @@
+/*
+ * ctd.h -- C ABI of the GB300 CTD (convolution tensor decomposition) Allen-Cahn solver.
+ *
+ * The library advances the stabilized semi-implicit Allen-Cahn step (Eq.
+ * AC-discrete-semi-stable-K of Lu, Yuan & Guo, arXiv 2410.15519) for a field kept in
+ * separated form u = sum_m prod_d u_d^(m) (Eq. CTD).  Each step builds the new field by
+ * greedy enrichment; every new mode is computed by the alternating fixed point of Section
+ * 3.3 (Eq. ux with K_x, Q_x of Eq. KxQx / Eq. KyQy, derivation in App. D), whose 1D systems
+ * use the C-FEM stiffness of Eq. KxxMxx built from the App. B / App. C shape functions.
+ * The full-grid nonlinear term M_xy (Eq. KxxMxx) is contracted on the GPU.
+ *
+ * Conventions for every entry point:
+ *  - Every call returns a ctd_status; nothing aborts or exits.  Values > 0 are warnings
+ *    (the result is valid), values < 0 are errors (outputs untouched unless stated).
+ *  - Device memory: the library allocates none.  The caller queries the workspace size
+ *    with ctd_workspace_size, allocates it on the current device and passes it to
+ *    ctd_create; the workspace must outlive the handle.  Host memory for the handle itself
+ *    is allocated with malloc.
+ *  - Caller buffers are never retained after a call returns.
+ *  - Work is queued on the CUDA stream given to ctd_create.  Calls that return data to the
+ *    host (ctd_energy, ctd_get_modes, ctd_step with stats) synchronise that stream.
+ *  - A handle is not thread safe.  Results are deterministic: the same inputs give
+ *    bitwise-identical outputs (fixed reduction orders, no floating-point atomics).
+ *  - Floating-point arguments are IEEE binary64 unless stated.
+ */
+#ifndef CTD_H
+#define CTD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CTD_OK = 0,
+  CTD_STATUS_CAPPED = 1,            /* a step reached M_max modes (Section 3.3 adaptivity cap) */
+  CTD_STATUS_ALS_NOT_CONVERGED = 2, /* some mode used I_max sweeps without meeting tol_als   */
+  CTD_ERR_ARG = -1,                 /* invalid argument or configuration                     */
+  CTD_ERR_WORKSPACE = -2,           /* workspace missing, too small or misaligned            */
+  CTD_ERR_CUDA = -3,                /* a CUDA runtime call failed                            */
+  CTD_ERR_NONFINITE = -4,           /* NaN or Inf met in the modes or a solve                */
+  CTD_ERR_TIMEOUT = -5,             /* a grid-wide wait exceeded its time limit              */
+  CTD_ERR_STATE = -6,               /* call out of order (e.g. step before initial modes)    */
+  CTD_ERR_UNSUPPORTED = -7          /* valid request this build does not implement           */
+} ctd_status;
+
+/* Arithmetic of the full-grid nonlinear contraction (all other parts are FP64-accurate). */
+enum {
+  CTD_PREC_FP64 = 0,      /* w(u^k) materialised once per step in FP64, FP64 contraction  */
+  CTD_PREC_SPLIT_BF16 = 1 /* u^k rebuilt per tile on tcgen05 tensor cores from hi/lo BF16
+                             modes (3 products, FP32 accumulation), cubic fused, FP32 sums */
+};
+
+typedef struct {
+  int dim;                  /* 2 or 3                                                       */
+  int n[3];                 /* nodes per dimension, 4 <= n[d] <= 4096                       */
+  double length[3];         /* domain [0, length[d]]                                        */
+  int s;                    /* C-FEM patch size, 1..3 (Section 3.2)                         */
+  int p;                    /* RBF polynomial order, 1..s (App. B)                          */
+  double a;                 /* dilation, natural-coordinate units (App. B)                  */
+  double L, kappa, a0, alpha; /* mobility, gradient coefficient, energy coefficient and
+                               stabiliser of Eq. AC, Eq. energyfunction, Eq.
+                               AC-discrete-semi-stable                                     */
+  double dt;                /* time increment                                                */
+  int M_max;                /* mode cap per step, 1..128                                    */
+  int I_max;                /* fixed-point sweeps per mode, >= 1                            */
+  double tol_als;           /* relative Frobenius change of a mode that ends its sweeps     */
+  double tol_enrich;        /* a mode with max|prod_d v_d| <= tol_enrich ends the step      */
+  int precision;            /* CTD_PREC_*                                                   */
+  int fixed_als_iters;      /* > 0: exactly this many sweeps per mode (strict parity)       */
+  int fixed_modes;          /* > 0: exactly this many modes per step (strict parity)        */
+  unsigned long long seed;  /* SplitMix64 seed for modes without a warm start               */
+  double wait_limit_s;      /* limit of each grid-wide wait; <= 0 means 1 second            */
+  int grid_ctas;            /* persistent CTAs; <= 0 means one per SM                       */
+} ctd_config;
+
+typedef struct {
+  int modes;                /* M of u^{k+1}                                                  */
+  int als_sweeps;           /* fixed-point sweeps over all modes tried in the step          */
+  int als_sweeps_max;       /* largest per-mode sweep count                                 */
+  int capped;               /* 1 if the step ended at M_max                                 */
+  int not_converged;        /* 1 if some mode ended at I_max without meeting tol_als       */
+  int status;               /* ctd_status of the step                                       */
+} ctd_step_stats;
+
+typedef struct ctd_ctx* ctd_handle;
+
+/* Bytes of device workspace a handle for cfg needs (256-byte aligned base required).
+ * Returns CTD_ERR_ARG for an invalid cfg. */
+ctd_status ctd_workspace_size(const ctd_config* cfg, size_t* bytes);
+
+/* Create a handle.  Builds the 1D C-FEM stiffness and nodal weights on the host (App. B,
+ * App. C, Eq. KxxMxx), uploads them into the workspace (a device pointer owned by the
+ * caller, at least ctd_workspace_size bytes) and records cuda_stream (a cudaStream_t, NULL
+ * for the legacy default stream).  The current CUDA device must be the workspace's. */
+ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_bytes,
+                      void* cuda_stream, ctd_handle* out);
+
+/* Set u^k to the rank-`rank` separated field whose factor d is the column-major
+ * n[d] x rank array modes[d] (mode r at modes[d] + r*n[d]); nodal values, by the
+ * Kronecker delta property of the C-FEM shape functions (Section 3.2).  modes[2] is
+ * ignored for dim 2.  on_device != 0: the arrays are device pointers.  0 <= rank <= M_max.
+ * Copies; resets the step counter to first_step. */
+ctd_status ctd_set_initial_modes(ctd_handle h, int rank, const double* const* modes,
+                                 int on_device, long long first_step);
+
+/* Advance nsteps time steps (Section 3.3 solution algorithm per step).  Asynchronous on the
+ * handle's stream when stats == NULL; otherwise synchronises and writes nsteps records.
+ * Returns the most severe status over the steps when stats != NULL. */
+ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats);
+
+/* Discrete energy of the current field, E_h = sum_grid omega F(u) + 1/2 kappa u^T K_grad u
+ * (energy functional of Section 2.1 with F of Eq. energyfunction; F integrated with the
+ * nodal rule, gradient with the exact stiffness).  FP64.  Synchronises. */
+ctd_status ctd_energy(ctd_handle h, double* energy);
+
+/* Copy the current field's factors out: *rank receives M; if M <= capacity, factor d is
+ * written column-major into modes_out[d] (n[d] x capacity leading dimension n[d]).
+ * Returns CTD_ERR_ARG with *rank set if capacity < M.  Synchronises. */
+ctd_status ctd_get_modes(ctd_handle h, int capacity, int* rank, double* const* modes_out,
+                         int on_device);
+
+/* Release the handle (not the caller's workspace).  Waits for queued work. */
+void ctd_destroy(ctd_handle h);
+
+/* Message of the last failing call on h (static text for h == NULL). */
+const char* ctd_last_error(ctd_handle h);
+const char* ctd_status_string(int status);
+
+/* ---------------------------------------------------------------------------------------
+ * Probes: single stages of the step exposed for parity tests and profiling.  Same
+ * conventions as above; they run on the handle's stream and synchronise.
+ * ------------------------------------------------------------------------------------- */
+
+/* Host-side C-FEM data of dimension d (no GPU work): nodal weights (n[d] values) and the
+ * stiffness band (n[d] x (2b+1) row-major, entry (i, j-i+b) = K[i][j], b = 2s+1).
+ * Either output may be NULL.  *half_bandwidth receives b. */
+ctd_status ctd_probe_cfem(const ctd_config* cfg, int d, double* omega, double* kband,
+                          int* half_bandwidth);
+
+/* Nonlinear contraction of Eq. KxxMxx for direction x with the current field as u^k:
+ * out[i] = sum over the other indices of w(u^k) * prod_{d != x} (omega_d v_d), i.e.
+ * M_xy u_y / (L omega_x[i]) under the nodal rule.  v[d] are host arrays of n[d] values
+ * (v[x] ignored).  Uses cfg.precision. */
+ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, double* out);
+
+/* Solve (alpha1 diag(omega_x) + alpha2 K_x) y = q with the step's banded solver (FP32
+ * block cyclic reduction + FP64-accurate iterative refinement); host arrays of n[x]. */
+ctd_status ctd_probe_solve(ctd_handle h, int x, double alpha1, double alpha2,
+                           const double* q, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTD_H */

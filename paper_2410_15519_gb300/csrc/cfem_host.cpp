@@ -1,0 +1,163 @@
+// Host-side 1D C-FEM builder: the stiffness band and nodal weights of one dimension.
+//
+// Shape functions (Section 3.2 Eq. CFEM, App. C Eq. CFEM-1D): on element e = [x_e, x_e+1]
+// with natural coordinate xi in [-1, 1], N~_k(xi) = sum_{i in {e, e+1}} N_i(xi) W_{i,k}(xi),
+// N_e = (1 - xi)/2, N_e+1 = (1 + xi)/2, and W_i the radial basis patch interpolant of node i
+// (App. B): W(xi) = Psi_a(xi) K + p(xi) L, L = (P^T R0^-1 P)^-1 P^T R0^-1,
+// K = R0^-1 (I - P L), R0_jl = Psi_a(|xi_j - xi_l| / a), P_jq = xi_j^q.
+// Node j of the mesh sits at xi_j = -1 + 2 (j - e) in the element's coordinate; node i's
+// patch is {max(0, i-s) .. min(n-1, i+s)} (truncated at the ends of the domain).
+//
+// Stiffness K_dd = int B~^T B~ dx (Eq. KxxMxx) per element with 5-point Gauss-Legendre,
+// dx = (h/2) dxi, d/dx = (2/h) d/dxi.  Exact when every break point of the kernel lies on
+// an element end (true for a = 12 with s <= 3).  Nodal weights: trapezoid rule.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cfem_host.h"
+
+namespace ctd {
+namespace {
+
+double kernel(double z) {
+  z = std::fabs(z);
+  if (z <= 0.5) return 2.0 / 3.0 - 4.0 * z * z + 4.0 * z * z * z;
+  if (z <= 1.0) return 4.0 / 3.0 - 4.0 * z + 4.0 * z * z - (4.0 / 3.0) * z * z * z;
+  return 0.0;
+}
+
+double kernel_dz(double z) {
+  z = std::fabs(z);
+  if (z <= 0.5) return -8.0 * z + 12.0 * z * z;
+  if (z <= 1.0) return -4.0 + 8.0 * z - 4.0 * z * z;
+  return 0.0;
+}
+
+// In-place inverse of a small dense matrix (Gauss-Jordan, partial pivoting).
+bool invert(std::vector<double>& A, int n) {
+  std::vector<double> I(n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[c * n + k], A[piv * n + k]);
+        std::swap(I[c * n + k], I[piv * n + k]);
+      }
+    const double d = 1.0 / A[c * n + c];
+    for (int k = 0; k < n; ++k) { A[c * n + k] *= d; I[c * n + k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) { A[r * n + k] -= f * A[c * n + k]; I[r * n + k] -= f * I[c * n + k]; }
+    }
+  }
+  A = I;
+  return true;
+}
+
+std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B,
+                           int m, int k, int n) {
+  std::vector<double> C(m * n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int l = 0; l < k; ++l) {
+      const double a = A[i * k + l];
+      for (int j = 0; j < n; ++j) C[i * n + j] += a * B[l * n + j];
+    }
+  return C;
+}
+
+// Patch interpolant of App. B for patch nodes at natural coordinates xs (np nodes):
+// outputs Kc (np x np) and Lc ((p+1) x np), row-major.
+bool patch_coefficients(const std::vector<double>& xs, double a, int p,
+                        std::vector<double>& Kc, std::vector<double>& Lc) {
+  const int np = static_cast<int>(xs.size()), nq = p + 1;
+  std::vector<double> R(np * np), P(np * nq), Pt(nq * np);
+  for (int j = 0; j < np; ++j)
+    for (int l = 0; l < np; ++l) R[j * np + l] = kernel(std::fabs(xs[j] - xs[l]) / a);
+  for (int j = 0; j < np; ++j) {
+    double v = 1.0;
+    for (int q = 0; q < nq; ++q) { P[j * nq + q] = v; Pt[q * np + j] = v; v *= xs[j]; }
+  }
+  if (!invert(R, np)) return false;                          // R <- R0^-1
+  std::vector<double> PtR = matmul(Pt, R, nq, np, np);       // P^T R0^-1
+  std::vector<double> S = matmul(PtR, P, nq, np, nq);        // P^T R0^-1 P
+  if (!invert(S, nq)) return false;
+  Lc = matmul(S, PtR, nq, nq, np);                           // L
+  std::vector<double> PL = matmul(P, Lc, np, nq, np);
+  for (int j = 0; j < np; ++j)
+    for (int l = 0; l < np; ++l) PL[j * np + l] = (j == l ? 1.0 : 0.0) - PL[j * np + l];
+  Kc = matmul(R, PL, np, np, np);                            // R0^-1 (I - P L)
+  return true;
+}
+
+}  // namespace
+
+int build_cfem_1d(int n, double length, int s, int p, double a, double* omega, double* kband) {
+  if (n < 2 || s < 1 || p < 0 || p > s || !(a > 0.0) || !(length > 0.0)) return -1;
+  const int b = 2 * s + 1, w = 2 * b + 1;
+  const double h = length / (n - 1);
+  if (omega) {
+    for (int i = 0; i < n; ++i) omega[i] = h;
+    omega[0] = omega[n - 1] = 0.5 * h;
+  }
+  if (!kband) return 0;
+  std::memset(kband, 0, sizeof(double) * static_cast<size_t>(n) * w);
+  static const double gx[5] = {-0.9061798459386640, -0.5384693101056831, 0.0,
+                               0.5384693101056831, 0.9061798459386640};
+  static const double gw[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889,
+                               0.4786286704993665, 0.2369268850561891};
+  for (int e = 0; e < n - 1; ++e) {
+    const int s0 = std::max(0, e - s), s1 = std::min(n - 1, e + 1 + s);
+    const int ns = s1 - s0 + 1;
+    // dN~/dxi at the Gauss points for every supporting node: dN[g][k]
+    std::vector<double> dN(5 * ns, 0.0);
+    for (int end = 0; end < 2; ++end) {
+      const int i = e + end;
+      const int p0 = std::max(0, i - s), p1 = std::min(n - 1, i + s), np = p1 - p0 + 1;
+      std::vector<double> xs(np);
+      for (int j = 0; j < np; ++j) xs[j] = -1.0 + 2.0 * (p0 + j - e);
+      std::vector<double> Kc, Lc;
+      if (!patch_coefficients(xs, a, p, Kc, Lc)) return -2;
+      for (int g = 0; g < 5; ++g) {
+        const double xi = gx[g];
+        const double Ni = end == 0 ? 0.5 * (1.0 - xi) : 0.5 * (1.0 + xi);
+        const double dNi = end == 0 ? -0.5 : 0.5;
+        // W(xi) and dW/dxi over the patch nodes
+        std::vector<double> psi(np), dpsi(np);
+        for (int l = 0; l < np; ++l) {
+          const double d = xi - xs[l];
+          psi[l] = kernel(std::fabs(d) / a);
+          dpsi[l] = kernel_dz(std::fabs(d) / a) * (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / a;
+        }
+        for (int j = 0; j < np; ++j) {
+          double W = 0.0, dW = 0.0;
+          for (int l = 0; l < np; ++l) { W += psi[l] * Kc[l * np + j]; dW += dpsi[l] * Kc[l * np + j]; }
+          double pv = 1.0, dpv = 0.0;
+          for (int q = 0; q <= p; ++q) {
+            W += pv * Lc[q * np + j];
+            dW += dpv * Lc[q * np + j];
+            dpv = (q + 1) * pv;   // d/dxi xi^(q+1) = (q+1) xi^q
+            pv *= xi;
+          }
+          dN[g * ns + (p0 + j - s0)] += dNi * W + Ni * dW;
+        }
+      }
+    }
+    for (int k = 0; k < ns; ++k)
+      for (int l = 0; l < ns; ++l) {
+        double acc = 0.0;
+        for (int g = 0; g < 5; ++g) acc += gw[g] * dN[g * ns + k] * dN[g * ns + l];
+        const int row = s0 + k, col = s0 + l;
+        kband[static_cast<size_t>(row) * w + (col - row + b)] += (2.0 / h) * acc;
+      }
+  }
+  return 0;
+}
+
+}  // namespace ctd

@@ -1,0 +1,204 @@
+// Shared device-side definitions of the CTD step: parameter blocks, the bounded grid
+// barrier, double-float (two FP32 words) arithmetic and the SplitMix64 generator.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace ctd {
+
+constexpr int kThreads = 256;          // threads per CTA of the step kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxDim = 3;
+constexpr int kMaxN = 4096;            // nodes per dimension
+constexpr int kMaxModes = 128;         // M_max limit
+constexpr int kTileRows = 128;         // tensor-core tile rows (operand rows padded to this)
+
+// status bits written by the kernels (host maps them to ctd_status)
+constexpr int kErrTimeout = 1;
+constexpr int kErrNonfinite = 2;
+constexpr int kErrSolve = 4;
+
+struct Dim {
+  int n;                   // nodes
+  int b;                   // half bandwidth of K (2s+1)
+  int n_pad;               // rows padded to kTileRows (tensor-core operands)
+  const double* omega;     // [n] nodal weights (FP64)
+  const double* kband;     // [n][2b+1] stiffness band (FP64)
+  float2* bank[2];         // [Mcap][n] factor banks (double-float): u^k and u^{k+1} alternate
+  float2* KB;              // [Mcap][n] K * committed factors of the step being built
+  float2* v;               // [n] trial factor (double-float)
+  float2* vold;            // [n] trial factor at the start of the sweep
+  __nv_bfloat16* op;       // [n_pad][2*Kpad] tensor-core operand: hi | lo split of u^k
+};
+
+struct InstState {
+  int Mk;                  // number of modes of u^k
+  int bank;                // bank index holding u^k
+  long long step;          // index of the next step (SplitMix64 key)
+  int status;              // kErr* bits
+  int err_info;            // where a wait gave up (phase id)
+};
+
+struct StepStatsDev {
+  int modes;
+  int als_sweeps;
+  int als_sweeps_max;
+  int capped;
+  int not_converged;
+  int status;
+};
+
+struct StepParams {
+  int dim;
+  Dim d[kMaxDim];
+  int Mcap;                // columns per bank
+  int Kpad;                // padded mode count of the tensor-core operands (multiple of 64)
+  int precision;           // 0 FP64, 1 split BF16 tensor cores
+  double c_t, c_k, L, a0;
+  double tol_als, tol_enrich;
+  int I_max, M_max, fixed_als, fixed_modes;
+  unsigned long long seed;
+  unsigned long long wait_ns;
+  // workspace scratch
+  double* W;               // [N] w(u^k) on the grid (FP64 path)
+  float2* gram;            // [slots][grid] per-CTA partial sums (double-float), slot-major
+  double* rpart;           // [n_x][rchunks[x]] partial contractions
+  int rchunks[kMaxDim];
+  float2* Q;               // [kMaxN] right-hand side (double-float)
+  float* solver;           // CR factor storage for the solver CTA
+  unsigned* barrier;       // grid barrier counter (zeroed before each launch)
+  InstState* st;
+  StepStatsDev* stats;     // one record per launch
+};
+
+// ------------------------------------------------------------------ time & barrier
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier over all CTAs of a (co-resident) launch.  The counter only grows
+// within a launch: barrier number k completes when it reaches (k+1) * gridDim.x.  Thread 0
+// arrives with a release reduction and polls with acquire loads; the wait gives up after
+// wait_ns, sets kErrTimeout and returns false (the caller then leaves the kernel).
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned& epoch,
+                                             unsigned long long wait_ns, InstState* st,
+                                             int where) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    epoch += 1;
+    const unsigned target = epoch * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+    unsigned v;
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+      if (static_cast<int>(v - target) >= 0) break;
+      if (global_ns() - t0 > wait_ns) {
+        ok = 0;
+        atomicOr(&st->status, kErrTimeout);
+        atomicExch(&st->err_info, where);
+        break;
+      }
+    }
+    // a CTA that timed out makes every later barrier fail fast for the others too
+    if (ok && (*reinterpret_cast<volatile int*>(&st->status) & kErrTimeout)) ok = 0;
+    s_ok = ok;
+  } else {
+    epoch += 1;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------ double-float
+// A value is hi + lo with |lo| <= ulp(hi)/2 (about 48 significant bits).  Error-free
+// transformations after Knuth (TwoSum) and Dekker (TwoProduct with a fused multiply-add).
+struct dfloat { float hi, lo; };
+
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  dfloat s = df_two_sum(a.hi, b.hi);
+  dfloat t = df_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = df_fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = a.hi * b.hi;
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+// a + b * c
+__device__ __forceinline__ dfloat df_fma(dfloat a, dfloat b, dfloat c) {
+  return df_add(a, df_mul(b, c));
+}
+__device__ __forceinline__ dfloat df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  const float lo = __double2float_rn(x - static_cast<double>(hi));
+  return {hi, lo};
+}
+__device__ __forceinline__ double df_to_double(dfloat a) {
+  return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+__device__ __forceinline__ double f2_to_double(float2 a) {
+  return static_cast<double>(a.x) + static_cast<double>(a.y);
+}
+
+// ------------------------------------------------------------------ SplitMix64
+// Steele, Lea & Flood (OOPSLA 2014) output function applied to x + golden gamma.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// Start vector of a mode without a warm start: chained key (seed, step, 4*mode+dim, node),
+// 53 random bits to [0, 1), shifted to [0.5, 1.5).
+__device__ __forceinline__ double mode_init_value(unsigned long long seed, long long step,
+                                                  int mode, int dim, int node) {
+  unsigned long long h = splitmix64(seed);
+  h = splitmix64(h ^ static_cast<unsigned long long>(step));
+  h = splitmix64(h ^ static_cast<unsigned long long>(4 * mode + dim));
+  h = splitmix64(h ^ static_cast<unsigned long long>(node));
+  return 0.5 + static_cast<double>(h >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// contiguous slice [lo, hi) of n items owned by part `k` of `parts`
+__device__ __forceinline__ void slice_of(int n, int parts, int k, int& lo, int& hi) {
+  const long long a = static_cast<long long>(n) * k / parts;
+  const long long b = static_cast<long long>(n) * (k + 1) / parts;
+  lo = static_cast<int>(a);
+  hi = static_cast<int>(b);
+}
+
+}  // namespace ctd

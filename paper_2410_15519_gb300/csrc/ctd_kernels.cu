@@ -1,0 +1,510 @@
+// Kernels of the CTD step: the persistent per-step kernel (Section 3.3 solution algorithm,
+// all control on the device), the discrete energy, and probe kernels for single stages.
+#include <cstdio>
+
+#include "ctd_kernels.h"
+#include "ctd_step.cuh"
+
+namespace ctd {
+
+// ---------------------------------------------------------------------------------------
+// Shared-memory plan of the step kernel (one union over phases)
+struct SmemStep {
+  union {
+    float2 gram_rows[3 * kChunk];   // Phase A Gram row data
+    double wv[kMaxDim * kMaxN];     // Phase A FP64 weights (96 KB)
+    float2 xsol[kMaxN];             // Phase C solution (32 KB)
+  } u;
+  Coef coef;
+  float2 red2[2 * kMaxDim];
+  float redf[kWarps];
+  double dred[kWarps * 8];
+};
+
+__device__ inline bool sync_all(const StepParams& P, unsigned& epoch, int where) {
+  if (gridDim.x == 1) {
+    __syncthreads();
+    return true;
+  }
+  return grid_barrier(P.barrier, epoch, P.wait_ns, P.st, where);
+}
+
+// Convert u^k factors of this CTA's slices to FP64 copies (FP64-path materialisation).
+__device__ void convert_prev_modes(const StepParams& P, const Extra& X, int pb, int Mk) {
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    int lo, hi;
+    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    for (int m = 0; m < Mk; ++m)
+      for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        X.Af[d][static_cast<size_t>(m) * dd.n + i] = f2_to_double(dd.bank[pb][static_cast<size_t>(m) * dd.n + i]);
+  }
+}
+
+// Mode start vectors (own slices): warm start from u^k's mode m if present and not zero,
+// otherwise SplitMix64 entries in [0.5, 1.5).
+__device__ void init_mode(const StepParams& P, int m, int pb, int Mk, long long step) {
+  __shared__ int s_nz[kMaxDim];
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    int nz = 0;
+    if (m < Mk) {
+      const float2* col = dd.bank[pb] + static_cast<size_t>(m) * dd.n;
+      for (int i = threadIdx.x; i < dd.n; i += blockDim.x)
+        if (col[i].x != 0.f || col[i].y != 0.f) nz = 1;
+    }
+    nz = __syncthreads_or(nz);
+    if (threadIdx.x == 0) s_nz[d] = nz;
+  }
+  __syncthreads();
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    int lo, hi;
+    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      float2 v;
+      if (s_nz[d]) {
+        v = dd.bank[pb][static_cast<size_t>(m) * dd.n + i];
+      } else {
+        const dfloat r = df_from_double(mode_init_value(P.seed, step, m, d, i));
+        v = make_float2(r.hi, r.lo);
+      }
+      dd.v[i] = v;
+    }
+  }
+}
+
+// Convergence partials (own slices): per dimension c the six products of old, delta = new -
+// old and new, and max |new|; slot (c * 6 + k) of the gram buffer, maxpart[c * G + cta].
+__device__ void convergence_partials(const StepParams& P, const Extra& X, float2* sh) {
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = 0; c < P.dim; ++c) {
+    const Dim& dd = P.d[c];
+    int lo, hi;
+    slice_of(dd.n, G, cta, lo, hi);
+    dfloat a[6];
+    for (int k = 0; k < 6; ++k) a[k] = {0.f, 0.f};
+    double mx = 0.0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const dfloat nv = ld_df(dd.v + i);
+      const dfloat od = ld_df(dd.vold + i);
+      const dfloat dl = df_add(nv, df_neg(od));
+      a[0] = df_fma(a[0], od, od);
+      a[1] = df_fma(a[1], od, dl);
+      a[2] = df_fma(a[2], od, nv);
+      a[3] = df_fma(a[3], dl, dl);
+      a[4] = df_fma(a[4], dl, nv);
+      a[5] = df_fma(a[5], nv, nv);
+      mx = fmax(mx, fabs(df_to_double(nv)));
+    }
+    for (int k = 0; k < 6; ++k) {
+      const dfloat r = group_sum(a[k], 32);
+      if (lane == 0) st_df(sh + warp * 6 + k, r);
+    }
+    mx = warp_max(mx);
+    __shared__ double s_mx[kWarps];
+    if (lane == 0) s_mx[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      dfloat s = {0.f, 0.f};
+      for (int w = 0; w < kWarps; ++w) s = df_add(s, ld_df(sh + w * 6 + threadIdx.x));
+      st_df(P.gram + static_cast<size_t>(c * 6 + threadIdx.x) * G + cta, s);
+    }
+    if (threadIdx.x == 6) {
+      double m = 0.0;
+      for (int w = 0; w < kWarps; ++w) m = fmax(m, s_mx[w]);
+      X.maxpart[c * G + cta] = m;
+    }
+    __syncthreads();
+  }
+}
+
+// Save the current trial factors (own slices) at the start of a sweep.
+__device__ void save_old(const StepParams& P) {
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    int lo, hi;
+    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) dd.vold[i] = dd.v[i];
+  }
+}
+
+// Commit the converged mode (own slices): b = v * scale_d, K b.
+__device__ void commit_mode(const StepParams& P, const Extra& X, int M, int cb,
+                            const double* scale) {
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    int lo, hi;
+    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    const dfloat sc = df_of(scale[d]);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      st_df(dd.bank[cb] + static_cast<size_t>(M) * dd.n + i, df_mul(ld_df(dd.v + i), sc));
+      st_df(dd.KB + static_cast<size_t>(M) * dd.n + i, df_mul(kv_row(X.kc[d], dd.v, i), sc));
+    }
+  }
+}
+
+// The solver CTA: solve Eq. ux for direction x, normalise unless x is the last dimension,
+// publish v_x (double-float) and flags in ctrl: [0] zero factor, [1] failure.
+__device__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
+                                float* solver_base) {
+  const Dim& dd = P.d[x];
+  const CRBuffers cr = cr_bind(solver_base, dd.n, dd.b);
+  const dfloat a1 = ld_df(&sm.coef.alpha1), a2 = ld_df(&sm.coef.alpha2);
+  float2* xs = sm.u.xsol;
+  bool ok = banded_solve(cr, X.kc[x], a1, a2, P.Q, xs, sm.redf);
+  // zero test and squared norm (double-float, fixed reduction order)
+  int nz = 0;
+  dfloat ss = {0.f, 0.f};
+  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) {
+    const dfloat v = {xs[i].x, xs[i].y};
+    if (v.hi != 0.f || v.lo != 0.f) nz = 1;
+    ss = df_fma(ss, v, v);
+  }
+  nz = __syncthreads_or(nz);
+  ss = group_sum(ss, 32);
+  __shared__ float2 s_part[kWarps];
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = make_float2(ss.hi, ss.lo);
+  __syncthreads();
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    dfloat t = {0.f, 0.f};
+    for (int w = 0; w < kWarps; ++w) t = df_add(t, ld_df(s_part + w));
+    const double nrm = sqrt(df_to_double(t));
+    s_inv = (nz && x != P.dim - 1) ? 1.0 / nrm : 1.0;
+    if (!(nrm == nrm) || nrm > 1e300) ok = false;
+    X.ctrl[0] = nz ? 0 : 1;
+    X.ctrl[1] = ok ? 0 : 1;
+  }
+  __syncthreads();
+  const dfloat inv = df_of(s_inv);
+  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) {
+    dfloat v = {xs[i].x, xs[i].y};
+    if (x != P.dim - 1) v = df_mul(v, inv);
+    st_df(dd.v + i, v);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, const Extra X) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
+  unsigned epoch = 0;
+  const InstState st0 = *P.st;
+  if (st0.status != 0) return;
+  const int D = P.dim, pb = st0.bank, cb = 1 - pb, Mk = st0.Mk;
+  const int G = gridDim.x;
+
+  // ---- prologue: the nonlinear term's data for this step
+  if (P.precision == 0) {
+    convert_prev_modes(P, X, pb, Mk);
+    if (!sync_all(P, epoch, 1)) return;
+    materialise_w(P, X, Mk);
+  }
+
+  int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0;
+  bool stopped = false;
+  const int n_modes = P.fixed_modes > 0 ? P.fixed_modes : P.M_max;
+  const int n_it = P.fixed_als > 0 ? P.fixed_als : P.I_max;
+  for (int m = 0; m < n_modes; ++m) {
+    init_mode(P, m, pb, Mk, st0.step);
+    if (!sync_all(P, epoch, 2)) return;
+    bool zero_mode = false;
+    double delta = 1e300, amp = 0.0;
+    double norms2[kMaxDim] = {1.0, 1.0, 1.0};
+    int it;
+    for (it = 1; it <= n_it; ++it) {
+      save_old(P);
+      for (int x = 0; x < D; ++x) {
+        // Phase A: Gram partials of the fixed factors + nonlinear contraction partials
+        gram_partials(P, X, x, Mk, M, pb, cb, sm.u.gram_rows);
+        __syncthreads();
+        if (P.precision == 0) {
+          load_weights_fp64(P, X, x, sm.u.wv);
+          contract_fp64(P, x, sm.u.wv);
+        }
+        if (!sync_all(P, epoch, 3)) return;
+        // Phase B: coefficients (every CTA, same order) and right-hand-side rows
+        build_coefficients(P, x, Mk, M, &sm.coef, sm.red2);
+        rhs_rows(P, X, x, Mk, M, pb, cb, &sm.coef);
+        if (!sync_all(P, epoch, 4)) return;
+        // Phase C: banded solve on CTA 0
+        if (blockIdx.x == 0) solve_direction(P, X, x, sm, P.solver);
+        if (!sync_all(P, epoch, 5)) return;
+        const int zflag = *reinterpret_cast<volatile int*>(X.ctrl + 0);
+        const int fflag = *reinterpret_cast<volatile int*>(X.ctrl + 1);
+        if (fflag) {
+          if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.st->status, kErrNonfinite);
+          return;
+        }
+        if (zflag) { zero_mode = true; break; }
+      }
+      ++sweeps;
+      if (zero_mode) break;
+      // Phase D: relative change of the rank-1 mode, max entries, norms
+      convergence_partials(P, X, sm.u.gram_rows);
+      if (!sync_all(P, epoch, 6)) return;
+      {
+        __shared__ double s_dots[kMaxDim * 6];
+        __shared__ double s_max[kMaxDim];
+        if (threadIdx.x < D * 6) s_dots[threadIdx.x] = df_to_double(reduce_slot(P.gram + static_cast<size_t>(threadIdx.x) * G, G));
+        if (threadIdx.x < D) {
+          double mx = 0.0;
+          for (int g = 0; g < G; ++g) mx = fmax(mx, X.maxpart[threadIdx.x * G + g]);
+          s_max[threadIdx.x] = mx;
+        }
+        __syncthreads();
+        // ||(x)new - (x)old||^2 = sum_{d,e} prod_c <T_d(c), T_e(c)>, factor of T_d at c:
+        // old (c < d), delta (c == d), new (c > d); dot index table over {old, delta, new}
+        const int idx[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+        double num = 0.0, den = 1.0;
+        for (int d1 = 0; d1 < D; ++d1)
+          for (int e1 = 0; e1 < D; ++e1) {
+            double prod = 1.0;
+            for (int c = 0; c < D; ++c) {
+              const int fa = c < d1 ? 0 : (c == d1 ? 1 : 2);
+              const int fb = c < e1 ? 0 : (c == e1 ? 1 : 2);
+              prod *= s_dots[c * 6 + idx[fa][fb]];
+            }
+            num += prod;
+          }
+        amp = 1.0;
+        for (int c = 0; c < D; ++c) {
+          den *= s_dots[c * 6 + 5];
+          norms2[c] = s_dots[c * 6 + 5];
+          amp *= s_max[c];
+        }
+        delta = den > 0.0 ? sqrt(fmax(num, 0.0) / den) : 0.0;
+        __syncthreads();
+      }
+      if (P.fixed_als == 0 && delta <= P.tol_als) break;
+    }
+    if (it > n_it) it = n_it;
+    sweeps_max = max(sweeps_max, it);
+    if (!zero_mode && P.fixed_als == 0 && !(delta <= P.tol_als)) not_conv = 1;
+    if (zero_mode) amp = 0.0;
+    if (P.fixed_modes == 0 && amp <= P.tol_enrich) { stopped = true; break; }
+    if (zero_mode) { stopped = true; break; }   // fixed-mode runs cannot commit a zero mode
+    // commit with equal 2-norms in every factor
+    double scale[kMaxDim], target = 1.0;
+    for (int c = 0; c < D; ++c) target *= sqrt(norms2[c]);
+    target = pow(target, 1.0 / D);
+    for (int c = 0; c < D; ++c) scale[c] = target / sqrt(norms2[c]);
+    commit_mode(P, X, M, cb, scale);
+    ++M;
+    if (!sync_all(P, epoch, 7)) return;
+  }
+  // ---- epilogue
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    InstState s = st0;
+    s.Mk = M;
+    s.bank = cb;
+    s.step = st0.step + 1;
+    s.status = P.st->status;
+    *P.st = s;
+    StepStatsDev r;
+    r.modes = M;
+    r.als_sweeps = sweeps;
+    r.als_sweeps_max = sweeps_max;
+    r.capped = (P.fixed_modes == 0 && !stopped) ? 1 : 0;
+    r.not_converged = not_conv;
+    r.status = 0;
+    *P.stats = r;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Energy: bulk part sum_grid (prod omega) a0 (u^2 - 1)^2 with u rebuilt in FP64, per-CTA
+// partial sums (fixed order); gradient part from the factors' Gram matrices.
+__global__ void __launch_bounds__(kThreads) energy_bulk_kernel(const StepParams P, const Extra X, int Mk,
+                                                               double* part) {
+  const int D = P.dim;
+  const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
+  const long long N = static_cast<long long>(n0) * n1 * n2;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  double acc = 0.0;
+  for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < N; p += stride) {
+    double u = 0.0, w;
+    if (D == 2) {
+      const int i = static_cast<int>(p / n1), j = static_cast<int>(p - static_cast<long long>(i) * n1);
+      for (int m = 0; m < Mk; ++m)
+        u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i], X.Af[1][static_cast<size_t>(m) * n1 + j], u);
+      w = P.d[0].omega[i] * P.d[1].omega[j];
+    } else {
+      const int l = static_cast<int>(p % n2);
+      const long long ij = p / n2;
+      const int j = static_cast<int>(ij % n1), i = static_cast<int>(ij / n1);
+      for (int m = 0; m < Mk; ++m)
+        u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i] * X.Af[1][static_cast<size_t>(m) * n1 + j],
+                X.Af[2][static_cast<size_t>(m) * n2 + l], u);
+      w = P.d[0].omega[i] * P.d[1].omega[j] * P.d[2].omega[l];
+    }
+    const double t = u * u - 1.0;
+    acc = fma(w * P.a0, t * t, acc);
+  }
+  acc = warp_sum(acc);
+  __shared__ double s[kWarps];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += s[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// FP64 copies of the current factors (whole arrays)
+__global__ void convert_modes_kernel(const StepParams P, const Extra X, int bank, int Mk) {
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    const long long total = static_cast<long long>(Mk) * dd.n;
+    for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x)
+      X.Af[d][t] = f2_to_double(dd.bank[bank][t]);
+  }
+}
+
+// Gram matrices of the current factors: out[d][2][Mk][Mk] = (b^T M b', b^T K b') in FP64
+__global__ void energy_gram_kernel(const StepParams P, const Extra X, int Mk, double* out) {
+  const int d = blockIdx.y;
+  const Dim& dd = P.d[d];
+  const int pair = blockIdx.x;
+  const int m1 = pair / Mk, m2 = pair % Mk;
+  const double* a = X.Af[d] + static_cast<size_t>(m1) * dd.n;
+  const double* c = X.Af[d] + static_cast<size_t>(m2) * dd.n;
+  double sm = 0.0, sk = 0.0;
+  const int w = 2 * dd.b + 1;
+  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) {
+    sm = fma(a[i] * dd.omega[i], c[i], sm);
+    double kc = 0.0;
+    for (int j = max(0, i - dd.b); j <= min(dd.n - 1, i + dd.b); ++j)
+      kc = fma(dd.kband[static_cast<size_t>(i) * w + (j - i + dd.b)], c[j], kc);
+    sk = fma(a[i], kc, sk);
+  }
+  sm = warp_sum(sm);
+  sk = warp_sum(sk);
+  __shared__ double s[2][kWarps];
+  if ((threadIdx.x & 31) == 0) { s[0][threadIdx.x >> 5] = sm; s[1][threadIdx.x >> 5] = sk; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int k = 0; k < kWarps; ++k) { t0 += s[0][k]; t1 += s[1][k]; }
+    out[(static_cast<size_t>(d) * 2 + 0) * Mk * Mk + pair] = t0;
+    out[(static_cast<size_t>(d) * 2 + 1) * Mk * Mk + pair] = t1;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Probe kernels
+__global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const StepParams P, const Extra X, int x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
+  unsigned epoch = 0;
+  const InstState st0 = *P.st;
+  if (P.precision == 0) {
+    convert_prev_modes(P, X, st0.bank, st0.Mk);
+    if (!sync_all(P, epoch, 11)) return;
+    materialise_w(P, X, st0.Mk);
+    if (!sync_all(P, epoch, 12)) return;
+    load_weights_fp64(P, X, x, sm.u.wv);
+    contract_fp64(P, x, sm.u.wv);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) probe_solve_kernel(const StepParams P, const Extra X, int x,
+                                                                  double a1, double a2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
+  if (threadIdx.x == 0) {
+    st_df(&sm.coef.alpha1, df_of(a1));
+    st_df(&sm.coef.alpha2, df_of(a2));
+  }
+  __syncthreads();
+  const Dim& dd = P.d[x];
+  const CRBuffers cr = cr_bind(P.solver, dd.n, dd.b);
+  bool ok = banded_solve(cr, X.kc[x], ld_df(&sm.coef.alpha1), ld_df(&sm.coef.alpha2), P.Q, sm.u.xsol, sm.redf);
+  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) dd.v[i] = sm.u.xsol[i];
+  if (threadIdx.x == 0) X.ctrl[1] = ok ? 0 : 1;
+}
+
+size_t step_smem_bytes() { return sizeof(SmemStep); }
+
+}  // namespace ctd
+
+namespace ctd {
+
+__global__ void f64_to_df_kernel(float2* dst, const double* src, long long count) {
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < count;
+       t += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const dfloat v = df_from_double(src[t]);
+    dst[t] = make_float2(v.hi, v.lo);
+  }
+}
+__global__ void df_to_f64_kernel(double* dst, const float2* src, long long count) {
+  for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < count;
+       t += static_cast<long long>(gridDim.x) * blockDim.x)
+    dst[t] = f2_to_double(src[t]);
+}
+
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+
+cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s) {
+  const size_t smem = step_smem_bytes();
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&step_kernel), smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&step_kernel), dim3(grid), dim3(kThreads),
+                                     args, smem, s);
+}
+
+cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x, cudaStream_t s) {
+  const size_t smem = step_smem_bytes();
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&probe_contract_kernel), smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), &x};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&probe_contract_kernel), dim3(grid),
+                                     dim3(kThreads), args, smem, s);
+}
+
+cudaError_t launch_probe_solve(const StepParams& P, const Extra& X, int x, double a1, double a2,
+                               cudaStream_t s) {
+  const size_t smem = step_smem_bytes();
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&probe_solve_kernel), smem);
+  if (e != cudaSuccess) return e;
+  probe_solve_kernel<<<1, kThreads, smem, s>>>(P, X, x, a1, a2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_modes(const StepParams& P, const Extra& X, int bank, int Mk, cudaStream_t s) {
+  convert_modes_kernel<<<256, kThreads, 0, s>>>(P, X, bank, Mk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_bulk(const StepParams& P, const Extra& X, int Mk, double* part, int grid,
+                               cudaStream_t s) {
+  energy_bulk_kernel<<<grid, kThreads, 0, s>>>(P, X, Mk, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_gram(const StepParams& P, const Extra& X, int Mk, double* out, cudaStream_t s) {
+  if (Mk == 0) return cudaSuccess;
+  energy_gram_kernel<<<dim3(Mk * Mk, P.dim), kThreads, 0, s>>>(P, X, Mk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_modes_from_fp64(float2* dst, const double* src, long long count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  f64_to_df_kernel<<<256, kThreads, 0, s>>>(dst, src, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_modes_to_fp64(double* dst, const float2* src, long long count, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  df_to_f64_kernel<<<256, kThreads, 0, s>>>(dst, src, count);
+  return cudaGetLastError();
+}
+
+}  // namespace ctd

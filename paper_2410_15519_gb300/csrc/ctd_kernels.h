@@ -1,0 +1,17 @@
+// Host-callable launch wrappers of the CTD kernels.
+#pragma once
+#include "ctd_step.cuh"
+
+namespace ctd {
+size_t step_smem_bytes();
+cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s);
+cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x, cudaStream_t s);
+cudaError_t launch_probe_solve(const StepParams& P, const Extra& X, int x, double a1, double a2,
+                               cudaStream_t s);
+cudaError_t launch_convert_modes(const StepParams& P, const Extra& X, int bank, int Mk, cudaStream_t s);
+cudaError_t launch_energy_bulk(const StepParams& P, const Extra& X, int Mk, double* part, int grid,
+                               cudaStream_t s);
+cudaError_t launch_energy_gram(const StepParams& P, const Extra& X, int Mk, double* out, cudaStream_t s);
+cudaError_t launch_modes_from_fp64(float2* dst, const double* src, long long count, cudaStream_t s);
+cudaError_t launch_modes_to_fp64(double* dst, const float2* src, long long count, cudaStream_t s);
+}  // namespace ctd

@@ -1,0 +1,359 @@
+// Device-side pieces of one CTD time step (Section 3.3) shared by the step kernel and the
+// probe kernels: mode-bank access, Gram partial sums (the 1D products of Eq. KxQx),
+// right-hand-side rows, the FP64 nonlinear contraction, convergence partials.
+#pragma once
+#include "ctd_common.cuh"
+#include "ctd_solve.cuh"
+
+namespace ctd {
+
+// per other-dimension slot block of the Gram partials:
+// [0] m = v^T M v, [1] k = v^T K v, [2, 2+Mcap) gM_j = v^T M b_j, [2+Mcap, 2+2Mcap) gK_j =
+// v^T K b_j, [2+2Mcap, 2+3Mcap) h_j = v^T M a_j   (a_j: factors of u^k, b_j: of u^{k+1})
+__host__ __device__ inline int slots_per_dim(int Mcap) { return 2 + 3 * Mcap; }
+
+struct Extra {            // per-launch workspace pieces not in StepParams
+  KCompressed kc[kMaxDim];
+  double* Af[kMaxDim];    // FP64 copy of u^k factors [Mcap][n] (FP64-path materialisation)
+  double* maxpart;        // [kMaxDim][grid]
+  int* ctrl;              // [4] solver flags broadcast
+  float* rpart32;         // [n][chunks] FP32 partials (tensor-core path)
+};
+
+__device__ __forceinline__ dfloat ld_df(const float2* p) {
+  const float2 v = *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void st_df(float2* p, dfloat v) { *p = make_float2(v.hi, v.lo); }
+__device__ __forceinline__ dfloat df_of(double x) { return df_from_double(x); }
+
+// K v at row i of dimension d (double-float), K read from the compressed band
+__device__ inline dfloat kv_row(const KCompressed& k, const float2* v, int i) {
+  dfloat acc = {0.f, 0.f};
+  const int j0 = max(0, i - k.b), j1 = min(k.n - 1, i + k.b);
+  for (int j = j0; j <= j1; ++j) {
+    const float2 kij = kc_entry(k, i, j - i);
+    acc = df_fma(acc, dfloat{kij.x, kij.y}, ld_df(v + j));
+  }
+  return acc;
+}
+
+// Reduce a double-float value over the `tp` consecutive lanes of a group (tp power of 2 <=
+// 32), fixed xor tree.
+__device__ inline dfloat group_sum(dfloat v, int tp) {
+  for (int o = tp >> 1; o > 0; o >>= 1) {
+    dfloat u;
+    u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, u);
+  }
+  return v;
+}
+
+__device__ inline int pow2_floor(int x) {
+  int p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
+// ---------------------------------------------------------------------------------------
+// Phase A (part 1): Gram partial sums for every dimension d != x over this CTA's slice of
+// dimension d's nodes.  Writes gram[(o * spd + slot) * G + cta] for the used slots.
+// Shared scratch: 3 * kChunk float2.
+constexpr int kChunk = 256;
+
+__device__ inline void gram_partials(const StepParams& P, const Extra& X, int x, int Mk, int M,
+                              int pb, int cb, float2* sh) {
+  const int G = gridDim.x, cta = blockIdx.x, D = P.dim, spd = slots_per_dim(P.Mcap);
+  float2* sv = sh;               // v_i
+  float2* sdv = sh + kChunk;     // omega_i v_i
+  float2* skv = sh + 2 * kChunk; // (K v)_i
+  int o = 0;
+  for (int d = 0; d < D; ++d) {
+    if (d == x) continue;
+    const Dim& dd = P.d[d];
+    int lo, hi;
+    slice_of(dd.n, G, cta, lo, hi);
+    const int nslots = 2 + 2 * M + Mk;
+    // thread group per slot
+    const int tp = min(32, pow2_floor(max(1, kThreads / max(1, nslots))));
+    const int groups = kThreads / tp;
+    const int g = threadIdx.x / tp, lane = threadIdx.x % tp;
+    // accumulators for the (up to ceil(nslots/groups)) slots of this group
+    dfloat acc[8];
+    const int per = (nslots + groups - 1) / groups;   // <= 8 since nslots <= 2+5*128 ... guarded
+    for (int k = 0; k < 8; ++k) acc[k] = {0.f, 0.f};
+    for (int c0 = lo; c0 < hi; c0 += kChunk) {
+      const int c1 = min(hi, c0 + kChunk);
+      __syncthreads();
+      for (int i = c0 + threadIdx.x; i < c1; i += kThreads) {
+        const dfloat v = ld_df(dd.v + i);
+        const float2 om = kc_omega(X.kc[d], i);
+        st_df(sv + i - c0, v);
+        st_df(sdv + i - c0, df_mul(dfloat{om.x, om.y}, v));
+        st_df(skv + i - c0, kv_row(X.kc[d], dd.v, i));
+      }
+      __syncthreads();
+      for (int k = 0; k < per; ++k) {
+        const int s = g + k * groups;
+        if (s >= nslots) break;
+        dfloat a = acc[k];
+        if (s == 0) {
+          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sv + i - c0), ld_df(sdv + i - c0));
+        } else if (s == 1) {
+          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sv + i - c0), ld_df(skv + i - c0));
+        } else if (s < 2 + M) {
+          const float2* col = dd.bank[cb] + static_cast<size_t>(s - 2) * dd.n;
+          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sdv + i - c0), ld_df(col + i));
+        } else if (s < 2 + 2 * M) {
+          const float2* col = dd.KB + static_cast<size_t>(s - 2 - M) * dd.n;
+          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sv + i - c0), ld_df(col + i));
+        } else {
+          const float2* col = dd.bank[pb] + static_cast<size_t>(s - 2 - 2 * M) * dd.n;
+          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sdv + i - c0), ld_df(col + i));
+        }
+        acc[k] = a;
+      }
+    }
+    for (int k = 0; k < per; ++k) {
+      const int s = g + k * groups;
+      const dfloat r = group_sum(acc[k], tp);   // all lanes of the warp participate
+      if (s < nslots && lane == 0) {
+        int slot;
+        if (s < 2) slot = s;
+        else if (s < 2 + M) slot = s;                               // gM
+        else if (s < 2 + 2 * M) slot = 2 + P.Mcap + (s - 2 - M);    // gK
+        else slot = 2 + 2 * P.Mcap + (s - 2 - 2 * M);               // h
+        st_df(P.gram + static_cast<size_t>(o * spd + slot) * G + cta, r);
+      }
+    }
+    ++o;
+  }
+}
+
+// Sum the G partials of one slot in a fixed order (four interleaved accumulators).
+__device__ inline dfloat reduce_slot(const float2* part, int G) {
+  dfloat a0 = {0.f, 0.f}, a1 = a0, a2 = a0, a3 = a0;
+  int g = 0;
+  for (; g + 3 < G; g += 4) {
+    a0 = df_add(a0, ld_df(part + g));
+    a1 = df_add(a1, ld_df(part + g + 1));
+    a2 = df_add(a2, ld_df(part + g + 2));
+    a3 = df_add(a3, ld_df(part + g + 3));
+  }
+  for (; g < G; ++g) a0 = df_add(a0, ld_df(part + g));
+  return df_add(df_add(a0, a1), df_add(a2, a3));
+}
+
+// Coefficients of Eq. KxQx for direction x, in shared memory (double-float):
+// coef[0] = alpha1, coef[1] = alpha2, H[m] = prod_{d!=x} h_d,m, GM[m] = prod gM_d,m,
+// GK[m] = sum_{d'} gK_{d',m} prod_{d != x,d'} gM_d,m.
+struct Coef {
+  float2 alpha1, alpha2;
+  float2 H[kMaxModes], GM[kMaxModes], GK[kMaxModes];
+};
+
+__device__ inline void build_coefficients(const StepParams& P, int x, int Mk, int M, Coef* c,
+                                   float2* red /* >= 2*kMaxDim float2 */) {
+  const int G = gridDim.x, D = P.dim, spd = slots_per_dim(P.Mcap);
+  const int nO = D - 1;
+  // m_d, k_d of the fixed factors
+  if (threadIdx.x < 2 * nO) {
+    const int o = threadIdx.x >> 1, s = threadIdx.x & 1;
+    st_df(red + threadIdx.x, reduce_slot(P.gram + static_cast<size_t>(o * spd + s) * G, G));
+  }
+  for (int m = threadIdx.x; m < max(M, Mk); m += blockDim.x) {
+    dfloat gm[kMaxDim - 1], gk[kMaxDim - 1];
+    dfloat H = {1.f, 0.f};
+    for (int o = 0; o < nO; ++o) {
+      const float2* base = P.gram + static_cast<size_t>(o * spd) * G;
+      if (m < M) {
+        gm[o] = reduce_slot(base + static_cast<size_t>(2 + m) * G, G);
+        gk[o] = reduce_slot(base + static_cast<size_t>(2 + P.Mcap + m) * G, G);
+      }
+      if (m < Mk) H = df_mul(H, reduce_slot(base + static_cast<size_t>(2 + 2 * P.Mcap + m) * G, G));
+    }
+    if (m < Mk) st_df(c->H + m, H);
+    if (m < M) {
+      dfloat GM = {1.f, 0.f}, GK = {0.f, 0.f};
+      for (int o = 0; o < nO; ++o) GM = df_mul(GM, gm[o]);
+      for (int o2 = 0; o2 < nO; ++o2) {
+        dfloat t = gk[o2];
+        for (int o = 0; o < nO; ++o)
+          if (o != o2) t = df_mul(t, gm[o]);
+        GK = df_add(GK, t);
+      }
+      st_df(c->GM + m, GM);
+      st_df(c->GK + m, GK);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const dfloat ct = df_of(P.c_t), ck = df_of(P.c_k);
+    dfloat pm = {1.f, 0.f}, stiff = {0.f, 0.f};
+    for (int o = 0; o < nO; ++o) pm = df_mul(pm, ld_df(red + 2 * o));
+    for (int o2 = 0; o2 < nO; ++o2) {
+      dfloat t = ld_df(red + 2 * o2 + 1);
+      for (int o = 0; o < nO; ++o)
+        if (o != o2) t = df_mul(t, ld_df(red + 2 * o));
+      stiff = df_add(stiff, t);
+    }
+    st_df(&c->alpha1, df_add(df_mul(ct, pm), df_mul(ck, stiff)));
+    st_df(&c->alpha2, df_mul(ck, pm));
+  }
+  __syncthreads();
+}
+
+// Right-hand side rows of this CTA's slice of direction x (Eq. KxQx), written as
+// double-float into P.Q.  R_i (the nonlinear contraction, without L omega_i) comes from the
+// partial buffers.
+__device__ inline void rhs_rows(const StepParams& P, const Extra& X, int x, int Mk, int M, int pb,
+                         int cb, const Coef* c) {
+  const Dim& dd = P.d[x];
+  int lo, hi;
+  slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const dfloat ct = df_of(P.c_t), ck = df_of(P.c_k), L = df_of(P.L);
+  const int C = P.rchunks[x];
+  for (int i = lo + warp; i < hi; i += kWarps) {
+    dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
+    for (int m = lane; m < Mk; m += 32)
+      s1 = df_fma(s1, ld_df(dd.bank[pb] + static_cast<size_t>(m) * dd.n + i), ld_df(c->H + m));
+    for (int m = lane; m < M; m += 32) {
+      const dfloat bmi = ld_df(dd.bank[cb] + static_cast<size_t>(m) * dd.n + i);
+      const dfloat gm = ld_df(c->GM + m);
+      s1 = df_add(s1, df_neg(df_mul(bmi, gm)));
+      s2 = df_fma(s2, ld_df(dd.KB + static_cast<size_t>(m) * dd.n + i), gm);
+      s3 = df_fma(s3, bmi, ld_df(c->GK + m));
+    }
+    s1 = group_sum(s1, 32);
+    s2 = group_sum(s2, 32);
+    s3 = group_sum(s3, 32);
+    if (lane == 0) {
+      dfloat R;
+      if (P.precision == 0) {
+        double r = 0.0;
+        for (int k = 0; k < C; ++k) r += P.rpart[static_cast<size_t>(i) * C + k];
+        R = df_of(r);
+      } else {
+        R = {0.f, 0.f};
+        for (int k = 0; k < C; ++k) R = df_add(R, dfloat{X.rpart32[static_cast<size_t>(i) * C + k], 0.f});
+      }
+      const float2 om2 = kc_omega(X.kc[x], i);
+      const dfloat om = {om2.x, om2.y};
+      // Q = c_t om s1 - c_k s2 - c_k om s3 - L om R
+      dfloat q = df_mul(df_mul(ct, om), s1);
+      q = df_add(q, df_neg(df_mul(ck, s2)));
+      q = df_add(q, df_neg(df_mul(df_mul(ck, om), s3)));
+      q = df_add(q, df_neg(df_mul(df_mul(L, om), R)));
+      st_df(P.Q + i, q);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 nonlinear contraction of the materialised w(u^k) grid (Eq. KxxMxx, nodal rule):
+// rpart[c * C + k] = partial over chunk k of sum_{other indices} W * prod_{d != x} wv_d,
+// wv_d = omega_d v_d in FP64 (shared memory, wv + d * kMaxN).
+__device__ inline void contract_fp64(const StepParams& P, int x, const double* wv) {
+  const int D = P.dim;
+  const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
+  const int C = P.rchunks[x];
+  const int nc = P.d[x].n;
+  const int warp_g = blockIdx.x * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int total_warps = gridDim.x * kWarps;
+  const double* W = P.W;
+  if (x == D - 1) {
+    // column sums: R[c] = sum_r W[r * nc + c] wrow(r); units (32-column block, row chunk)
+    const int rows = static_cast<int>(static_cast<long long>(n0) * n1 * n2 / nc);
+    const int cblocks = (nc + 31) / 32;
+    const int units = cblocks * C;
+    for (int u = warp_g; u < units; u += total_warps) {
+      const int cb = u / C, k = u - cb * C;
+      const int c = cb * 32 + lane;
+      int r0, r1;
+      slice_of(rows, C, k, r0, r1);
+      double acc = 0.0;
+      for (int rb = r0; rb < r1; rb += 32) {
+        const int r = rb + lane;
+        double wr = 0.0;
+        if (r < r1) wr = (D == 2) ? wv[r] : wv[r / n1] * wv[kMaxN + (r % n1)];
+        const int cnt = min(32, r1 - rb);
+        for (int t = 0; t < cnt; ++t) {
+          const double w = __shfl_sync(0xffffffffu, wr, t);
+          if (c < nc) acc = fma(W[static_cast<size_t>(rb + t) * nc + c], w, acc);
+        }
+      }
+      if (c < nc) P.rpart[static_cast<size_t>(c) * C + k] = acc;
+    }
+  } else {
+    // row dots over the last axis
+    const int nl = (D == 2) ? n1 : n2;
+    const double* wl = wv + (D - 1) * kMaxN;   // weights of the last dimension
+    const int units = nc * C;
+    for (int u = warp_g; u < units; u += total_warps) {
+      const int c = u / C, k = u - c * C;
+      double acc = 0.0;
+      if (D == 2) {          // x = 0: one row per c, chunk over the last axis
+        int q0, q1;
+        slice_of(nl, C, k, q0, q1);
+        const double* row = W + static_cast<size_t>(c) * nl;
+        for (int q = q0 + lane; q < q1; q += 32) acc = fma(row[q], wl[q], acc);
+      } else {               // D == 3, x in {0, 1}: rows over the other leading dimension
+        const int no = (x == 0) ? n1 : n0;
+        const double* wo = wv + ((x == 0) ? 1 : 0) * kMaxN;
+        int i0, i1;
+        slice_of(no, C, k, i0, i1);
+        for (int i = i0; i < i1; ++i) {
+          const size_t base = (x == 0) ? (static_cast<size_t>(c) * n1 + i) * nl
+                                       : (static_cast<size_t>(i) * n1 + c) * nl;
+          double s = 0.0;
+          for (int q = lane; q < nl; q += 32) s = fma(W[base + q], wl[q], s);
+          acc = fma(wo[i], s, acc);
+        }
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) P.rpart[static_cast<size_t>(c) * C + k] = acc;
+    }
+  }
+}
+
+// FP64 weights omega_d v_d of every dimension but x (shared memory wv + d * kMaxN).
+__device__ inline void load_weights_fp64(const StepParams& P, const Extra& X, int x, double* wv) {
+  for (int d = 0; d < P.dim; ++d) {
+    if (d == x) continue;
+    const Dim& dd = P.d[d];
+    for (int i = threadIdx.x; i < dd.n; i += blockDim.x)
+      wv[d * kMaxN + i] = dd.omega[i] * f2_to_double(dd.v[i]);
+  }
+  __syncthreads();
+}
+
+// w(u) = dF/du = 4 a0 (u^3 - u) (Eq. energyfunction)
+__device__ __forceinline__ double w_of_u(double u, double a0) { return 4.0 * a0 * (u * u * u - u); }
+
+// Materialise W = w(u^k) on the grid from FP64 factor copies Af[d][m][i] (row-major grid).
+__device__ inline void materialise_w(const StepParams& P, const Extra& X, int Mk) {
+  const int D = P.dim;
+  const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
+  const long long N = static_cast<long long>(n0) * n1 * n2;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < N; p += stride) {
+    double u = 0.0;
+    if (D == 2) {
+      const int i = static_cast<int>(p / n1), j = static_cast<int>(p - static_cast<long long>(i) * n1);
+      for (int m = 0; m < Mk; ++m)
+        u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i], X.Af[1][static_cast<size_t>(m) * n1 + j], u);
+    } else {
+      const int l = static_cast<int>(p % n2);
+      const long long ij = p / n2;
+      const int j = static_cast<int>(ij % n1), i = static_cast<int>(ij / n1);
+      for (int m = 0; m < Mk; ++m)
+        u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i] * X.Af[1][static_cast<size_t>(m) * n1 + j],
+                X.Af[2][static_cast<size_t>(m) * n2 + l], u);
+    }
+    P.W[p] = w_of_u(u, P.a0);
+  }
+}
+
+}  // namespace ctd

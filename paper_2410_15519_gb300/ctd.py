@@ -1,0 +1,240 @@
+"""Python binding of the CTD C ABI (``include/ctd.h``): argument marshalling only.
+
+Every stage of a time step runs in the CUDA library ``libctd.so``; this module allocates the
+workspace with PyTorch, passes PyTorch's current CUDA stream, and converts arrays.  There is
+no CPU fallback: if the library is missing or cannot be loaded every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctd.so")
+
+PREC_FP64 = 0
+PREC_SPLIT_BF16 = 1
+
+STATUS = {0: "CTD_OK", 1: "CTD_STATUS_CAPPED", 2: "CTD_STATUS_ALS_NOT_CONVERGED", -1: "CTD_ERR_ARG",
+          -2: "CTD_ERR_WORKSPACE", -3: "CTD_ERR_CUDA", -4: "CTD_ERR_NONFINITE", -5: "CTD_ERR_TIMEOUT",
+          -6: "CTD_ERR_STATE", -7: "CTD_ERR_UNSUPPORTED"}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("length", ctypes.c_double * 3),
+                ("s", ctypes.c_int), ("p", ctypes.c_int), ("a", ctypes.c_double),
+                ("L", ctypes.c_double), ("kappa", ctypes.c_double), ("a0", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("dt", ctypes.c_double), ("M_max", ctypes.c_int),
+                ("I_max", ctypes.c_int), ("tol_als", ctypes.c_double), ("tol_enrich", ctypes.c_double),
+                ("precision", ctypes.c_int), ("fixed_als_iters", ctypes.c_int),
+                ("fixed_modes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("modes", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("als_sweeps_max", ctypes.c_int),
+                ("capped", ctypes.c_int), ("not_converged", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class CTDError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libctd.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2410_15519_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    pcfg = ctypes.POINTER(Config)
+    lib.ctd_workspace_size.argtypes = [pcfg, ctypes.POINTER(sz)]
+    lib.ctd_create.argtypes = [pcfg, vp, sz, vp, ctypes.POINTER(vp)]
+    lib.ctd_set_initial_modes.argtypes = [vp, i, ctypes.POINTER(vp), i, ctypes.c_longlong]
+    lib.ctd_step.argtypes = [vp, i, ctypes.POINTER(StepStats)]
+    lib.ctd_energy.argtypes = [vp, ctypes.POINTER(d)]
+    lib.ctd_get_modes.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(vp), i]
+    lib.ctd_destroy.argtypes = [vp]
+    lib.ctd_destroy.restype = None
+    lib.ctd_last_error.argtypes = [vp]
+    lib.ctd_last_error.restype = ctypes.c_char_p
+    lib.ctd_status_string.argtypes = [i]
+    lib.ctd_status_string.restype = ctypes.c_char_p
+    lib.ctd_probe_cfem.argtypes = [pcfg, i, vp, vp, ctypes.POINTER(i)]
+    lib.ctd_probe_contract.argtypes = [vp, i, ctypes.POINTER(vp), vp]
+    lib.ctd_probe_solve.argtypes = [vp, i, d, d, vp, vp]
+    for f in ("ctd_workspace_size", "ctd_create", "ctd_set_initial_modes", "ctd_step", "ctd_energy",
+              "ctd_get_modes", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
+                precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
+                grid_ctas=0) -> Config:
+    c = Config()
+    c.dim = dim
+    for k in range(3):
+        c.n[k] = int(n[k]) if k < dim else 0
+        c.length[k] = float(length[k]) if k < dim else 0.0
+    c.s, c.p, c.a = int(s), int(p), float(a)
+    c.L, c.kappa, c.a0, c.alpha, c.dt = float(L), float(kappa), float(a0), float(alpha), float(dt)
+    c.M_max, c.I_max = int(M_max), int(I_max)
+    c.tol_als, c.tol_enrich = float(tol_als), float(tol_enrich)
+    c.precision, c.fixed_als_iters, c.fixed_modes = int(precision), int(fixed_als_iters), int(fixed_modes)
+    c.seed, c.wait_limit_s, c.grid_ctas = int(seed), float(wait_limit_s), int(grid_ctas)
+    return c
+
+
+def config_from_workload(w, precision=PREC_FP64, **overrides) -> Config:
+    """Config of a ``workloads.Workload`` (paper symbols L, kappa, a0, alpha)."""
+    args = dict(dim=w.dim, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
+                alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+                tol_enrich=w.tol_enrich, precision=precision, seed=w.seed)
+    args.update(overrides)
+    return make_config(**args)
+
+
+def _check(lib, h, st, what):
+    if st < 0:
+        msg = lib.ctd_last_error(h).decode() if h else lib.ctd_status_string(st).decode()
+        raise CTDError(st, f"{what}: {msg}")
+    return st
+
+
+def workspace_size(cfg: Config) -> int:
+    lib = load()
+    n = ctypes.c_size_t(0)
+    _check(lib, None, lib.ctd_workspace_size(ctypes.byref(cfg), ctypes.byref(n)), "ctd_workspace_size")
+    return n.value
+
+
+def probe_cfem(cfg: Config, d: int):
+    """Host-side C-FEM data of dimension d: (omega, band [n x (2b+1)], b)."""
+    lib = load()
+    b = ctypes.c_int(0)
+    _check(lib, None, lib.ctd_probe_cfem(ctypes.byref(cfg), d, None, None, ctypes.byref(b)), "probe_cfem")
+    n = cfg.n[d]
+    om = np.zeros(n)
+    kb = np.zeros((n, 2 * b.value + 1))
+    _check(lib, None, lib.ctd_probe_cfem(ctypes.byref(cfg), d, om.ctypes.data, kb.ctypes.data, ctypes.byref(b)),
+           "probe_cfem")
+    return om, kb, b.value
+
+
+class Solver:
+    """One CTD Allen-Cahn instance on the current CUDA device."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.lib = load()
+        self.cfg = cfg
+        self.torch = torch
+        nbytes = workspace_size(cfg)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.ctd_create(ctypes.byref(cfg), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        _check(self.lib, None, st, "ctd_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ctd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_initial_modes(self, modes: Sequence, first_step: int = 0):
+        """modes[d]: n_d x rank array (numpy on the host, or a CUDA torch tensor)."""
+        torch = self.torch
+        rank = int(modes[0].shape[1])
+        on_dev = isinstance(modes[0], torch.Tensor) and modes[0].is_cuda
+        keep = []
+        ptrs = (ctypes.c_void_p * 3)()
+        for d in range(self.cfg.dim):
+            if on_dev:
+                t = modes[d].to(torch.float64).t().contiguous()      # column-major n x rank
+                keep.append(t)
+                ptrs[d] = t.data_ptr()
+            else:
+                a = np.asfortranarray(np.asarray(modes[d], dtype=np.float64))
+                keep.append(a)
+                ptrs[d] = a.ctypes.data
+        st = self.lib.ctd_set_initial_modes(self.h, rank, ptrs, 1 if on_dev else 0, int(first_step))
+        if on_dev:
+            self.stream.synchronize()
+        _check(self.lib, self.h, st, "ctd_set_initial_modes")
+
+    def step(self, nsteps: int = 1, stats: bool = True):
+        if not stats:
+            _check(self.lib, self.h, self.lib.ctd_step(self.h, nsteps, None), "ctd_step")
+            return None
+        rec = (StepStats * nsteps)()
+        st = self.lib.ctd_step(self.h, nsteps, rec)
+        _check(self.lib, self.h, st, "ctd_step")
+        return [dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
+                     capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status) for r in rec]
+
+    def energy(self) -> float:
+        e = ctypes.c_double(0.0)
+        _check(self.lib, self.h, self.lib.ctd_energy(self.h, ctypes.byref(e)), "ctd_energy")
+        return e.value
+
+    def get_modes(self, device: bool = False) -> List:
+        torch = self.torch
+        r = ctypes.c_int(0)
+        st = self.lib.ctd_get_modes(self.h, 0, ctypes.byref(r), None, 0)
+        if st < 0 and r.value == 0:
+            _check(self.lib, self.h, st, "ctd_get_modes")
+        rank = r.value
+        ptrs = (ctypes.c_void_p * 3)()
+        outs = []
+        for d in range(self.cfg.dim):
+            if device:
+                t = torch.empty((rank, self.cfg.n[d]), dtype=torch.float64, device="cuda")
+                ptrs[d] = t.data_ptr()
+            else:
+                t = np.zeros((self.cfg.n[d], rank), order="F")
+                ptrs[d] = t.ctypes.data
+            outs.append(t)
+        if rank:
+            _check(self.lib, self.h, self.lib.ctd_get_modes(self.h, rank, ctypes.byref(r), ptrs, 1 if device else 0),
+                   "ctd_get_modes")
+        if device:
+            return [t.t() for t in outs]
+        return [np.ascontiguousarray(t) for t in outs]
+
+    def probe_contract(self, x: int, v: Sequence[np.ndarray]) -> np.ndarray:
+        ptrs = (ctypes.c_void_p * 3)()
+        keep = []
+        for d in range(self.cfg.dim):
+            a = np.ascontiguousarray(np.asarray(v[d], dtype=np.float64))
+            keep.append(a)
+            ptrs[d] = a.ctypes.data
+        out = np.zeros(self.cfg.n[x])
+        _check(self.lib, self.h, self.lib.ctd_probe_contract(self.h, x, ptrs, out.ctypes.data), "probe_contract")
+        return out
+
+    def probe_solve(self, x: int, alpha1: float, alpha2: float, q: np.ndarray) -> np.ndarray:
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        y = np.zeros(self.cfg.n[x])
+        _check(self.lib, self.h, self.lib.ctd_probe_solve(self.h, x, float(alpha1), float(alpha2), q.ctypes.data,
+                                                          y.ctypes.data), "probe_solve")
+        return y
