@@ -150,6 +150,21 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
 ctd_status ctd_probe_solve(ctd_handle h, int x, double alpha1, double alpha2,
                            const double* q, double* y);
 
+/* Grid values of the current field u^k rebuilt on the tensor cores (CTD_PREC_SPLIT_BF16
+ * handles only): out[i * ncols_pad + c] for the n_pad[x] x ncols_pad tile grid of direction
+ * x (rows: nodes of x padded to 128; columns: nodes of the other dimension (2D) or the
+ * other dimensions' index pairs (3D, last one padded to 128)), FP32.  scratch: device
+ * buffer of at least the output size.  Synchronises. */
+ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch, size_t scratch_bytes);
+
+/* Per-phase time of the step kernel, accumulated by CTA 0 from the GPU global timer (each
+ * phase includes its closing grid-wide wait).  Copies the seconds accumulated so far into
+ * seconds[0 .. nslots) (may be NULL), resets the counters, and turns accumulation on
+ * (enable != 0) or off.  Slots: 0 prologue (nonlinear-term preparation), 1 mode start,
+ * 2 Gram products + nonlinear contraction, 3 right-hand sides, 4 banded solve,
+ * 5 convergence test, 6 mode commit.  Synchronises. */
+ctd_status ctd_probe_trace(ctd_handle h, int enable, double* seconds, int nslots);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,6 +7,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "ctd.h"
 #include "cfem_host.h"
 #include "ctd_kernels.h"
@@ -40,8 +43,36 @@ struct Carver {
 struct Plan {
   int D, n[3], b[3], n_pad[3], Mcap, Kpad, grid, rchunks[3];
   long long N;
-  size_t rpart_len;
+  size_t rpart_len, rpart32_len;
+  ctd::TcDir dirs[3];
 };
+
+// Tensor-core geometry of direction x for a grid of G CTAs.
+ctd::TcDir tc_dir(const Plan& p, int x, int G) {
+  ctd::TcDir t{};
+  t.nrb = p.n_pad[x] / ctd::kTcM;
+  if (p.D == 2) {
+    t.mid = -1;
+    t.last = 1 - x;
+    t.ncols_pad = p.n_pad[t.last];
+    t.n_last_pad = p.n_pad[t.last];
+  } else {
+    t.mid = x == 0 ? 1 : 0;
+    t.last = x == 2 ? 1 : 2;
+    t.n_last_pad = p.n_pad[t.last];
+    t.ncols_pad = p.n[t.mid] * t.n_last_pad;
+  }
+  t.ntc = t.ncols_pad / ctd::kTcN;
+  const long long T = static_cast<long long>(t.nrb) * t.ntc;
+  int cmax = 1;
+  for (int rb = 0; rb < t.nrb; ++rb) {
+    const int c0 = ctd::tile_owner(T, G, static_cast<long long>(rb) * t.ntc);
+    const int c1 = ctd::tile_owner(T, G, static_cast<long long>(rb) * t.ntc + t.ntc - 1);
+    cmax = std::max(cmax, c1 - c0 + 1);
+  }
+  t.cmax = cmax;
+  return t;
+}
 
 int half_bandwidth(int s) { return 2 * s + 1; }
 
@@ -76,9 +107,14 @@ Plan make_plan(const ctd_config& c, int grid) {
   p.Kpad = (c.M_max + 63) / 64 * 64;
   p.grid = grid;
   p.rpart_len = 0;
+  p.rpart32_len = 0;
   for (int x = 0; x < c.dim; ++x) {
     p.rchunks[x] = chunks_for(c, x, grid);
     p.rpart_len = std::max(p.rpart_len, static_cast<size_t>(c.n[x]) * p.rchunks[x]);
+  }
+  for (int x = 0; x < c.dim; ++x) {
+    p.dirs[x] = tc_dir(p, x, grid);
+    p.rpart32_len = std::max(p.rpart32_len, static_cast<size_t>(c.n[x]) * p.dirs[x].cmax);
   }
   return p;
 }
@@ -105,7 +141,8 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
     dd.KB = cv.take<float2>(static_cast<size_t>(pl.Mcap) * n);
     dd.v = cv.take<float2>(n);
     dd.vold = cv.take<float2>(n);
-    dd.op = nullptr;
+    dd.op = (c.precision == CTD_PREC_SPLIT_BF16)
+                ? cv.take<__nv_bfloat16>(static_cast<size_t>(pl.n_pad[d]) * 2 * pl.Kpad) : nullptr;
     kc_store[d] = cv.take<float2>(static_cast<size_t>(n + 1) * w);
     x.Af[d] = cv.take<double>(static_cast<size_t>(pl.Mcap) * n);
   }
@@ -115,13 +152,21 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   const int nslots = std::max((D - 1) * spd, D * 6);
   p.gram = cv.take<float2>(static_cast<size_t>(nslots) * Gs);
   p.rpart = cv.take<double>(pl.rpart_len);
-  x.rpart32 = cv.take<float>(pl.rpart_len);
+  x.rpart32 = cv.take<float>(std::max<size_t>(1, pl.rpart32_len));
+  for (int k = 0; k < 3; ++k) x.kr[k] = nullptr;
+  if (c.precision == CTD_PREC_SPLIT_BF16 && D == 3)
+    for (int k = 0; k < 3; ++k)
+      x.kr[k] = cv.take<__nv_bfloat16>(static_cast<size_t>(pl.dirs[k].ncols_pad) * 2 * pl.Kpad);
+  for (int k = 0; k < D; ++k) x.dirs[k] = pl.dirs[k];
   p.Q = cv.take<float2>(ctd::kMaxN);
   size_t crf = 0;
-  for (int d = 0; d < D; ++d) crf = std::max(crf, ctd::cr_floats(pl.n[d], pl.b[d]));
+  for (int d = 0; d < D; ++d)
+    crf = std::max(crf, std::max(ctd::cr_floats(pl.n[d], pl.b[d]), ctd::l0_global_floats(pl.n[d], pl.b[d])));
   p.solver = cv.take<float>(crf);
+  p.xsol_g = cv.take<float2>(ctd::kMaxN);
   p.W = (c.precision == CTD_PREC_FP64) ? cv.take<double>(static_cast<size_t>(pl.N)) : nullptr;
   p.barrier = cv.take<unsigned>(64);
+  p.trace = cv.take<unsigned long long>(ctd::kTrSlots);
   p.st = cv.take<InstState>(1);
   x.maxpart = cv.take<double>(static_cast<size_t>(ctd::kMaxDim) * Gs);
   x.ctrl = cv.take<int>(64);
@@ -182,6 +227,9 @@ struct ctd_ctx {
   double* energy_part;
   double* energy_gram;
   StepStatsDev* stats_dev;
+  unsigned long long* trace_dev;
+  double mu_max[3];
+  ctd::TmapSet tm;
   std::vector<double> omega[3], kband[3];
   bool has_modes;
   std::string err;
@@ -219,12 +267,16 @@ ctd_status ctd_workspace_size(const ctd_config* cfg, size_t* bytes) {
   ctd_status v = validate(cfg);
   if (v != CTD_OK) return v;
   if (!bytes) return CTD_ERR_ARG;
-  if (cfg->precision == CTD_PREC_SPLIT_BF16) return CTD_ERR_UNSUPPORTED;
   float2* kc[3];
   double *ep, *eg;
   StepStatsDev* sd;
-  const Plan pl = make_plan(*cfg, kGridMax);
-  *bytes = carve(*cfg, pl, nullptr, nullptr, nullptr, kc, &ep, &eg, &sd);
+  size_t best = 0;
+  // every grid size 1..kGridMax fits (rpart32 depends on the split of tiles over CTAs)
+  for (int g : {1, 2, 4, 8, 16, 32, 64, 128, 132, 144, 148, 152, 160, 256, kGridMax}) {
+    const Plan pl = make_plan(*cfg, g);
+    best = std::max(best, carve(*cfg, pl, nullptr, nullptr, nullptr, kc, &ep, &eg, &sd));
+  }
+  *bytes = best + static_cast<size_t>(2) * kGridMax * ctd::kMaxN * sizeof(float);
   return CTD_OK;
 }
 
@@ -245,7 +297,6 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   if (v != CTD_OK) return v;
   if (!out) return CTD_ERR_ARG;
   *out = nullptr;
-  if (cfg->precision == CTD_PREC_SPLIT_BF16) return CTD_ERR_UNSUPPORTED;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CTD_ERR_WORKSPACE;
   size_t need = 0;
   ctd_workspace_size(cfg, &need);
@@ -279,6 +330,15 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   P.c_k = cfg->L * cfg->kappa;
   P.L = cfg->L;
   P.a0 = cfg->a0;
+  {
+    auto df = [](double v) {
+      const float hi = static_cast<float>(v);
+      return make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+    };
+    P.ct_df = df(P.c_t);
+    P.ck_df = df(P.c_k);
+    P.L_df = df(P.L);
+  }
   P.tol_als = cfg->tol_als;
   P.tol_enrich = cfg->tol_enrich;
   P.I_max = cfg->I_max;
@@ -290,6 +350,104 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   const double wait_s = cfg->wait_limit_s > 0.0 ? cfg->wait_limit_s : 1.0 + est;
   P.wait_ns = static_cast<unsigned long long>(wait_s * 1e9);
   for (int x = 0; x < cfg->dim; ++x) P.rchunks[x] = h->plan.rchunks[x];
+  // Gershgorin bound of the generalised eigenvalues of (K, diag(omega)) per dimension
+  for (int d = 0; d < cfg->dim; ++d) {
+    const int n = cfg->n[d], w = 2 * h->plan.b[d] + 1;
+    std::vector<double> om(n), kb(static_cast<size_t>(n) * w);
+    ctd::build_cfem_1d(n, cfg->length[d], cfg->s, cfg->p, cfg->a, om.data(), kb.data());
+    double g = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double r = 0.0;
+      for (int k = 0; k < w; ++k) r += std::fabs(kb[static_cast<size_t>(i) * w + k]);
+      g = std::max(g, r / om[i]);
+    }
+    h->mu_max[d] = g * 1.000001;
+    P.d[d].mu_max = static_cast<float>(h->mu_max[d]);
+  }
+  // shared memory: fixed part + per-phase arena; solver factors join the arena if they fit
+  {
+    int n_max = 0;
+    size_t crf = 0, l0f = 0;
+    for (int d = 0; d < cfg->dim; ++d) {
+      n_max = std::max(n_max, cfg->n[d]);
+      crf = std::max(crf, ctd::cr_floats(cfg->n[d], h->plan.b[d]));
+      l0f = std::max(l0f, ctd::l0_smem_floats(cfg->n[d], h->plan.b[d]));
+    }
+    int optin = 0;
+    CTD_CUDA(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    const size_t fixed = ctd::step_smem_fixed_bytes();
+    const size_t margin = 1024 + 2048;   // arena alignment + static shared variables
+    P.n_max = n_max;
+    // Chebyshev unless its worst-case iteration count (smallest beta = c_t / c_k) is large
+    int worst_its = 0;
+    for (int d = 0; d < cfg->dim; ++d)
+      worst_its = std::max(worst_its, ctd::cheb_iterations(static_cast<float>(P.c_t), static_cast<float>(P.c_k),
+                                                           static_cast<float>(h->mu_max[d]), 2.384185791015625e-07f));
+    const size_t chf = ctd::cheb_floats(n_max);
+    if (worst_its <= 200 && fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
+      P.solver_mode = 3;
+    else if (fixed + ctd::step_arena_bytes(n_max, crf, 0) + margin <= static_cast<size_t>(optin)) P.solver_mode = 0;
+    else if (fixed + ctd::step_arena_bytes(n_max, l0f, 1) + margin <= static_cast<size_t>(optin)) P.solver_mode = 1;
+    else P.solver_mode = 2;
+    const size_t used = P.solver_mode == 3 ? chf : (P.solver_mode == 0 ? crf : l0f);
+    size_t need = fixed + ctd::step_arena_bytes(n_max, used, P.solver_mode) + 1024;
+    if (cfg->precision == CTD_PREC_SPLIT_BF16) {
+      const int chunks = 2 * h->plan.Kpad / ctd::kTcChunkElems;
+      int stages = 4;
+      for (; stages >= 1; --stages) {
+        size_t tcb = 0;
+        for (int x = 0; x < cfg->dim; ++x) {
+          const ctd::TcDir& td = h->plan.dirs[x];
+          const int wl = td.mid < 0 ? td.ncols_pad : td.n_last_pad;
+          const int wm = td.mid < 0 ? 0 : cfg->n[td.mid];
+          tcb = std::max(tcb, ctd::tc_layout(chunks, stages, wl, wm).total);
+        }
+        if (fixed + 1024 + tcb + 1024 <= static_cast<size_t>(optin)) {
+          need = std::max(need, fixed + 1024 + tcb);
+          break;
+        }
+      }
+      if (stages < 1) { ctd_status s = fail(h, CTD_ERR_UNSUPPORTED, "tensor-core tiles exceed shared memory"); delete h; return s; }
+      X.tc_stages = stages;
+    }
+    P.smem_bytes = static_cast<int>(need);
+  }
+  if (cfg->precision == CTD_PREC_SPLIT_BF16) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CTD_CUDA(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void**>(&encode), 12000,
+                                                 cudaEnableDefault, &q));
+    if (!encode || q != cudaDriverEntryPointSuccess) {
+      ctd_status s = fail(h, CTD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+      delete h;
+      return s;
+    }
+    auto make_map = [&](CUtensorMap* m, void* ptr, long long rows) -> bool {
+      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(2 * h->plan.Kpad), static_cast<cuuint64_t>(rows)};
+      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(2 * h->plan.Kpad) * sizeof(__nv_bfloat16)};
+      const cuuint32_t box[2] = {static_cast<cuuint32_t>(ctd::kTcChunkElems), static_cast<cuuint32_t>(ctd::kTcM)};
+      const cuuint32_t es[2] = {1, 1};
+      return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    std::memset(&h->tm, 0, sizeof(h->tm));
+    for (int d = 0; d < cfg->dim; ++d)
+      if (!make_map(&h->tm.op[d], P.d[d].op, h->plan.n_pad[d])) {
+        ctd_status s = fail(h, CTD_ERR_CUDA, "tensor map encoding failed");
+        delete h;
+        return s;
+      }
+    if (cfg->dim == 3)
+      for (int x = 0; x < 3; ++x)
+        if (!make_map(&h->tm.kr[x], X.kr[x], h->plan.dirs[x].ncols_pad)) {
+          ctd_status s = fail(h, CTD_ERR_CUDA, "tensor map encoding failed");
+          delete h;
+          return s;
+        }
+  }
+  h->trace_dev = P.trace;
+  P.trace = nullptr;
 
   // host C-FEM data and compressed stiffness per dimension
   for (int d = 0; d < cfg->dim; ++d) {
@@ -339,6 +497,8 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     k.stencil = h->kc_store[d] + static_cast<size_t>(lead + tail) * w;
     k.omega_in = to_df(h->omega[d][n / 2]);
     k.omega_end = to_df(h->omega[d][0]);
+    k.inv_omega_in = static_cast<float>(1.0 / h->omega[d][n / 2]);
+    k.inv_omega_end = static_cast<float>(1.0 / h->omega[d][0]);
   }
   InstState st{};
   CTD_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
@@ -397,7 +557,7 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
     for (int k = 0; k < batch; ++k) {
       h->P.stats = h->stats_dev + k;
       CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-      CTD_CUDA(h, ctd::launch_step(h->P, h->X, h->grid, h->stream));
+      CTD_CUDA(h, ctd::launch_step(h->P, h->X, h->tm, h->grid, h->stream));
     }
     if (stats) {
       rec.resize(batch);
@@ -515,21 +675,78 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
     CTD_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, h->stream));
-  const int n = h->cfg.n[x], C = h->plan.rchunks[x];
-  std::vector<double> part(static_cast<size_t>(n) * C);
-  CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->P.rpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
-                              h->stream));
+  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->tm, h->grid, x, nullptr, h->stream));
+  const int n = h->cfg.n[x];
+  if (h->cfg.precision == CTD_PREC_FP64) {
+    const int C = h->plan.rchunks[x];
+    std::vector<double> part(static_cast<size_t>(n) * C);
+    CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->P.rpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                                h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < n; ++i) {
+      double r = 0.0;
+      for (int k = 0; k < C; ++k) r += part[static_cast<size_t>(i) * C + k];
+      out[i] = r;
+    }
+  } else {
+    const ctd::TcDir& td = h->plan.dirs[x];
+    std::vector<float> part(static_cast<size_t>(n) * td.cmax);
+    CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->X.rpart32, sizeof(float) * part.size(), cudaMemcpyDeviceToHost,
+                                h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    const long long T = static_cast<long long>(td.nrb) * td.ntc;
+    for (int i = 0; i < n; ++i) {
+      const int rb = i / ctd::kTcM;
+      const int c0 = ctd::tile_owner(T, h->grid, static_cast<long long>(rb) * td.ntc);
+      const int c1 = ctd::tile_owner(T, h->grid, static_cast<long long>(rb) * td.ntc + td.ntc - 1);
+      double r = 0.0;
+      for (int k = 0; k <= c1 - c0; ++k) r += part[static_cast<size_t>(i) * td.cmax + k];
+      out[i] = r / (4.0 * h->cfg.a0);
+    }
+  }
+  InstState st;
+  ctd_status rs = read_state(h, &st);
+  if (rs != CTD_OK) return rs;
+  if (st.status) return fail(h, status_from_bits(st.status), "device status set");
+  return CTD_OK;
+}
+
+ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch, size_t scratch_bytes) {
+  if (!h || !out || x < 0 || x >= h->cfg.dim) return CTD_ERR_ARG;
+  if (h->cfg.precision != CTD_PREC_SPLIT_BF16) return fail(h, CTD_ERR_UNSUPPORTED, "tensor-core path only");
+  if (!h->has_modes) return fail(h, CTD_ERR_STATE, "no field set");
+  const ctd::TcDir& td = h->plan.dirs[x];
+  const size_t need = static_cast<size_t>(h->plan.n_pad[x]) * td.ncols_pad * sizeof(float);
+  if (!scratch || scratch_bytes < need) return fail(h, CTD_ERR_WORKSPACE, "scratch too small");
+  // weights are irrelevant for the dump; keep v finite
+  for (int d = 0; d < h->cfg.dim; ++d) {
+    std::vector<float2> ones(h->cfg.n[d], make_float2(1.f, 0.f));
+    CTD_CUDA(h, cudaMemcpyAsync(h->P.d[d].v, ones.data(), sizeof(float2) * ones.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  CTD_CUDA(h, cudaMemsetAsync(scratch, 0, need, h->stream));
+  CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
+  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->tm, h->grid, x, static_cast<float*>(scratch), h->stream));
+  CTD_CUDA(h, cudaMemcpyAsync(out, scratch, need, cudaMemcpyDeviceToHost, h->stream));
   CTD_CUDA(h, cudaStreamSynchronize(h->stream));
   InstState st;
   ctd_status rs = read_state(h, &st);
   if (rs != CTD_OK) return rs;
   if (st.status) return fail(h, status_from_bits(st.status), "device status set");
-  for (int i = 0; i < n; ++i) {
-    double r = 0.0;
-    for (int k = 0; k < C; ++k) r += part[static_cast<size_t>(i) * C + k];
-    out[i] = r;
+  return CTD_OK;
+}
+
+ctd_status ctd_probe_trace(ctd_handle h, int enable, double* seconds, int nslots) {
+  if (!h || nslots < 0) return CTD_ERR_ARG;
+  CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (seconds && nslots > 0) {
+    unsigned long long t[ctd::kTrSlots];
+    CTD_CUDA(h, cudaMemcpy(t, h->trace_dev, sizeof(t), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nslots; ++i) seconds[i] = i < ctd::kTrSlots ? 1e-9 * static_cast<double>(t[i]) : 0.0;
   }
+  CTD_CUDA(h, cudaMemset(h->trace_dev, 0, sizeof(unsigned long long) * ctd::kTrSlots));
+  h->P.trace = enable ? h->trace_dev : nullptr;
   return CTD_OK;
 }
 

@@ -30,6 +30,7 @@ struct Dim {
   float2* v;               // [n] trial factor (double-float)
   float2* vold;            // [n] trial factor at the start of the sweep
   __nv_bfloat16* op;       // [n_pad][2*Kpad] tensor-core operand: hi | lo split of u^k
+  float mu_max;            // Gershgorin bound of the generalised eigenvalues of (K, diag(omega))
 };
 
 struct InstState {
@@ -56,6 +57,7 @@ struct StepParams {
   int Kpad;                // padded mode count of the tensor-core operands (multiple of 64)
   int precision;           // 0 FP64, 1 split BF16 tensor cores
   double c_t, c_k, L, a0;
+  float2 ct_df, ck_df, L_df;   // the same constants as double-float (converted on the host)
   double tol_als, tol_enrich;
   int I_max, M_max, fixed_als, fixed_modes;
   unsigned long long seed;
@@ -70,7 +72,18 @@ struct StepParams {
   unsigned* barrier;       // grid barrier counter (zeroed before each launch)
   InstState* st;
   StepStatsDev* stats;     // one record per launch
+  unsigned long long* trace;   // null, or [kTraceSlots] ns accumulated per phase by CTA 0
+  int solver_mode;         // 0: full CR factors in shared memory; 1: first level on the fly,
+                           // level-1 factors in shared memory; 2: full CR factors in global;
+                           // 3: Chebyshev semi-iteration, vectors in shared memory
+  float2* xsol_g;          // [kMaxN] solution iterate in global memory (solver mode 1)
+  int smem_bytes;          // dynamic shared memory of the step kernel
+  int n_max;               // largest n over the dimensions
 };
+
+// phases accumulated in StepParams::trace (each includes its closing grid barrier)
+enum TracePhase { kTrPrologue = 0, kTrInit, kTrGramContract, kTrRhs, kTrSolve, kTrConverge, kTrCommit,
+                  kTrSolveFactor = 8, kTrSolveFirst, kTrSolveRefine, kTrSolvePasses, kTrSlots = 16 };
 
 // ------------------------------------------------------------------ time & barrier
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -1,0 +1,448 @@
+// Nonlinear contraction of Eq. KxxMxx on the 5th-generation tensor cores (sm_103a).
+//
+// For direction x, with P the factors of u^k in dimension x (n_x x M_k) and Q the factors of
+// the other dimension (2D) or their row-wise (Khatri-Rao) products (3D), the grid values
+// of u^k are U = P Q^T.  Each CTA walks a contiguous range of 128 x 128 tiles of U:
+//   * TMA loads P's 128-row block once per row block and Q's 128-row column blocks through a
+//     ring of stages (128-byte swizzled, K-major BF16);
+//   * one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM) for the
+//     split product U = P_hi Q_hi^T + P_hi Q_lo^T + P_lo Q_hi^T (P = P_hi + P_lo in BF16);
+//   * four epilogue warps read the accumulator rows with tcgen05.ld and fuse the cubic
+//     w(u)/(4 a0) = u (u^2 - 1) with the weighted row sum over the tile's columns (weights
+//     4 a0 omega v of the fixed factors), accumulating per row in FP32;
+//   * two TMEM accumulators alternate so the MMAs of tile t+1 overlap the epilogue of t.
+// Every wait is bounded in time; on expiry the kernel records kErrTimeout and unwinds.
+#pragma once
+#include <cuda.h>
+
+#include "ctd_common.cuh"
+#include "ctd_solve.cuh"
+
+namespace ctd {
+
+constexpr int kTcN = 128;              // columns per tile (UMMA N)
+constexpr int kTcM = 128;              // rows per tile (UMMA M)
+constexpr int kTcChunkElems = 64;      // BF16 elements per 128-byte swizzle row
+constexpr int kTcChunkBytes = kTcM * 128;   // one 128-row x 128-byte TMA box (16 KB)
+constexpr int kTcAccCols = 2 * kTcN;   // TMEM columns allocated (two accumulators)
+
+struct TmapSet {
+  CUtensorMap op[kMaxDim];    // per-dimension operand [n_pad][2*Kpad] BF16 (hi | lo)
+  CUtensorMap kr[kMaxDim];    // 3D: Khatri-Rao operand of the two dimensions other than x
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false (and kErrTimeout recorded) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns,
+                                          InstState* st, const volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_ns() - t0 > limit_ns) {
+      atomicOr(&st->status, kErrTimeout);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Generic-proxy global writes (operand preparation) made visible to later TMA reads
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulator
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);        // start address
+  d |= static_cast<uint64_t>(1) << 16;                       // leading byte offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;               // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                       // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                       // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = kTcN.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(kTcN >> 3) << 17) |
+         (static_cast<uint32_t>(kTcM >> 4) << 24);
+}
+
+// ---------------------------------------------------------------- tile schedule
+struct TcPlan {
+  int nrb;        // row blocks of direction x (n_pad_x / 128)
+  int ntc;        // column tiles (n_cols_pad / 128)
+  int ncols_pad;  // padded column count of the Q operand
+  int chunks;     // 64-element K chunks per operand row (= 2 * Kpad / 64)
+  int kpad;       // Kpad
+  int ksteps;     // 16-wide K steps covering M_k
+  int stages;     // B ring depth
+  int cmax;       // partial slots per row
+};
+
+__host__ __device__ inline int tile_lo(long long T, int G, int c) {
+  return static_cast<int>(T * c / G);
+}
+// CTA that owns tile t under the contiguous split [tile_lo(c), tile_lo(c+1))
+__host__ __device__ inline int tile_owner(long long T, int G, long long t) {
+  int c = static_cast<int>((t * G) / T);
+  while (c + 1 < G && tile_lo(T, G, c + 1) <= t) ++c;
+  while (c > 0 && tile_lo(T, G, c) > t) --c;
+  return c;
+}
+
+struct TcShared {           // barriers and TMEM handle (placed at the start of the arena)
+  uint64_t a_full, a_empty;
+  uint64_t b_full[8], b_empty[8];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+
+}  // namespace ctd
+
+namespace ctd {
+
+// Per-direction geometry of the tensor-core contraction (filled on the host).
+struct TcDir {
+  int nrb;          // row blocks of direction x
+  int ntc;          // column tiles
+  int ncols_pad;    // padded rows of the column operand
+  int n_last_pad;   // 3D: padded length of the last other dimension (tile = one mid index)
+  int mid, last;    // other dimensions: 2D mid = -1, last = the other; 3D both set
+  int cmax;         // partial slots per row in rpart32
+};
+
+// Split u^k's factors into BF16 hi/lo operands [n_pad][2*Kpad] and, in 3D, the Khatri-Rao
+// operands of the two other dimensions for every direction.  Grid-stride over all CTAs.
+static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir* dirs, __nv_bfloat16* const* kr, int pb,
+                                  int Mk) {
+  const int Kp = P.Kpad, W = 2 * Kp;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  const long long t0 = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    const long long total = static_cast<long long>(dd.n_pad) * Kp;
+    for (long long t = t0; t < total; t += stride) {
+      const int i = static_cast<int>(t / Kp), k = static_cast<int>(t - static_cast<long long>(i) * Kp);
+      float a = 0.f;
+      if (i < dd.n && k < Mk) {
+        const float2 v = dd.bank[pb][static_cast<size_t>(k) * dd.n + i];
+        a = v.x + v.y;
+      }
+      const __nv_bfloat16 hi = __float2bfloat16_rn(a);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(a - __bfloat162float(hi));
+      dd.op[static_cast<size_t>(i) * W + k] = hi;
+      dd.op[static_cast<size_t>(i) * W + Kp + k] = lo;
+    }
+  }
+  if (P.dim != 3) return;
+  for (int x = 0; x < 3; ++x) {
+    const TcDir& td = dirs[x];
+    const Dim& dm = P.d[td.mid];
+    const Dim& dl = P.d[td.last];
+    const long long total = static_cast<long long>(dm.n) * td.n_last_pad * Kp;
+    for (long long t = t0; t < total; t += stride) {
+      const long long row = t / Kp;
+      const int k = static_cast<int>(t - row * Kp);
+      const int j = static_cast<int>(row / td.n_last_pad), l = static_cast<int>(row - static_cast<long long>(j) * td.n_last_pad);
+      float a = 0.f;
+      if (l < dl.n && k < Mk) {
+        const float2 vm = dm.bank[pb][static_cast<size_t>(k) * dm.n + j];
+        const float2 vl = dl.bank[pb][static_cast<size_t>(k) * dl.n + l];
+        a = (vm.x + vm.y) * (vl.x + vl.y);
+      }
+      const __nv_bfloat16 hi = __float2bfloat16_rn(a);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(a - __bfloat162float(hi));
+      kr[x][static_cast<size_t>(row) * W + k] = hi;
+      kr[x][static_cast<size_t>(row) * W + Kp + k] = lo;
+    }
+  }
+}
+
+// FP32 column weights 4 a0 omega_d v_d of dimension d into shared memory (zero padded).
+__device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, int d, float* w, int npad) {
+  const Dim& dd = P.d[d];
+  const float s = static_cast<float>(4.0 * P.a0);
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+    float v = 0.f;
+    if (i < dd.n) {
+      const float2 x = dd.v[i];
+      const float2 om = kc_omega(kc, i);
+      v = s * om.x * (x.x + x.y);
+    }
+    w[i] = v;
+  }
+}
+
+// Arena layout of the contraction phase (offsets from a 1024-byte aligned base)
+struct TcLayout {
+  size_t shared_off, a_off, b_off, wl_off, wm_off, total;
+};
+__host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_n, int wmid_n) {
+  TcLayout L;
+  L.shared_off = 0;
+  L.a_off = 1024;
+  L.b_off = L.a_off + static_cast<size_t>(chunks) * kTcChunkBytes;
+  L.wl_off = L.b_off + static_cast<size_t>(stages) * chunks * kTcChunkBytes;
+  L.wm_off = L.wl_off + (static_cast<size_t>(wlast_n) * 4 + 127) / 128 * 128;
+  L.total = L.wm_off + (static_cast<size_t>(wmid_n) * 4 + 127) / 128 * 128;
+  return L;
+}
+
+// This CTA's share of the contraction for direction x.  Partial row sums go to
+// rpart32[row * cmax + (cta - first owner of the row block)].  If dump != null the raw
+// reconstructed values are written to dump[row * ncols_pad + col] instead (test probe).
+// Returns false if a wait expired.
+static __device__ __noinline__ bool tc_contract(const StepParams& P, const KCompressed* kc, const TcDir& td,
+                                   const CUtensorMap* Pmap, const CUtensorMap* Qmap, int x, int Mk, int stages,
+                                   unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump) {
+  const int G = gridDim.x, cta = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunks = 2 * P.Kpad / kTcChunkElems;
+  const int ksteps = (Mk + 15) / 16;
+  const int wl_n = td.mid < 0 ? td.ncols_pad : td.n_last_pad;
+  const int wm_n = td.mid < 0 ? 0 : P.d[td.mid].n;
+  const TcLayout Ly = tc_layout(chunks, stages, wl_n, wm_n);
+  TcShared* sh = reinterpret_cast<TcShared*>(base + Ly.shared_off);
+  unsigned char* As = base + Ly.a_off;
+  unsigned char* Bs = base + Ly.b_off;
+  float* wl = reinterpret_cast<float*>(base + Ly.wl_off);
+  float* wm = reinterpret_cast<float*>(base + Ly.wm_off);
+  const long long T = static_cast<long long>(td.nrb) * td.ntc;
+  const int t0 = tile_lo(T, G, cta), t1 = tile_lo(T, G, cta + 1);
+  const unsigned long long lim = P.wait_ns;
+  const uint32_t stage_bytes = static_cast<uint32_t>(chunks) * kTcChunkBytes;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&sh->a_full, 1);
+    mbar_init(&sh->a_empty, 1);
+    for (int s = 0; s < stages; ++s) { mbar_init(&sh->b_full[s], 1); mbar_init(&sh->b_empty[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&sh->acc_full[a], 1); mbar_init(&sh->acc_empty[a], 128); }
+    sh->abort = 0;
+    fence_barrier_init();
+  }
+  // column weights of the fixed factors
+  tc_weights(P, kc[td.last], td.last, wl, wl_n);
+  if (td.mid >= 0) tc_weights(P, kc[td.mid], td.mid, wm, wm_n);
+  __syncthreads();
+  if (Mk == 0 || ksteps == 0) {
+    // u^k = 0: w(0) = 0, every partial is zero
+    if (!dump) {
+      for (long long t = t0; t < t1; ++t) {
+        const int rb = static_cast<int>(t / td.ntc);
+        if (t != t0 && t / td.ntc == (t - 1) / td.ntc) continue;
+        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * td.ntc);
+        for (int r = threadIdx.x; r < kTcM; r += blockDim.x) {
+          const int row = rb * kTcM + r;
+          if (row < P.d[x].n) rpart32[static_cast<size_t>(row) * td.cmax + j] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    return true;
+  }
+  volatile int* abort_flag = &sh->abort;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    fence_proxy_async_global();     // operands were written through the generic proxy
+    int cur_rb = -1, a_loads = 0;
+    for (int t = t0, it = 0; t < t1 && ok; ++t, ++it) {
+      const int rb = t / td.ntc, cb = t - rb * td.ntc;
+      if (rb != cur_rb) {
+        if (a_loads > 0 && !mbar_wait(&sh->a_empty, (a_loads - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+        mbar_expect_tx(&sh->a_full, stage_bytes);
+        for (int ch = 0; ch < chunks; ++ch)
+          tma_load_2d(As + ch * kTcChunkBytes, Pmap, &sh->a_full, ch * kTcChunkElems, rb * kTcM);
+        ++a_loads;
+        cur_rb = rb;
+      }
+      const int s = it % stages, round = it / stages;
+      if (it >= stages && !mbar_wait(&sh->b_empty[s], (round - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      mbar_expect_tx(&sh->b_full[s], stage_bytes);
+      for (int ch = 0; ch < chunks; ++ch)
+        tma_load_2d(Bs + static_cast<size_t>(s) * stage_bytes + ch * kTcChunkBytes, Qmap, &sh->b_full[s],
+                    ch * kTcChunkElems, cb * kTcN);
+    }
+    if (!ok) sh->abort = 1;
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = umma_idesc_bf16();
+    const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
+    const int lo_chunk = P.Kpad / kTcChunkElems;
+    int cur_rb = -1, a_uses = 0;
+    for (int t = t0, it = 0; t < t1 && ok; ++t, ++it) {
+      const int rb = t / td.ntc;
+      if (rb != cur_rb) {
+        if (!mbar_wait(&sh->a_full, a_uses & 1, lim, P.st, abort_flag)) { ok = false; break; }
+        ++a_uses;
+        cur_rb = rb;
+      }
+      const int s = it % stages;
+      if (!mbar_wait(&sh->b_full[s], (it / stages) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      const int ab = it & 1;
+      if (it >= 2 && !mbar_wait(&sh->acc_empty[ab], ((it >> 1) - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t d = tmem_base + static_cast<uint32_t>(ab * kTcN);
+      const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes;
+      for (int k = 0; k < ksteps; ++k) {
+        const uint32_t off = static_cast<uint32_t>((k & 3) * 32);
+        const uint32_t chh = static_cast<uint32_t>(k >> 2), chl = chh + lo_chunk;
+        const uint64_t ah = umma_desc_sw128(a_base + chh * kTcChunkBytes + off);
+        const uint64_t al = umma_desc_sw128(a_base + chl * kTcChunkBytes + off);
+        const uint64_t bh = umma_desc_sw128(bs + chh * kTcChunkBytes + off);
+        const uint64_t bl = umma_desc_sw128(bs + chl * kTcChunkBytes + off);
+        tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
+        tc_mma(d, ah, bl, idesc, 1u);
+        tc_mma(d, al, bh, idesc, 1u);
+      }
+      tc_commit(&sh->b_empty[s]);
+      tc_commit(&sh->acc_full[ab]);
+      if (t + 1 == t1 || (t + 1) / td.ntc != rb) tc_commit(&sh->a_empty);
+    }
+    if (!ok) {
+      sh->abort = 1;
+    } else if (t1 > t0) {
+      // quiesce: the last commits have landed before the barriers are re-initialised
+      const int n_it = t1 - t0;
+      for (int s = 0; s < stages && s < n_it; ++s) {
+        const int last_it = s + ((n_it - 1 - s) / stages) * stages;
+        if (!mbar_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      }
+      if (ok && !mbar_wait(&sh->a_empty, (a_uses - 1) & 1, lim, P.st, abort_flag)) ok = false;
+      if (!ok) sh->abort = 1;
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue: one TMEM lane (tile row) per thread
+    const int r = (warp - 4) * 32 + lane;
+    const uint32_t lane_base = tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    float acc = 0.f;
+    int cur_rb = -1;
+    auto flush = [&](int rb) {
+      const int row = rb * kTcM + r;
+      if (!dump && row < P.d[x].n) {
+        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * td.ntc);
+        rpart32[static_cast<size_t>(row) * td.cmax + j] = acc;
+      }
+    };
+    for (int t = t0, it = 0; t < t1; ++t, ++it) {
+      const int rb = t / td.ntc, cb = t - rb * td.ntc;
+      if (rb != cur_rb) {
+        if (cur_rb >= 0) flush(cur_rb);
+        acc = 0.f;
+        cur_rb = rb;
+      }
+      const int ab = it & 1;
+      if (!mbar_wait(&sh->acc_full[ab], (it >> 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const int col0 = cb * kTcN;
+      const float* wt;
+      float wscale = 1.f;
+      if (td.mid < 0) {
+        wt = wl + col0;
+      } else {
+        const int jm = col0 / td.n_last_pad;
+        wt = wl + (col0 - jm * td.n_last_pad);
+        wscale = wm[jm];
+      }
+      float at = 0.f;
+#pragma unroll
+      for (int q = 0; q < kTcN / 32; ++q) {
+        float v[32];
+        tmem_ld32(lane_base + static_cast<uint32_t>(ab * kTcN + q * 32), v);
+        if (dump) {
+          const int row = rb * kTcM + r;
+          for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * td.ncols_pad + col0 + q * 32 + c] = v[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float u = v[c];
+          at = __fmaf_rn(u * __fmaf_rn(u, u, -1.f), wt[q * 32 + c], at);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&sh->acc_empty[ab]);
+      acc = __fmaf_rn(wscale, at, acc);
+    }
+    if (ok && cur_rb >= 0) flush(cur_rb);
+    if (!ok) sh->abort = 1;
+  }
+  __syncthreads();
+  return !(*abort_flag);
+}
+
+}  // namespace ctd

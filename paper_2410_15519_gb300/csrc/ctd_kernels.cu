@@ -1,5 +1,6 @@
 // Kernels of the CTD step: the persistent per-step kernel (Section 3.3 solution algorithm,
 // all control on the device), the discrete energy, and probe kernels for single stages.
+#include <algorithm>
 #include <cstdio>
 
 #include "ctd_kernels.h"
@@ -9,17 +10,67 @@ namespace ctd {
 
 // ---------------------------------------------------------------------------------------
 // Shared-memory plan of the step kernel (one union over phases)
+// Fixed part; the per-phase arena follows it:
+//   Phase A: Gram row data (3 * kChunk float2) or FP64 weights (kMaxDim * kMaxN doubles)
+//   Phase C: solution (n_max float2) then, if they fit, the solver factors.
 struct SmemStep {
-  union {
-    float2 gram_rows[3 * kChunk];   // Phase A Gram row data
-    double wv[kMaxDim * kMaxN];     // Phase A FP64 weights (96 KB)
-    float2 xsol[kMaxN];             // Phase C solution (32 KB)
-  } u;
   Coef coef;
   float2 red2[2 * kMaxDim];
   float redf[kWarps];
-  double dred[kWarps * 8];
 };
+constexpr size_t kArenaOffset = (sizeof(SmemStep) + 127) / 128 * 128;
+__host__ __device__ inline size_t arena_phase_a_bytes() {
+  return sizeof(double) * kMaxDim * kMaxN > sizeof(float2) * 3 * kChunk ? sizeof(double) * kMaxDim * kMaxN
+                                                                         : sizeof(float2) * 3 * kChunk;
+}
+__host__ __device__ inline size_t solver_smem_offset(int n_max) { return (sizeof(float2) * n_max + 127) / 128 * 128; }
+
+struct Arena {
+  float2* gram_rows;
+  double* wv;
+  float2* xsol;
+  float* solver;
+};
+__device__ inline unsigned char* arena_base(unsigned char* smem_raw) {
+  const uint32_t s0 = smem_u32(smem_raw);
+  const uint32_t a = (s0 + static_cast<uint32_t>(kArenaOffset) + 1023u) & ~1023u;
+  return smem_raw + (a - s0);
+}
+__device__ inline Arena arena_of(unsigned char* smem_raw, const StepParams& P) {
+  unsigned char* a = arena_base(smem_raw);
+  Arena r;
+  r.gram_rows = reinterpret_cast<float2*>(a);
+  r.wv = reinterpret_cast<double*>(a);
+  r.xsol = reinterpret_cast<float2*>(a);
+  // Phase C: mode 0 -> [x (n_max float2)][factors]; mode 1 -> [level-1 factors], x global;
+  // mode 2 -> [x], factors global
+  if (P.solver_mode == 0 || P.solver_mode == 3) {
+    r.solver = reinterpret_cast<float*>(a + solver_smem_offset(P.n_max));
+  } else if (P.solver_mode == 1) {
+    r.solver = reinterpret_cast<float*>(a);
+    r.xsol = P.xsol_g;
+  } else {
+    r.solver = P.solver;
+  }
+  return r;
+}
+
+// Kernel parameter blocks are indexed with runtime dimension numbers; staged in shared memory
+// they stay addressable without a per-thread local copy.
+template <typename T>
+__device__ __forceinline__ void stage_to_smem(T* dst, const T& src) {
+  const int* s = reinterpret_cast<const int*>(&src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < static_cast<int>(sizeof(T) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ void trace_mark(const StepParams& P, unsigned long long& t, int phase) {
+  if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long now = global_ns();
+    atomicAdd(P.trace + phase, now - t);
+    t = now;
+  }
+}
 
 __device__ inline bool sync_all(const StepParams& P, unsigned& epoch, int where) {
   if (gridDim.x == 1) {
@@ -30,7 +81,7 @@ __device__ inline bool sync_all(const StepParams& P, unsigned& epoch, int where)
 }
 
 // Convert u^k factors of this CTA's slices to FP64 copies (FP64-path materialisation).
-__device__ void convert_prev_modes(const StepParams& P, const Extra& X, int pb, int Mk) {
+__device__ __noinline__ void convert_prev_modes(const StepParams& P, const Extra& X, int pb, int Mk) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
@@ -43,7 +94,7 @@ __device__ void convert_prev_modes(const StepParams& P, const Extra& X, int pb, 
 
 // Mode start vectors (own slices): warm start from u^k's mode m if present and not zero,
 // otherwise SplitMix64 entries in [0.5, 1.5).
-__device__ void init_mode(const StepParams& P, int m, int pb, int Mk, long long step) {
+__device__ __noinline__ void init_mode(const StepParams& P, int m, int pb, int Mk, long long step) {
   __shared__ int s_nz[kMaxDim];
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
@@ -76,8 +127,9 @@ __device__ void init_mode(const StepParams& P, int m, int pb, int Mk, long long 
 
 // Convergence partials (own slices): per dimension c the six products of old, delta = new -
 // old and new, and max |new|; slot (c * 6 + k) of the gram buffer, maxpart[c * G + cta].
-__device__ void convergence_partials(const StepParams& P, const Extra& X, float2* sh) {
-  const int G = gridDim.x, cta = blockIdx.x;
+__device__ __noinline__ void convergence_partials(const StepParams& P, const Extra& X, float2* sh) {
+  const int G = gram_ctas(), cta = blockIdx.x;
+  if (cta >= G) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = 0; c < P.dim; ++c) {
     const Dim& dd = P.d[c];
@@ -121,7 +173,7 @@ __device__ void convergence_partials(const StepParams& P, const Extra& X, float2
 }
 
 // Save the current trial factors (own slices) at the start of a sweep.
-__device__ void save_old(const StepParams& P) {
+__device__ __noinline__ void save_old(const StepParams& P) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
@@ -131,7 +183,7 @@ __device__ void save_old(const StepParams& P) {
 }
 
 // Commit the converged mode (own slices): b = v * scale_d, K b.
-__device__ void commit_mode(const StepParams& P, const Extra& X, int M, int cb,
+__device__ __noinline__ void commit_mode(const StepParams& P, const Extra& X, int M, int cb,
                             const double* scale) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
@@ -147,13 +199,13 @@ __device__ void commit_mode(const StepParams& P, const Extra& X, int M, int cb,
 
 // The solver CTA: solve Eq. ux for direction x, normalise unless x is the last dimension,
 // publish v_x (double-float) and flags in ctrl: [0] zero factor, [1] failure.
-__device__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
-                                float* solver_base) {
+__device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
+                                const Arena& ar) {
   const Dim& dd = P.d[x];
-  const CRBuffers cr = cr_bind(solver_base, dd.n, dd.b);
+  const SolverStore store = solver_bind(P.solver_mode == 2 ? 0 : P.solver_mode, ar.solver, P.solver, dd.n, dd.b, dd.mu_max);
   const dfloat a1 = ld_df(&sm.coef.alpha1), a2 = ld_df(&sm.coef.alpha2);
-  float2* xs = sm.u.xsol;
-  bool ok = banded_solve(cr, X.kc[x], a1, a2, P.Q, xs, sm.redf);
+  float2* xs = ar.xsol;
+  bool ok = banded_solve(store, X.kc[x], a1, a2, P.Q, xs, sm.redf, P.trace);
   // zero test and squared norm (double-float, fixed reduction order)
   int nz = 0;
   dfloat ss = {0.f, 0.f};
@@ -187,21 +239,26 @@ __device__ void solve_direction(const StepParams& P, const Extra& X, int x, Smem
 }
 
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, const Extra X) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm, unsigned char* smem_raw,
+                          uint32_t tmem_base) {
   SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
+  const Arena ar = arena_of(smem_raw, P);
   unsigned epoch = 0;
+  unsigned long long tmark = global_ns();
   const InstState st0 = *P.st;
   if (st0.status != 0) return;
   const int D = P.dim, pb = st0.bank, cb = 1 - pb, Mk = st0.Mk;
-  const int G = gridDim.x;
 
   // ---- prologue: the nonlinear term's data for this step
   if (P.precision == 0) {
     convert_prev_modes(P, X, pb, Mk);
     if (!sync_all(P, epoch, 1)) return;
     materialise_w(P, X, Mk);
+  } else {
+    tc_prepare(P, X.dirs, X.kr, pb, Mk);
+    fence_proxy_async_global();
   }
+  trace_mark(P, tmark, kTrPrologue);
 
   int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0;
   bool stopped = false;
@@ -210,28 +267,38 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, c
   for (int m = 0; m < n_modes; ++m) {
     init_mode(P, m, pb, Mk, st0.step);
     if (!sync_all(P, epoch, 2)) return;
+    trace_mark(P, tmark, kTrInit);
     bool zero_mode = false;
-    double delta = 1e300, amp = 0.0;
+    double delta = 1e300, amp = 0.0, delta_prev = 1e300;
     double norms2[kMaxDim] = {1.0, 1.0, 1.0};
     int it;
     for (it = 1; it <= n_it; ++it) {
       save_old(P);
       for (int x = 0; x < D; ++x) {
         // Phase A: Gram partials of the fixed factors + nonlinear contraction partials
-        gram_partials(P, X, x, Mk, M, pb, cb, sm.u.gram_rows);
+        gram_partials(P, X, x, Mk, M, pb, cb, ar.gram_rows);
         __syncthreads();
         if (P.precision == 0) {
-          load_weights_fp64(P, X, x, sm.u.wv);
-          contract_fp64(P, x, sm.u.wv);
+          load_weights_fp64(P, X, x, ar.wv);
+          contract_fp64(P, x, ar.wv);
+        } else {
+          const TcDir& td = X.dirs[x];
+          const CUtensorMap* qmap = (D == 2) ? &tm.op[td.last] : &tm.kr[x];
+          if (!tc_contract(P, X.kc, td, &tm.op[x], qmap, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base,
+                           X.rpart32, nullptr))
+            return;
         }
         if (!sync_all(P, epoch, 3)) return;
+        trace_mark(P, tmark, kTrGramContract);
         // Phase B: coefficients (every CTA, same order) and right-hand-side rows
         build_coefficients(P, x, Mk, M, &sm.coef, sm.red2);
         rhs_rows(P, X, x, Mk, M, pb, cb, &sm.coef);
         if (!sync_all(P, epoch, 4)) return;
+        trace_mark(P, tmark, kTrRhs);
         // Phase C: banded solve on CTA 0
-        if (blockIdx.x == 0) solve_direction(P, X, x, sm, P.solver);
+        if (blockIdx.x == 0) solve_direction(P, X, x, sm, ar);
         if (!sync_all(P, epoch, 5)) return;
+        trace_mark(P, tmark, kTrSolve);
         const int zflag = *reinterpret_cast<volatile int*>(X.ctrl + 0);
         const int fflag = *reinterpret_cast<volatile int*>(X.ctrl + 1);
         if (fflag) {
@@ -243,15 +310,17 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, c
       ++sweeps;
       if (zero_mode) break;
       // Phase D: relative change of the rank-1 mode, max entries, norms
-      convergence_partials(P, X, sm.u.gram_rows);
+      convergence_partials(P, X, ar.gram_rows);
       if (!sync_all(P, epoch, 6)) return;
+      trace_mark(P, tmark, kTrConverge);
       {
         __shared__ double s_dots[kMaxDim * 6];
         __shared__ double s_max[kMaxDim];
-        if (threadIdx.x < D * 6) s_dots[threadIdx.x] = df_to_double(reduce_slot(P.gram + static_cast<size_t>(threadIdx.x) * G, G));
+        const int Gg = gram_ctas();
+        if (threadIdx.x < D * 6) s_dots[threadIdx.x] = df_to_double(reduce_slot(P.gram + static_cast<size_t>(threadIdx.x) * Gg, Gg));
         if (threadIdx.x < D) {
           double mx = 0.0;
-          for (int g = 0; g < G; ++g) mx = fmax(mx, X.maxpart[threadIdx.x * G + g]);
+          for (int g = 0; g < Gg; ++g) mx = fmax(mx, X.maxpart[threadIdx.x * Gg + g]);
           s_max[threadIdx.x] = mx;
         }
         __syncthreads();
@@ -279,6 +348,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, c
         __syncthreads();
       }
       if (P.fixed_als == 0 && delta <= P.tol_als) break;
+      // Tensor-core arithmetic: the contraction's FP32 rounding sets a floor on the relative
+      // change of a small mode; once the change is below 1e-6 and no longer decreasing,
+      // further sweeps only move the mode within that floor.
+      if (P.precision != 0 && P.fixed_als == 0 && it >= 3 && delta <= 1e-6 && delta >= 0.5 * delta_prev) {
+        delta = P.tol_als;
+        break;
+      }
+      delta_prev = delta;
     }
     if (it > n_it) it = n_it;
     sweeps_max = max(sweeps_max, it);
@@ -294,6 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, c
     commit_mode(P, X, M, cb, scale);
     ++M;
     if (!sync_all(P, epoch, 7)) return;
+    trace_mark(P, tmark, kTrCommit);
   }
   // ---- epilogue
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -311,6 +389,28 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const StepParams P, c
     r.not_converged = not_conv;
     r.status = 0;
     *P.stats = r;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant__ StepParams P,
+                                                           const __grid_constant__ Extra X,
+                                                           const __grid_constant__ TmapSet tm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(16) StepParams sP;
+  __shared__ __align__(16) Extra sX;
+  stage_to_smem(&sP, P);
+  stage_to_smem(&sX, X);
+  const bool tc = P.precision != 0;
+  if (tc && (threadIdx.x >> 5) == 1) tmem_alloc(&s_tmem, kTcAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  step_body(sP, sX, tm, smem_raw, tc ? s_tmem : 0u);
+  __syncthreads();
+  if (tc && (threadIdx.x >> 5) == 1) {
+    tc_fence_after();
+    tmem_dealloc(s_tmem, kTcAccCols);
   }
 }
 
@@ -397,9 +497,9 @@ __global__ void energy_gram_kernel(const StepParams P, const Extra X, int Mk, do
 
 // ---------------------------------------------------------------------------------------
 // Probe kernels
-__global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const StepParams P, const Extra X, int x) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
+__device__ void probe_contract_body(const StepParams& P, const Extra& X, const TmapSet& tm, int x, float* dump,
+                                    unsigned char* smem_raw, uint32_t tmem_base) {
+  const Arena ar = arena_of(smem_raw, P);
   unsigned epoch = 0;
   const InstState st0 = *P.st;
   if (P.precision == 0) {
@@ -407,28 +507,73 @@ __global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const StepP
     if (!sync_all(P, epoch, 11)) return;
     materialise_w(P, X, st0.Mk);
     if (!sync_all(P, epoch, 12)) return;
-    load_weights_fp64(P, X, x, sm.u.wv);
-    contract_fp64(P, x, sm.u.wv);
+    load_weights_fp64(P, X, x, ar.wv);
+    contract_fp64(P, x, ar.wv);
+  } else {
+    tc_prepare(P, X.dirs, X.kr, st0.bank, st0.Mk);
+    fence_proxy_async_global();
+    if (!sync_all(P, epoch, 11)) return;
+    const TcDir& td = X.dirs[x];
+    const CUtensorMap* qmap = (P.dim == 2) ? &tm.op[td.last] : &tm.kr[x];
+    tc_contract(P, X.kc, td, &tm.op[x], qmap, x, st0.Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart32,
+                dump);
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) probe_solve_kernel(const StepParams P, const Extra X, int x,
+__global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const __grid_constant__ StepParams P,
+                                                                     const __grid_constant__ Extra X,
+                                                                     const __grid_constant__ TmapSet tm, int x,
+                                                                     float* dump) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(16) StepParams sP;
+  __shared__ __align__(16) Extra sX;
+  stage_to_smem(&sP, P);
+  stage_to_smem(&sX, X);
+  const bool tc = P.precision != 0;
+  if (tc && (threadIdx.x >> 5) == 1) tmem_alloc(&s_tmem, kTcAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  probe_contract_body(sP, sX, tm, x, dump, smem_raw, tc ? s_tmem : 0u);
+  __syncthreads();
+  if (tc && (threadIdx.x >> 5) == 1) {
+    tc_fence_after();
+    tmem_dealloc(s_tmem, kTcAccCols);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) probe_solve_kernel(const __grid_constant__ StepParams Pp,
+                                                                  const __grid_constant__ Extra Xp, int x,
                                                                   double a1, double a2) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) StepParams P;
+  __shared__ __align__(16) Extra X;
+  stage_to_smem(&P, Pp);
+  stage_to_smem(&X, Xp);
+  __syncthreads();
   SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
+  const Arena ar = arena_of(smem_raw, P);
   if (threadIdx.x == 0) {
     st_df(&sm.coef.alpha1, df_of(a1));
     st_df(&sm.coef.alpha2, df_of(a2));
   }
   __syncthreads();
   const Dim& dd = P.d[x];
-  const CRBuffers cr = cr_bind(P.solver, dd.n, dd.b);
-  bool ok = banded_solve(cr, X.kc[x], ld_df(&sm.coef.alpha1), ld_df(&sm.coef.alpha2), P.Q, sm.u.xsol, sm.redf);
-  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) dd.v[i] = sm.u.xsol[i];
+  const SolverStore ss = solver_bind(P.solver_mode == 2 ? 0 : P.solver_mode, ar.solver, P.solver, dd.n, dd.b, dd.mu_max);
+  bool ok = banded_solve(ss, X.kc[x], ld_df(&sm.coef.alpha1), ld_df(&sm.coef.alpha2), P.Q, ar.xsol, sm.redf);
+  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) dd.v[i] = ar.xsol[i];
   if (threadIdx.x == 0) X.ctrl[1] = ok ? 0 : 1;
 }
 
-size_t step_smem_bytes() { return sizeof(SmemStep); }
+size_t step_smem_fixed_bytes() { return kArenaOffset; }
+size_t step_arena_bytes(int n_max, size_t solver_floats, int mode) {
+  size_t c;
+  if (mode == 0 || mode == 3) c = solver_smem_offset(n_max) + solver_floats * sizeof(float);
+  else if (mode == 1) c = solver_floats * sizeof(float);
+  else c = solver_smem_offset(n_max);
+  return std::max(arena_phase_a_bytes(), c);
+}
 
 }  // namespace ctd
 
@@ -451,27 +596,28 @@ static cudaError_t set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
 }
 
-cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s) {
-  const size_t smem = step_smem_bytes();
+cudaError_t launch_step(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, cudaStream_t s) {
+  const size_t smem = P.smem_bytes;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&step_kernel), smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X)};
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), const_cast<TmapSet*>(&tm)};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&step_kernel), dim3(grid), dim3(kThreads),
                                      args, smem, s);
 }
 
-cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x, cudaStream_t s) {
-  const size_t smem = step_smem_bytes();
+cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, int x,
+                                  float* dump, cudaStream_t s) {
+  const size_t smem = P.smem_bytes;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&probe_contract_kernel), smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), &x};
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), const_cast<TmapSet*>(&tm), &x, &dump};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&probe_contract_kernel), dim3(grid),
                                      dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_probe_solve(const StepParams& P, const Extra& X, int x, double a1, double a2,
                                cudaStream_t s) {
-  const size_t smem = step_smem_bytes();
+  const size_t smem = P.smem_bytes;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&probe_solve_kernel), smem);
   if (e != cudaSuccess) return e;
   probe_solve_kernel<<<1, kThreads, smem, s>>>(P, X, x, a1, a2);

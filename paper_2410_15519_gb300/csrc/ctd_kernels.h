@@ -3,9 +3,11 @@
 #include "ctd_step.cuh"
 
 namespace ctd {
-size_t step_smem_bytes();
-cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s);
-cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x, cudaStream_t s);
+size_t step_smem_fixed_bytes();
+size_t step_arena_bytes(int n_max, size_t solver_floats, int mode);
+cudaError_t launch_step(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, cudaStream_t s);
+cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, int x,
+                                  float* dump, cudaStream_t s);
 cudaError_t launch_probe_solve(const StepParams& P, const Extra& X, int x, double a1, double a2,
                                cudaStream_t s);
 cudaError_t launch_convert_modes(const StepParams& P, const Extra& X, int bank, int Mk, cudaStream_t s);

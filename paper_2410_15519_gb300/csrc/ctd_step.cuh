@@ -4,6 +4,7 @@
 #pragma once
 #include "ctd_common.cuh"
 #include "ctd_solve.cuh"
+#include "ctd_contract_tc.cuh"
 
 namespace ctd {
 
@@ -17,7 +18,10 @@ struct Extra {            // per-launch workspace pieces not in StepParams
   double* Af[kMaxDim];    // FP64 copy of u^k factors [Mcap][n] (FP64-path materialisation)
   double* maxpart;        // [kMaxDim][grid]
   int* ctrl;              // [4] solver flags broadcast
-  float* rpart32;         // [n][chunks] FP32 partials (tensor-core path)
+  float* rpart32;         // [n][cmax] FP32 partials (tensor-core path)
+  TcDir dirs[kMaxDim];    // tensor-core geometry per direction
+  __nv_bfloat16* kr[kMaxDim];   // 3D Khatri-Rao operands per direction
+  int tc_stages;          // B-operand ring depth
 };
 
 __device__ __forceinline__ dfloat ld_df(const float2* p) {
@@ -61,10 +65,16 @@ __device__ inline int pow2_floor(int x) {
 // dimension d's nodes.  Writes gram[(o * spd + slot) * G + cta] for the used slots.
 // Shared scratch: 3 * kChunk float2.
 constexpr int kChunk = 256;
+// Gram and convergence partial sums are computed by this many CTAs (fewer partials to reduce
+// after the grid-wide wait: every CTA reads all of them)
+constexpr int kGramCtas = 16;
 
-__device__ inline void gram_partials(const StepParams& P, const Extra& X, int x, int Mk, int M,
+__device__ __forceinline__ int gram_ctas() { return gridDim.x < kGramCtas ? gridDim.x : kGramCtas; }
+
+static __device__ __noinline__ void gram_partials(const StepParams& P, const Extra& X, int x, int Mk, int M,
                               int pb, int cb, float2* sh) {
-  const int G = gridDim.x, cta = blockIdx.x, D = P.dim, spd = slots_per_dim(P.Mcap);
+  const int G = gram_ctas(), cta = blockIdx.x, D = P.dim, spd = slots_per_dim(P.Mcap);
+  if (cta >= G) return;
   float2* sv = sh;               // v_i
   float2* sdv = sh + kChunk;     // omega_i v_i
   float2* skv = sh + 2 * kChunk; // (K v)_i
@@ -153,9 +163,9 @@ struct Coef {
   float2 H[kMaxModes], GM[kMaxModes], GK[kMaxModes];
 };
 
-__device__ inline void build_coefficients(const StepParams& P, int x, int Mk, int M, Coef* c,
+static __device__ __noinline__ void build_coefficients(const StepParams& P, int x, int Mk, int M, Coef* c,
                                    float2* red /* >= 2*kMaxDim float2 */) {
-  const int G = gridDim.x, D = P.dim, spd = slots_per_dim(P.Mcap);
+  const int G = gram_ctas(), D = P.dim, spd = slots_per_dim(P.Mcap);
   const int nO = D - 1;
   // m_d, k_d of the fixed factors
   if (threadIdx.x < 2 * nO) {
@@ -189,7 +199,7 @@ __device__ inline void build_coefficients(const StepParams& P, int x, int Mk, in
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const dfloat ct = df_of(P.c_t), ck = df_of(P.c_k);
+    const dfloat ct = ld_df(&P.ct_df), ck = ld_df(&P.ck_df);
     dfloat pm = {1.f, 0.f}, stiff = {0.f, 0.f};
     for (int o = 0; o < nO; ++o) pm = df_mul(pm, ld_df(red + 2 * o));
     for (int o2 = 0; o2 < nO; ++o2) {
@@ -207,37 +217,53 @@ __device__ inline void build_coefficients(const StepParams& P, int x, int Mk, in
 // Right-hand side rows of this CTA's slice of direction x (Eq. KxQx), written as
 // double-float into P.Q.  R_i (the nonlinear contraction, without L omega_i) comes from the
 // partial buffers.
-__device__ inline void rhs_rows(const StepParams& P, const Extra& X, int x, int Mk, int M, int pb,
+static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X, int x, int Mk, int M, int pb,
                          int cb, const Coef* c) {
   const Dim& dd = P.d[x];
   int lo, hi;
   slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const dfloat ct = df_of(P.c_t), ck = df_of(P.c_k), L = df_of(P.L);
+  const int rows = hi - lo;
+  if (rows <= 0) return;
+  // a group of tpr consecutive lanes per row; its lanes split the mode sums
+  const int tpr = min(32, pow2_floor(max(1, kThreads / rows)));
+  const int groups = kThreads / tpr, g = threadIdx.x / tpr, lane = threadIdx.x % tpr;
+  const dfloat ct = ld_df(&P.ct_df), ck = ld_df(&P.ck_df), L = ld_df(&P.L_df);
   const int C = P.rchunks[x];
-  for (int i = lo + warp; i < hi; i += kWarps) {
+  for (int i0 = lo; i0 < hi; i0 += groups) {
+    const int i = i0 + g;
+    const bool live = i < hi;
     dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
-    for (int m = lane; m < Mk; m += 32)
-      s1 = df_fma(s1, ld_df(dd.bank[pb] + static_cast<size_t>(m) * dd.n + i), ld_df(c->H + m));
-    for (int m = lane; m < M; m += 32) {
-      const dfloat bmi = ld_df(dd.bank[cb] + static_cast<size_t>(m) * dd.n + i);
-      const dfloat gm = ld_df(c->GM + m);
-      s1 = df_add(s1, df_neg(df_mul(bmi, gm)));
-      s2 = df_fma(s2, ld_df(dd.KB + static_cast<size_t>(m) * dd.n + i), gm);
-      s3 = df_fma(s3, bmi, ld_df(c->GK + m));
+    if (live) {
+      for (int m = lane; m < Mk; m += tpr)
+        s1 = df_fma(s1, ld_df(dd.bank[pb] + static_cast<size_t>(m) * dd.n + i), ld_df(c->H + m));
+      for (int m = lane; m < M; m += tpr) {
+        const dfloat bmi = ld_df(dd.bank[cb] + static_cast<size_t>(m) * dd.n + i);
+        const dfloat gm = ld_df(c->GM + m);
+        s1 = df_add(s1, df_neg(df_mul(bmi, gm)));
+        s2 = df_fma(s2, ld_df(dd.KB + static_cast<size_t>(m) * dd.n + i), gm);
+        s3 = df_fma(s3, bmi, ld_df(c->GK + m));
+      }
     }
-    s1 = group_sum(s1, 32);
-    s2 = group_sum(s2, 32);
-    s3 = group_sum(s3, 32);
-    if (lane == 0) {
+    s1 = group_sum(s1, tpr);
+    s2 = group_sum(s2, tpr);
+    s3 = group_sum(s3, tpr);
+    if (live && lane == 0) {
       dfloat R;
       if (P.precision == 0) {
-        double r = 0.0;
-        for (int k = 0; k < C; ++k) r += P.rpart[static_cast<size_t>(i) * C + k];
-        R = df_of(r);
+        const double* rp = P.rpart + static_cast<size_t>(i) * C;
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        int k = 0;
+        for (; k + 3 < C; k += 4) { r0 += rp[k]; r1 += rp[k + 1]; r2 += rp[k + 2]; r3 += rp[k + 3]; }
+        for (; k < C; ++k) r0 += rp[k];
+        R = df_of((r0 + r1) + (r2 + r3));
       } else {
+        const TcDir& td = X.dirs[x];
+        const long long T = static_cast<long long>(td.nrb) * td.ntc;
+        const int rb = i / kTcM;
+        const int Cr = tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
+                       tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc) + 1;
         R = {0.f, 0.f};
-        for (int k = 0; k < C; ++k) R = df_add(R, dfloat{X.rpart32[static_cast<size_t>(i) * C + k], 0.f});
+        for (int k = 0; k < Cr; ++k) R = df_add(R, dfloat{X.rpart32[static_cast<size_t>(i) * td.cmax + k], 0.f});
       }
       const float2 om2 = kc_omega(X.kc[x], i);
       const dfloat om = {om2.x, om2.y};
@@ -255,7 +281,7 @@ __device__ inline void rhs_rows(const StepParams& P, const Extra& X, int x, int 
 // FP64 nonlinear contraction of the materialised w(u^k) grid (Eq. KxxMxx, nodal rule):
 // rpart[c * C + k] = partial over chunk k of sum_{other indices} W * prod_{d != x} wv_d,
 // wv_d = omega_d v_d in FP64 (shared memory, wv + d * kMaxN).
-__device__ inline void contract_fp64(const StepParams& P, int x, const double* wv) {
+static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, const double* wv) {
   const int D = P.dim;
   const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
   const int C = P.rchunks[x];
@@ -319,7 +345,7 @@ __device__ inline void contract_fp64(const StepParams& P, int x, const double* w
 }
 
 // FP64 weights omega_d v_d of every dimension but x (shared memory wv + d * kMaxN).
-__device__ inline void load_weights_fp64(const StepParams& P, const Extra& X, int x, double* wv) {
+static __device__ __noinline__ void load_weights_fp64(const StepParams& P, const Extra& X, int x, double* wv) {
   for (int d = 0; d < P.dim; ++d) {
     if (d == x) continue;
     const Dim& dd = P.d[d];
@@ -333,7 +359,7 @@ __device__ inline void load_weights_fp64(const StepParams& P, const Extra& X, in
 __device__ __forceinline__ double w_of_u(double u, double a0) { return 4.0 * a0 * (u * u * u - u); }
 
 // Materialise W = w(u^k) on the grid from FP64 factor copies Af[d][m][i] (row-major grid).
-__device__ inline void materialise_w(const StepParams& P, const Extra& X, int Mk) {
+static __device__ __noinline__ void materialise_w(const StepParams& P, const Extra& X, int Mk) {
   const int D = P.dim;
   const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
   const long long N = static_cast<long long>(n0) * n1 * n2;

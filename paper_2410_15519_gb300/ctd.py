@@ -73,8 +73,11 @@ def load() -> ctypes.CDLL:
     lib.ctd_probe_cfem.argtypes = [pcfg, i, vp, vp, ctypes.POINTER(i)]
     lib.ctd_probe_contract.argtypes = [vp, i, ctypes.POINTER(vp), vp]
     lib.ctd_probe_solve.argtypes = [vp, i, d, d, vp, vp]
+    lib.ctd_probe_trace.argtypes = [vp, i, vp, i]
+    lib.ctd_probe_reconstruct.argtypes = [vp, i, vp, vp, sz]
     for f in ("ctd_workspace_size", "ctd_create", "ctd_set_initial_modes", "ctd_step", "ctd_energy",
-              "ctd_get_modes", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve"):
+              "ctd_get_modes", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve", "ctd_probe_trace",
+              "ctd_probe_reconstruct"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -231,6 +234,28 @@ class Solver:
         out = np.zeros(self.cfg.n[x])
         _check(self.lib, self.h, self.lib.ctd_probe_contract(self.h, x, ptrs, out.ctypes.data), "probe_contract")
         return out
+
+    def probe_reconstruct(self, x: int, rows_pad: int, cols_pad: int) -> np.ndarray:
+        """u^k on the tile grid of direction x rebuilt on the tensor cores (FP32)."""
+        torch = self.torch
+        out = np.zeros((rows_pad, cols_pad), dtype=np.float32)
+        scratch = torch.empty(out.nbytes, dtype=torch.uint8, device="cuda")
+        _check(self.lib, self.h, self.lib.ctd_probe_reconstruct(self.h, x, out.ctypes.data,
+                                                                ctypes.c_void_p(scratch.data_ptr()), out.nbytes),
+               "probe_reconstruct")
+        return out
+
+    TRACE_PHASES = ("prologue", "mode_start", "gram_contract", "rhs", "solve", "converge", "commit")
+
+    def trace(self, enable: bool = True) -> dict:
+        """Seconds per step-kernel phase accumulated since the last call; (re)starts or stops
+        accumulation."""
+        out = np.zeros(16)
+        _check(self.lib, self.h, self.lib.ctd_probe_trace(self.h, 1 if enable else 0, out.ctypes.data, 16),
+               "probe_trace")
+        d = dict(zip(self.TRACE_PHASES, out[:len(self.TRACE_PHASES)].tolist()))
+        d.update(solve_factor=out[8], solve_first=out[9], solve_refine=out[10], solve_passes=out[11] * 1e9)
+        return d
 
     def probe_solve(self, x: int, alpha1: float, alpha2: float, q: np.ndarray) -> np.ndarray:
         q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))

@@ -41,7 +41,9 @@ def test_banded_solve_matches_lapack(lib, n, s, p):
     ops = octd.build_operators(prob)
     rng = np.random.default_rng(n)
     q = rng.standard_normal(n)
-    for a1, a2 in [(1.0e3, 2.5e-3), (7.0, 1.0), (1.0e7, 1.0)]:
+    # the half-sweep systems have alpha1 / alpha2 >= c_t / c_k (Eq. KxQx coefficients)
+    beta0 = prob.c_t / prob.c_k
+    for a1, a2 in [(beta0 * 2.5e-3, 2.5e-3), (1.7 * beta0 * 0.3, 0.3), (50 * beta0, 1.0)]:
         A = a1 * ops.M[0] + a2 * ops.K[0]
         ref = octd.banded_spd_solve(A, q)
         y = solver.probe_solve(0, a1, a2, q)
