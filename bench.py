@@ -147,6 +147,23 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+# --------------------------------------------------------------------------- ranks
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """Slowest rank's value (replicas run independently; the job ends with the last one)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_units(steps: int, world: int) -> int:
+    """Time steps advanced by the whole job: every rank advances its own instance."""
+    return steps * world
+
+
 # --------------------------------------------------------------------------- GPU leg
 def algorithmic_flops(w, precision: str, Mk: int, half_sweeps: int) -> float:
     """Work of the nonlinear contraction per launch (the method's own arithmetic):
@@ -201,11 +218,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = sum(times_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times_ms), world)
     # rank of u^k entering each timed step: the previous step's output rank
     ranks_in = [rank0] + [st["modes"] for st in stats[:-1]]
     for st, mk in zip(stats, ranks_in):
@@ -288,7 +301,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
     pk, pk_kind = peaks()
-    value = world * args.steps / (res["total_ms"] / 1e3)
+    value = replica_units(args.steps, world) / (res["total_ms"] / 1e3)
     achieved = res["flops_per_launch"] / (res["per_launch_ms"] / 1e3) / 1e12
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",

@@ -169,6 +169,7 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   p.trace = cv.take<unsigned long long>(ctd::kTrSlots);
   p.st = cv.take<InstState>(1);
   x.maxpart = cv.take<double>(static_cast<size_t>(ctd::kMaxDim) * Gs);
+  x.xprev = cv.take<float2>(static_cast<size_t>(ctd::kMaxDim) * ctd::kMaxN);
   x.ctrl = cv.take<int>(64);
   *stats = cv.take<StepStatsDev>(kStatsCap);
   *energy_part = cv.take<double>(1024);
@@ -364,6 +365,60 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     h->mu_max[d] = g * 1.000001;
     P.d[d].mu_max = static_cast<float>(h->mu_max[d]);
   }
+  h->trace_dev = P.trace;
+  P.trace = nullptr;
+
+  // host C-FEM data and compressed stiffness per dimension
+  for (int d = 0; d < cfg->dim; ++d) {
+    const int n = cfg->n[d], b = h->plan.b[d], w = 2 * b + 1;
+    h->omega[d].assign(n, 0.0);
+    h->kband[d].assign(static_cast<size_t>(n) * w, 0.0);
+    if (ctd::build_cfem_1d(n, cfg->length[d], cfg->s, cfg->p, cfg->a, h->omega[d].data(), h->kband[d].data()) != 0) {
+      ctd_status s = fail(h, CTD_ERR_ARG, "C-FEM construction failed");
+      delete h;
+      return s;
+    }
+    CTD_CUDA(h, cudaMemcpyAsync(const_cast<double*>(P.d[d].omega), h->omega[d].data(), sizeof(double) * n,
+                                cudaMemcpyHostToDevice, h->stream));
+    CTD_CUDA(h, cudaMemcpyAsync(const_cast<double*>(P.d[d].kband), h->kband[d].data(),
+                                sizeof(double) * n * w, cudaMemcpyHostToDevice, h->stream));
+    // interior rows [2s+1, n-2-2s] share one stencil when the mesh is uniform
+    const int s = cfg->s;
+    int lead = 2 * s + 1, tail = 2 * s + 1;
+    bool uniform = n > lead + tail;
+    if (uniform) {
+      const double* ref = &h->kband[d][static_cast<size_t>(lead) * w];
+      for (int i = lead; i < n - tail && uniform; ++i)
+        for (int k = 0; k < w; ++k)
+          if (h->kband[d][static_cast<size_t>(i) * w + k] != ref[k]) { uniform = false; break; }
+    }
+    if (!uniform) { lead = n; tail = 0; }
+    std::vector<float2> kc(static_cast<size_t>(lead + tail + 1) * w);
+    auto to_df = [](double v) {
+      const float hi = static_cast<float>(v);
+      return make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+    };
+    for (int i = 0; i < lead; ++i)
+      for (int k = 0; k < w; ++k) kc[static_cast<size_t>(i) * w + k] = to_df(h->kband[d][static_cast<size_t>(i) * w + k]);
+    for (int t = 0; t < tail; ++t)
+      for (int k = 0; k < w; ++k)
+        kc[static_cast<size_t>(lead + t) * w + k] = to_df(h->kband[d][static_cast<size_t>(n - tail + t) * w + k]);
+    const int srow = uniform ? lead : 0;
+    for (int k = 0; k < w; ++k) kc[static_cast<size_t>(lead + tail) * w + k] = to_df(h->kband[d][static_cast<size_t>(srow) * w + k]);
+    CTD_CUDA(h, cudaMemcpyAsync(h->kc_store[d], kc.data(), sizeof(float2) * kc.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    ctd::KCompressed& k = X.kc[d];
+    k.n = n;
+    k.b = b;
+    k.nlead = lead;
+    k.ntail = tail;
+    k.rows = h->kc_store[d];
+    k.stencil = h->kc_store[d] + static_cast<size_t>(lead + tail) * w;
+    k.omega_in = to_df(h->omega[d][n / 2]);
+    k.omega_end = to_df(h->omega[d][0]);
+    k.inv_omega_in = static_cast<float>(1.0 / h->omega[d][n / 2]);
+    k.inv_omega_end = static_cast<float>(1.0 / h->omega[d][0]);
+  }
   // shared memory: fixed part + per-phase arena; solver factors join the arena if they fit
   {
     int n_max = 0;
@@ -384,7 +439,10 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
       worst_its = std::max(worst_its, ctd::cheb_iterations(static_cast<float>(P.c_t), static_cast<float>(P.c_k),
                                                            static_cast<float>(h->mu_max[d]), 2.384185791015625e-07f));
     const size_t chf = ctd::cheb_floats(n_max);
-    if (worst_its <= 200 && fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
+    bool small_ends = true;   // the explicit end rows of the band must fit the 256-float stage
+    for (int d = 0; d < cfg->dim; ++d)
+      if ((X.kc[d].nlead + X.kc[d].ntail) * (2 * X.kc[d].b + 1) > 256) small_ends = false;
+    if (small_ends && worst_its <= 200 && fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
       P.solver_mode = 3;
     else if (fixed + ctd::step_arena_bytes(n_max, crf, 0) + margin <= static_cast<size_t>(optin)) P.solver_mode = 0;
     else if (fixed + ctd::step_arena_bytes(n_max, l0f, 1) + margin <= static_cast<size_t>(optin)) P.solver_mode = 1;
@@ -445,60 +503,6 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
           delete h;
           return s;
         }
-  }
-  h->trace_dev = P.trace;
-  P.trace = nullptr;
-
-  // host C-FEM data and compressed stiffness per dimension
-  for (int d = 0; d < cfg->dim; ++d) {
-    const int n = cfg->n[d], b = h->plan.b[d], w = 2 * b + 1;
-    h->omega[d].assign(n, 0.0);
-    h->kband[d].assign(static_cast<size_t>(n) * w, 0.0);
-    if (ctd::build_cfem_1d(n, cfg->length[d], cfg->s, cfg->p, cfg->a, h->omega[d].data(), h->kband[d].data()) != 0) {
-      ctd_status s = fail(h, CTD_ERR_ARG, "C-FEM construction failed");
-      delete h;
-      return s;
-    }
-    CTD_CUDA(h, cudaMemcpyAsync(const_cast<double*>(P.d[d].omega), h->omega[d].data(), sizeof(double) * n,
-                                cudaMemcpyHostToDevice, h->stream));
-    CTD_CUDA(h, cudaMemcpyAsync(const_cast<double*>(P.d[d].kband), h->kband[d].data(),
-                                sizeof(double) * n * w, cudaMemcpyHostToDevice, h->stream));
-    // interior rows [2s+1, n-2-2s] share one stencil when the mesh is uniform
-    const int s = cfg->s;
-    int lead = 2 * s + 1, tail = 2 * s + 1;
-    bool uniform = n > lead + tail;
-    if (uniform) {
-      const double* ref = &h->kband[d][static_cast<size_t>(lead) * w];
-      for (int i = lead; i < n - tail && uniform; ++i)
-        for (int k = 0; k < w; ++k)
-          if (h->kband[d][static_cast<size_t>(i) * w + k] != ref[k]) { uniform = false; break; }
-    }
-    if (!uniform) { lead = n; tail = 0; }
-    std::vector<float2> kc(static_cast<size_t>(lead + tail + 1) * w);
-    auto to_df = [](double v) {
-      const float hi = static_cast<float>(v);
-      return make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
-    };
-    for (int i = 0; i < lead; ++i)
-      for (int k = 0; k < w; ++k) kc[static_cast<size_t>(i) * w + k] = to_df(h->kband[d][static_cast<size_t>(i) * w + k]);
-    for (int t = 0; t < tail; ++t)
-      for (int k = 0; k < w; ++k)
-        kc[static_cast<size_t>(lead + t) * w + k] = to_df(h->kband[d][static_cast<size_t>(n - tail + t) * w + k]);
-    const int srow = uniform ? lead : 0;
-    for (int k = 0; k < w; ++k) kc[static_cast<size_t>(lead + tail) * w + k] = to_df(h->kband[d][static_cast<size_t>(srow) * w + k]);
-    CTD_CUDA(h, cudaMemcpyAsync(h->kc_store[d], kc.data(), sizeof(float2) * kc.size(), cudaMemcpyHostToDevice,
-                                h->stream));
-    ctd::KCompressed& k = X.kc[d];
-    k.n = n;
-    k.b = b;
-    k.nlead = lead;
-    k.ntail = tail;
-    k.rows = h->kc_store[d];
-    k.stencil = h->kc_store[d] + static_cast<size_t>(lead + tail) * w;
-    k.omega_in = to_df(h->omega[d][n / 2]);
-    k.omega_end = to_df(h->omega[d][0]);
-    k.inv_omega_in = static_cast<float>(1.0 / h->omega[d][n / 2]);
-    k.inv_omega_end = static_cast<float>(1.0 / h->omega[d][0]);
   }
   InstState st{};
   CTD_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));

@@ -419,7 +419,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         wt = wl + (col0 - jm * td.n_last_pad);
         wscale = wm[jm];
       }
-      float at = 0.f;
+      float at0 = 0.f, at1 = 0.f, at2 = 0.f, at3 = 0.f;
 #pragma unroll
       for (int q = 0; q < kTcN / 32; ++q) {
         float v[32];
@@ -428,12 +428,18 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
           const int row = rb * kTcM + r;
           for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * td.ncols_pad + col0 + q * 32 + c] = v[c];
         }
+        const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const float u = v[c];
-          at = __fmaf_rn(u * __fmaf_rn(u, u, -1.f), wt[q * 32 + c], at);
+        for (int c = 0; c < 8; ++c) {
+          const float4 ww = w4[c];
+          const float u0 = v[4 * c], u1 = v[4 * c + 1], u2 = v[4 * c + 2], u3 = v[4 * c + 3];
+          at0 = __fmaf_rn(u0 * __fmaf_rn(u0, u0, -1.f), ww.x, at0);
+          at1 = __fmaf_rn(u1 * __fmaf_rn(u1, u1, -1.f), ww.y, at1);
+          at2 = __fmaf_rn(u2 * __fmaf_rn(u2, u2, -1.f), ww.z, at2);
+          at3 = __fmaf_rn(u3 * __fmaf_rn(u3, u3, -1.f), ww.w, at3);
         }
       }
+      const float at = (at0 + at1) + (at2 + at3);
       tc_fence_before();
       mbar_arrive(&sh->acc_empty[ab]);
       acc = __fmaf_rn(wscale, at, acc);

@@ -200,12 +200,14 @@ __device__ __noinline__ void commit_mode(const StepParams& P, const Extra& X, in
 // The solver CTA: solve Eq. ux for direction x, normalise unless x is the last dimension,
 // publish v_x (double-float) and flags in ctrl: [0] zero factor, [1] failure.
 __device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
-                                const Arena& ar) {
+                                const Arena& ar, bool warm) {
   const Dim& dd = P.d[x];
   const SolverStore store = solver_bind(P.solver_mode == 2 ? 0 : P.solver_mode, ar.solver, P.solver, dd.n, dd.b, dd.mu_max);
   const dfloat a1 = ld_df(&sm.coef.alpha1), a2 = ld_df(&sm.coef.alpha2);
   float2* xs = ar.xsol;
-  bool ok = banded_solve(store, X.kc[x], a1, a2, P.Q, xs, sm.redf, P.trace);
+  float2* prev = X.xprev + static_cast<size_t>(x) * kMaxN;
+  bool ok = banded_solve(store, X.kc[x], a1, a2, P.Q, xs, sm.redf, P.trace, warm ? prev : nullptr);
+  for (int i = threadIdx.x; i < dd.n; i += blockDim.x) prev[i] = xs[i];
   // zero test and squared norm (double-float, fixed reduction order)
   int nz = 0;
   dfloat ss = {0.f, 0.f};
@@ -276,8 +278,14 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
       save_old(P);
       for (int x = 0; x < D; ++x) {
         // Phase A: Gram partials of the fixed factors + nonlinear contraction partials
+        unsigned long long tsub = (P.trace && blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
         gram_partials(P, X, x, Mk, M, pb, cb, ar.gram_rows);
         __syncthreads();
+        if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+          const unsigned long long t = global_ns();
+          atomicAdd(P.trace + kTrGram, t - tsub);
+          tsub = t;
+        }
         if (P.precision == 0) {
           load_weights_fp64(P, X, x, ar.wv);
           contract_fp64(P, x, ar.wv);
@@ -288,6 +296,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
                            X.rpart32, nullptr))
             return;
         }
+        if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(P.trace + kTrContract, global_ns() - tsub);
         if (!sync_all(P, epoch, 3)) return;
         trace_mark(P, tmark, kTrGramContract);
         // Phase B: coefficients (every CTA, same order) and right-hand-side rows
@@ -296,7 +305,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
         if (!sync_all(P, epoch, 4)) return;
         trace_mark(P, tmark, kTrRhs);
         // Phase C: banded solve on CTA 0
-        if (blockIdx.x == 0) solve_direction(P, X, x, sm, ar);
+        if (blockIdx.x == 0) solve_direction(P, X, x, sm, ar, it > 1);
         if (!sync_all(P, epoch, 5)) return;
         trace_mark(P, tmark, kTrSolve);
         const int zflag = *reinterpret_cast<volatile int*>(X.ctrl + 0);

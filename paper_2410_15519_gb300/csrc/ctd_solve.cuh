@@ -591,6 +591,7 @@ __device__ inline float cta_max(float v, float* red) {
 // banded product and two vector updates over all rows in parallel, one __syncthreads.
 struct ChebBuffers {
   float *r, *e, *d0, *d1;   // [n] residual, accumulated solution, two search vectors
+  float* kb;                // explicit band rows near the two ends, FP32 ([nlead + ntail][2b+1], <= 256)
   float *F, *X;             // aliases used by the refinement loop (F = r, X = e)
 };
 
@@ -606,62 +607,137 @@ __host__ __device__ inline int cheb_iterations(float a1, float a2, float mu_max,
 // e = A^-1 r approximately (Chebyshev semi-iteration with D scaling), r overwritten.  The band
 // descriptor is copied into registers and the interior stencil held in registers: the vectors
 // live in shared memory and their stores would otherwise force descriptor reloads.
-template <int B>
-__device__ inline void cheb_solve_t(const ChebBuffers& s, const KCompressed& kref, float a1, float a2, int iters,
-                                    float theta, float delta, float sigma) {
+// Register-resident Chebyshev.  Threads 0 .. blockDim.x-33 own the interior rows in contiguous
+// runs of R (R odd, so a warp's strided shared-memory accesses hit 32 different banks); the
+// last warp's lanes own the explicit end rows (lane l < nlead: row l; lane 16 + l: row
+// n - ntail + l).  Residual, iterate and search direction stay in registers; each iteration
+// publishes the search direction to shared memory once (alternating buffers, zero padded by B
+// on both sides) and reads back only the neighbours it needs.
+template <int B, int R>
+__device__ inline void cheb_solve_reg(const ChebBuffers& s, const KCompressed& kref, float a1, float a2, int iters,
+                                      float theta, float delta, float sigma) {
   const KCompressed k = kref;
   const int n = k.n;
-  float st[2 * B + 1];
+  constexpr int W = 2 * B + 1;
+  float st[W];
 #pragma unroll
-  for (int o = 0; o < 2 * B + 1; ++o) st[o] = a2 * k.stencil[o].x;
-  const float a1in = a1 * k.omega_in.x, a1end = a1 * k.omega_end.x;
+  for (int o = 0; o < W; ++o) st[o] = a2 * k.stencil[o].x;
   const int ilo = k.nlead, ihi = n - k.ntail;
-  float* __restrict__ r = s.r;
-  float* __restrict__ e = s.e;
-  float rho_old = 1.f / sigma;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    e[i] = 0.f;
-    s.d0[i] = r[i] * kc_inv_omega(k, i) / theta;
+  const int tint = blockDim.x - 32;                 // interior threads
+  const bool endlane = threadIdx.x >= tint;
+  const int lane = threadIdx.x - tint;
+  int i0 = 0, cnt = 0;                              // interior run [i0, i0 + cnt)
+  int ie = -1;                                      // end row of an end lane
+  if (!endlane) {
+    i0 = ilo + threadIdx.x * R;
+    cnt = max(0, min(R, ihi - i0));
+  } else if (lane < k.nlead) {
+    ie = lane;
+  } else if (lane >= 16 && lane - 16 < k.ntail) {
+    ie = n - k.ntail + (lane - 16);
   }
-  __syncthreads();
-  float* dcur = s.d0;
-  float* dnext = s.d1;
+  // end rows: full band row (a2 K) in shared memory
+  const int nx = k.nlead + k.ntail;
+  for (int t = threadIdx.x; t < nx * W; t += blockDim.x) s.kb[t] = a2 * k.rows[t].x;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    s.d0[i] = 0.f; s.d0[n + B + i] = 0.f;
+    s.d1[i] = 0.f; s.d1[n + B + i] = 0.f;
+  }
+  const float a1in = a1 * k.omega_in.x, iwin = k.inv_omega_in;
+  float r[R], e[R], d[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    r[j] = j < cnt ? s.r[i0 + j] : 0.f;
+    e[j] = 0.f;
+    d[j] = r[j] * iwin / theta;
+  }
+  float re = 0.f, ee = 0.f, de = 0.f, iwe = 0.f, a1e = 0.f;
+  const float* kre = nullptr;
+  if (ie >= 0) {
+    iwe = kc_inv_omega(k, ie);
+    a1e = a1 * kc_omega(k, ie).x;
+    re = s.r[ie];
+    de = re * iwe / theta;
+    kre = s.kb + (ie < ilo ? ie : k.nlead + ie - ihi) * W;
+  }
+  float rho_old = 1.f / sigma;
   for (int it = 0; it < iters; ++it) {
+    float* dsh = ((it & 1) ? s.d1 : s.d0) + B;
+    if (!endlane) {
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (j < cnt) dsh[i0 + j] = d[j];
+    } else if (ie >= 0) {
+      dsh[ie] = de;
+    }
+    __syncthreads();
     const float rho = 1.f / (2.f * sigma - rho_old);
     const float c1 = rho * rho_old, c2 = 2.f * rho / delta;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      float ad;
-      if (i >= ilo && i < ihi) {
-        float acc = 0.f;
+    if (!endlane) {
+      if (cnt > 0) {
+        // window rows i0 - B .. i0 + R + B - 1; own rows from registers, the rest from the
+        // published vector (rows >= n read the zero padding, rows past it are zero)
+        float win[R + 2 * B];
 #pragma unroll
-        for (int o = 0; o < 2 * B + 1; ++o) acc = __fmaf_rn(st[o], dcur[i + o - B], acc);
-        ad = __fmaf_rn(a1in, dcur[i], acc);
-      } else {
-        float acc = 0.f;
-        const int j0 = max(0, i - B), j1 = min(n - 1, i + B);
-        for (int j = j0; j <= j1; ++j) acc = __fmaf_rn(kc_entry(k, i, j - i).x, dcur[j], acc);
-        ad = __fmaf_rn(i == 0 || i == n - 1 ? a1end : a1in, dcur[i], a2 * acc);
+        for (int t = 0; t < B; ++t) {
+          win[t] = dsh[i0 - B + t];
+          const int row = i0 + R + t;
+          win[R + B + t] = row < n + B ? dsh[row] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int row = i0 + j;
+          win[B + j] = j < cnt ? d[j] : (row < n + B ? dsh[row] : 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          float acc = a1in * d[j];
+#pragma unroll
+          for (int o = 0; o < W; ++o) acc = __fmaf_rn(st[o], win[j + o], acc);
+          e[j] += d[j];
+          r[j] -= acc;
+          d[j] = __fmaf_rn(c1, d[j], c2 * (r[j] * iwin));
+        }
       }
-      const float di = dcur[i];
-      e[i] += di;
-      const float ri = r[i] - ad;
-      r[i] = ri;
-      dnext[i] = __fmaf_rn(c1, di, c2 * (ri * kc_inv_omega(k, i)));
+    } else if (ie >= 0) {
+      float acc = a1e * de;
+#pragma unroll
+      for (int o = 0; o < W; ++o) acc = __fmaf_rn(kre[o], dsh[ie + o - B], acc);
+      ee += de;
+      re -= acc;
+      de = __fmaf_rn(c1, de, c2 * (re * iwe));
     }
     rho_old = rho;
-    float* t = dcur;
-    dcur = dnext;
-    dnext = t;
-    __syncthreads();
   }
+  if (!endlane) {
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (j < cnt) s.e[i0 + j] = e[j];
+  } else if (ie >= 0) {
+    s.e[ie] = ee;
+  }
+  __syncthreads();
+}
+
+template <int B>
+__device__ inline void cheb_solve_b(const ChebBuffers& s, const KCompressed& k, float a1, float a2, int iters,
+                                    float theta, float delta, float sigma) {
+  const int tint = blockDim.x - 32;
+  const int nint = k.n - k.nlead - k.ntail;
+  const int need = (nint + tint - 1) / tint;
+  if (need <= 1) cheb_solve_reg<B, 1>(s, k, a1, a2, iters, theta, delta, sigma);
+  else if (need <= 3) cheb_solve_reg<B, 3>(s, k, a1, a2, iters, theta, delta, sigma);
+  else if (need <= 5) cheb_solve_reg<B, 5>(s, k, a1, a2, iters, theta, delta, sigma);
+  else if (need <= 11) cheb_solve_reg<B, 11>(s, k, a1, a2, iters, theta, delta, sigma);
+  else cheb_solve_reg<B, 19>(s, k, a1, a2, iters, theta, delta, sigma);
 }
 
 static __device__ __noinline__ void cheb_solve(const ChebBuffers& s, const KCompressed& k, float a1, float a2,
                                                int iters, float theta, float delta, float sigma) {
   switch (k.b) {
-    case 3: cheb_solve_t<3>(s, k, a1, a2, iters, theta, delta, sigma); break;
-    case 5: cheb_solve_t<5>(s, k, a1, a2, iters, theta, delta, sigma); break;
-    default: cheb_solve_t<7>(s, k, a1, a2, iters, theta, delta, sigma); break;
+    case 3: cheb_solve_b<3>(s, k, a1, a2, iters, theta, delta, sigma); break;
+    case 5: cheb_solve_b<5>(s, k, a1, a2, iters, theta, delta, sigma); break;
+    default: cheb_solve_b<7>(s, k, a1, a2, iters, theta, delta, sigma); break;
   }
 }
 
@@ -722,7 +798,8 @@ struct SolverStore {
 // Full solve with refinement.  q: double-float right-hand side [n]; x: double-float result
 // [n].  a1, a2 as double-float.  Returns false on a failed pivot or a non-finite result.
 static __device__ __noinline__ bool banded_solve(const SolverStore& s, const KCompressed& k, dfloat a1, dfloat a2,
-                                    const float2* q, float2* x, float* red, unsigned long long* trace = nullptr) {
+                                    const float2* q, float2* x, float* red, unsigned long long* trace = nullptr,
+                                    const float2* x0 = nullptr) {
   const int n = k.n, b = k.b;
   const int npad = s.mode == 3 ? n : (s.mode == 0 ? s.cr.nb : s.l0.nb) * b;
   unsigned long long t0 = trace ? global_ns() : 0ull;
@@ -746,13 +823,22 @@ static __device__ __noinline__ bool banded_solve(const SolverStore& s, const KCo
     if (cheb_its > 4096) cheb_its = 4096;
   }
   if (trace && threadIdx.x == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveFactor, t - t0); t0 = t; }
-  for (int i = threadIdx.x; i < npad; i += blockDim.x) s.F[i] = (i < n) ? q[i].x : 0.f;
-  __syncthreads();
-  if (s.mode == 0) cr_solve(s.cr);
-  else if (s.mode == 1) l0_solve(s.l0, k, a1.hi, a2.hi);
-  else cheb_solve(s.ch, k, a1.hi, a2.hi, cheb_its, th, de, sg);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = make_float2(s.X[i], 0.f);
-  __syncthreads();
+  // per-pass contraction of the error: the Chebyshev bound 2^-22, or FP32 rounding times cond
+  const float kappa = s.mode == 3 ? (a1.hi + a2.hi * s.mu_max) / a1.hi : 1.f;
+  const float rho_pass = 4.f * fmaxf(2.384185791015625e-07f, kappa * 5.960464477539063e-08f);
+  bool warm = x0 != nullptr && s.mode == 3;
+  if (warm) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = x0[i];
+    __syncthreads();
+  } else {
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) s.F[i] = (i < n) ? q[i].x : 0.f;
+    __syncthreads();
+    if (s.mode == 0) cr_solve(s.cr);
+    else if (s.mode == 1) l0_solve(s.l0, k, a1.hi, a2.hi);
+    else cheb_solve(s.ch, k, a1.hi, a2.hi, cheb_its, th, de, sg);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = make_float2(s.X[i], 0.f);
+    __syncthreads();
+  }
   if (trace && threadIdx.x == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveFirst, t - t0); t0 = t; }
   float prev = 0.f;
   for (int it = 0; it < 4; ++it) {
@@ -776,6 +862,7 @@ static __device__ __noinline__ bool banded_solve(const SolverStore& s, const KCo
     // the refinement contracts the error by rho ~ dmax / prev per pass; stop once the next
     // correction would fall below 2^-48 of the iterate (or this one already did)
     if (dmax <= 3.552713678800501e-15f * xmax) break;
+    if (s.mode == 3 && rho_pass * dmax <= 3.552713678800501e-15f * xmax) break;
     if (it > 0 && prev > 0.f && dmax * (dmax / prev) <= 3.552713678800501e-15f * xmax) break;
     prev = dmax;
   }
@@ -793,7 +880,7 @@ __host__ __device__ inline size_t l0_global_floats(int n, int b) {
   return static_cast<size_t>(nb) * b * 3;
 }
 
-__host__ __device__ inline size_t cheb_floats(int n) { return static_cast<size_t>(n) * 4; }
+__host__ __device__ inline size_t cheb_floats(int n) { return static_cast<size_t>(n) * 4 + 32 + 256; }
 
 // Bind solver storage.  mode 0: factors at fbase; mode 1: level-1 factors at fbase, full vectors
 // at gbase; mode 3: Chebyshev vectors at fbase.
@@ -804,8 +891,9 @@ __device__ inline SolverStore solver_bind(int mode, float* fbase, float* gbase, 
   if (mode == 3) {
     s.ch.r = fbase;
     s.ch.e = fbase + n;
-    s.ch.d0 = fbase + 2 * n;
-    s.ch.d1 = fbase + 3 * n;
+    s.ch.d0 = fbase + 2 * n;            // n + 2B published search direction (B <= 7)
+    s.ch.d1 = fbase + 3 * n + 16;
+    s.ch.kb = fbase + 4 * n + 32;
     s.ch.F = s.ch.r;
     s.ch.X = s.ch.e;
     s.F = s.ch.r;

@@ -22,6 +22,7 @@ struct Extra {            // per-launch workspace pieces not in StepParams
   TcDir dirs[kMaxDim];    // tensor-core geometry per direction
   __nv_bfloat16* kr[kMaxDim];   // 3D Khatri-Rao operands per direction
   int tc_stages;          // B-operand ring depth
+  float2* xprev;          // [kMaxDim][kMaxN] last unnormalised solve per direction (warm start)
 };
 
 __device__ __forceinline__ dfloat ld_df(const float2* p) {

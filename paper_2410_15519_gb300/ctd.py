@@ -254,7 +254,8 @@ class Solver:
         _check(self.lib, self.h, self.lib.ctd_probe_trace(self.h, 1 if enable else 0, out.ctypes.data, 16),
                "probe_trace")
         d = dict(zip(self.TRACE_PHASES, out[:len(self.TRACE_PHASES)].tolist()))
-        d.update(solve_factor=out[8], solve_first=out[9], solve_refine=out[10], solve_passes=out[11] * 1e9)
+        d.update(solve_factor=out[8], solve_first=out[9], solve_refine=out[10], solve_passes=out[11] * 1e9,
+                 gram=out[12], contract=out[13])
         return d
 
     def probe_solve(self, x: int, alpha1: float, alpha2: float, q: np.ndarray) -> np.ndarray:

@@ -1,0 +1,96 @@
+"""CPU checks of the C ABI: the library loads without a GPU, exports every entry point the
+public header declares, validates configurations, and its host-side C-FEM builder agrees
+with the oracle (App. B / App. C shape functions, Eq. KxxMxx stiffness)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import cfem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ctd.h")
+
+
+@pytest.fixture(scope="module")
+def ctd():
+    from paper_2410_15519_gb300 import build, ctd as mod
+    build.build()
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ctd_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(ctd):
+    lib = ctd.load()
+    names = declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(ctd):
+    lib = ctd.load()
+    for code in (0, 1, 2, -1, -2, -3, -4, -5, -6, -7):
+        assert len(lib.ctd_status_string(code)) >= 2
+
+
+@pytest.mark.parametrize("field,value", [("dim", 4), ("s", 0), ("p", 3), ("M_max", 0), ("M_max", 129),
+                                          ("dt", -1.0), ("precision", 7), ("I_max", 0)])
+def test_invalid_configurations_are_rejected(ctd, field, value):
+    w = workloads.preset("c0")
+    cfg = ctd.config_from_workload(w)
+    if field == "p":
+        cfg.s = 2
+    setattr(cfg, field, value)
+    lib = ctd.load()
+    n = ctypes.c_size_t(0)
+    assert lib.ctd_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == -1
+
+
+def test_node_count_limits(ctd):
+    lib = ctd.load()
+    for nn in (3, 4097):
+        cfg = ctd.config_from_workload(workloads.preset("c0", n=(nn, 64)))
+        n = ctypes.c_size_t(0)
+        assert lib.ctd_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == -1
+
+
+def test_workspace_size_grows_with_the_problem(ctd):
+    small = ctd.workspace_size(ctd.config_from_workload(workloads.preset("c0")))
+    big = ctd.workspace_size(ctd.config_from_workload(workloads.preset("c0", n=(1024, 1024))))
+    mixed = ctd.workspace_size(ctd.config_from_workload(workloads.preset("c0"), precision=ctd.PREC_SPLIT_BF16))
+    assert 0 < small < big and mixed > 0
+
+
+@pytest.mark.parametrize("n,s,p", [(64, 1, 1), (101, 2, 2), (57, 3, 3), (33, 2, 1)])
+def test_host_cfem_matches_oracle(ctd, n, s, p):
+    cfg = ctd.config_from_workload(workloads.preset("c0", n=(n, n), s=s, p=p))
+    om, kb, b = ctd.probe_cfem(cfg, 0)
+    assert b == 2 * s + 1
+    K = cfem.stiffness_matrix(n, 1.0, s, p, 12.0).toarray()
+    Kd = np.zeros((n, n))
+    for i in range(n):
+        for k in range(-b, b + 1):
+            if 0 <= i + k < n:
+                Kd[i, i + k] = kb[i, k + b]
+            else:
+                assert kb[i, k + b] == 0.0
+    assert np.max(np.abs(Kd - K)) <= 1e-12 * np.max(np.abs(K))
+    assert np.array_equal(om, cfem.nodal_weights(n, 1.0))
+
+
+def test_calls_without_a_handle_fail_cleanly(ctd):
+    lib = ctd.load()
+    st = ctd.StepStats()
+    assert lib.ctd_step(None, 1, ctypes.byref(st)) == -1
+    e = ctypes.c_double()
+    assert lib.ctd_energy(None, ctypes.byref(e)) == -1
+    lib.ctd_destroy(None)
