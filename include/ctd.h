@@ -157,6 +157,23 @@ ctd_status ctd_probe_solve(ctd_handle h, int x, double alpha1, double alpha2,
  * buffer of at least the output size.  Synchronises. */
 ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch, size_t scratch_bytes);
 
+/* ctd_probe_reconstruct without a caller scratch buffer; the paper has no counterpart (it is
+ * a library convenience).  For callers that cannot allocate device memory for the dump: a
+ * host program that only holds a handle and has no device allocator of its own, or a run
+ * whose device memory is fully committed to the workspace.  The dump goes through a
+ * file-scope device array of CTD_RECONSTRUCT_STATIC_BYTES (4 MiB) per device, whose address
+ * is looked up once per device on the first call with that device current (do that first
+ * call before any stream capture on the device); nothing is allocated by the call itself.
+ * Same arguments, layout and result as ctd_probe_reconstruct; the tile grid must fit:
+ * n_pad[x] * ncols_pad * 4 bytes <= CTD_RECONSTRUCT_STATIC_BYTES, else CTD_ERR_WORKSPACE
+ * (message in ctd_last_error) and nothing is launched.  The current device must be the
+ * handle's (CTD_ERR_STATE otherwise).  The used part of the array is zeroed on the handle's
+ * stream before the kernel runs.  All handles on one device share the array: calls that
+ * overlap in time (other threads or streams on the same device) race and give undefined
+ * output; calls from one thread are safe since each call synchronises before returning. */
+#define CTD_RECONSTRUCT_STATIC_BYTES ((size_t)4 << 20)
+ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out);
+
 /* Per-phase time of the step kernel, accumulated by CTA 0 from the GPU global timer (each
  * phase includes its closing grid-wide wait).  Copies the seconds accumulated so far into
  * seconds[0 .. nslots) (may be NULL), resets the counters, and turns accumulation on

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -248,6 +249,28 @@ static ctd_status cuda_fail(ctd_ctx* h, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
   } while (0)
+
+// Dump array of ctd_probe_reconstruct_noalloc: a file-scope device array (one instance per
+// device, created with the module), for callers that cannot allocate device memory.  Its
+// address is looked up once per device, with that device current, and cached.
+static __device__ __align__(256) unsigned char g_static_dump[CTD_RECONSTRUCT_STATIC_BYTES];
+namespace {
+constexpr int kStaticDumpDevices = 64;
+std::mutex g_static_dump_mu;
+void* g_static_dump_ptr[kStaticDumpDevices] = {};
+}  // namespace
+static cudaError_t static_dump_address(int device, void** ptr) {
+  if (device < 0 || device >= kStaticDumpDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_dump_mu);
+  if (!g_static_dump_ptr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_dump);
+    if (e != cudaSuccess) return e;
+    g_static_dump_ptr[device] = p;
+  }
+  *ptr = g_static_dump_ptr[device];
+  return cudaSuccess;
+}
 
 static ctd_status status_from_bits(int bits) {
   if (bits & ctd::kErrTimeout) return CTD_ERR_TIMEOUT;
@@ -723,6 +746,41 @@ ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch,
   const size_t need = static_cast<size_t>(h->plan.n_pad[x]) * td.ncols_pad * sizeof(float);
   if (!scratch || scratch_bytes < need) return fail(h, CTD_ERR_WORKSPACE, "scratch too small");
   // weights are irrelevant for the dump; keep v finite
+  for (int d = 0; d < h->cfg.dim; ++d) {
+    std::vector<float2> ones(h->cfg.n[d], make_float2(1.f, 0.f));
+    CTD_CUDA(h, cudaMemcpyAsync(h->P.d[d].v, ones.data(), sizeof(float2) * ones.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  CTD_CUDA(h, cudaMemsetAsync(scratch, 0, need, h->stream));
+  CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
+  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->tm, h->grid, x, static_cast<float*>(scratch), h->stream));
+  CTD_CUDA(h, cudaMemcpyAsync(out, scratch, need, cudaMemcpyDeviceToHost, h->stream));
+  CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+  InstState st;
+  ctd_status rs = read_state(h, &st);
+  if (rs != CTD_OK) return rs;
+  if (st.status) return fail(h, status_from_bits(st.status), "device status set");
+  return CTD_OK;
+}
+
+ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out) {
+  if (!h || !out || x < 0 || x >= h->cfg.dim) return CTD_ERR_ARG;
+  if (h->cfg.precision != CTD_PREC_SPLIT_BF16) return fail(h, CTD_ERR_UNSUPPORTED, "tensor-core path only");
+  const ctd::TcDir& td = h->plan.dirs[x];
+  const size_t need = static_cast<size_t>(h->plan.n_pad[x]) * td.ncols_pad * sizeof(float);
+  if (need > CTD_RECONSTRUCT_STATIC_BYTES) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "tile grid of %zu bytes exceeds the %zu-byte static dump array", need,
+                  static_cast<size_t>(CTD_RECONSTRUCT_STATIC_BYTES));
+    return fail(h, CTD_ERR_WORKSPACE, buf);
+  }
+  if (!h->has_modes) return fail(h, CTD_ERR_STATE, "no field set");
+  int cur = -1;
+  CTD_CUDA(h, cudaGetDevice(&cur));
+  if (cur != h->device) return fail(h, CTD_ERR_STATE, "current device is not the handle's");
+  void* scratch = nullptr;
+  CTD_CUDA(h, static_dump_address(cur, &scratch));
   for (int d = 0; d < h->cfg.dim; ++d) {
     std::vector<float2> ones(h->cfg.n[d], make_float2(1.f, 0.f));
     CTD_CUDA(h, cudaMemcpyAsync(h->P.d[d].v, ones.data(), sizeof(float2) * ones.size(), cudaMemcpyHostToDevice,

@@ -75,9 +75,10 @@ def load() -> ctypes.CDLL:
     lib.ctd_probe_solve.argtypes = [vp, i, d, d, vp, vp]
     lib.ctd_probe_trace.argtypes = [vp, i, vp, i]
     lib.ctd_probe_reconstruct.argtypes = [vp, i, vp, vp, sz]
+    lib.ctd_probe_reconstruct_noalloc.argtypes = [vp, i, vp]
     for f in ("ctd_workspace_size", "ctd_create", "ctd_set_initial_modes", "ctd_step", "ctd_energy",
               "ctd_get_modes", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve", "ctd_probe_trace",
-              "ctd_probe_reconstruct"):
+              "ctd_probe_reconstruct", "ctd_probe_reconstruct_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -243,6 +244,13 @@ class Solver:
         _check(self.lib, self.h, self.lib.ctd_probe_reconstruct(self.h, x, out.ctypes.data,
                                                                 ctypes.c_void_p(scratch.data_ptr()), out.nbytes),
                "probe_reconstruct")
+        return out
+
+    def probe_reconstruct_noalloc(self, x: int, rows_pad: int, cols_pad: int) -> np.ndarray:
+        """probe_reconstruct through the library's static dump array (no scratch allocated)."""
+        out = np.zeros((rows_pad, cols_pad), dtype=np.float32)
+        _check(self.lib, self.h, self.lib.ctd_probe_reconstruct_noalloc(self.h, x, out.ctypes.data),
+               "probe_reconstruct_noalloc")
         return out
 
     TRACE_PHASES = ("prologue", "mode_start", "gram_contract", "rhs", "solve", "converge", "commit")
