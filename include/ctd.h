@@ -179,7 +179,10 @@ ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out);
  * seconds[0 .. nslots) (may be NULL), resets the counters, and turns accumulation on
  * (enable != 0) or off.  Slots: 0 prologue (nonlinear-term preparation), 1 mode start,
  * 2 Gram products + nonlinear contraction, 3 right-hand sides, 4 banded solve,
- * 5 convergence test, 6 mode commit.  Synchronises. */
+ * 5 convergence test, 6 mode commit; inside the banded solve: 8 set-up, 9 first pass,
+ * 10 refinement, 11 refinement passes (a count, in units of 1e-9), 14 double-float
+ * residuals, 15 inner FP32 solves; 12 Gram products, 13 contraction.  Also counts
+ * ctd_probe_solve.  Synchronises. */
 ctd_status ctd_probe_trace(ctd_handle h, int enable, double* seconds, int nslots);
 
 #ifdef __cplusplus

@@ -462,10 +462,13 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
       worst_its = std::max(worst_its, ctd::cheb_iterations(static_cast<float>(P.c_t), static_cast<float>(P.c_k),
                                                            static_cast<float>(h->mu_max[d]), 2.384185791015625e-07f));
     const size_t chf = ctd::cheb_floats(n_max);
-    bool small_ends = true;   // the explicit end rows of the band must fit the 256-float stage
-    for (int d = 0; d < cfg->dim; ++d)
-      if ((X.kc[d].nlead + X.kc[d].ntail) * (2 * X.kc[d].b + 1) > 256) small_ends = false;
-    if (small_ends && worst_its <= 200 && fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
+    bool cheb_split = true;   // every dimension has a row split for the Chebyshev CTA
+    for (int d = 0; d < cfg->dim; ++d) {
+      ctd::ChebLayout lay;
+      if (!ctd::cheb_layout(cfg->n[d], X.kc[d].nlead, X.kc[d].ntail, X.kc[d].b, ctd::kThreads - 32, lay))
+        cheb_split = false;
+    }
+    if (cheb_split && worst_its <= 200 && fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
       P.solver_mode = 3;
     else if (fixed + ctd::step_arena_bytes(n_max, crf, 0) + margin <= static_cast<size_t>(optin)) P.solver_mode = 0;
     else if (fixed + ctd::step_arena_bytes(n_max, l0f, 1) + margin <= static_cast<size_t>(optin)) P.solver_mode = 1;

@@ -84,7 +84,7 @@ struct StepParams {
 // phases accumulated in StepParams::trace (each includes its closing grid barrier)
 enum TracePhase { kTrPrologue = 0, kTrInit, kTrGramContract, kTrRhs, kTrSolve, kTrConverge, kTrCommit,
                   kTrSolveFactor = 8, kTrSolveFirst, kTrSolveRefine, kTrSolvePasses, kTrGram, kTrContract,
-                  kTrSlots = 16 };
+                  kTrSolveResidual, kTrSolveInner, kTrSlots = 16 };
 
 // ------------------------------------------------------------------ time & barrier
 __device__ __forceinline__ unsigned long long global_ns() {

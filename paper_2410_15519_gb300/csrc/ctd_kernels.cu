@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) probe_solve_kernel(const __grid_c
   __syncthreads();
   const Dim& dd = P.d[x];
   const SolverStore ss = solver_bind(P.solver_mode == 2 ? 0 : P.solver_mode, ar.solver, P.solver, dd.n, dd.b, dd.mu_max);
-  bool ok = banded_solve(ss, X.kc[x], ld_df(&sm.coef.alpha1), ld_df(&sm.coef.alpha2), P.Q, ar.xsol, sm.redf);
+  bool ok = banded_solve(ss, X.kc[x], ld_df(&sm.coef.alpha1), ld_df(&sm.coef.alpha2), P.Q, ar.xsol, sm.redf, P.trace);
   for (int i = threadIdx.x; i < dd.n; i += blockDim.x) dd.v[i] = ar.xsol[i];
   if (threadIdx.x == 0) X.ctrl[1] = ok ? 0 : 1;
 }

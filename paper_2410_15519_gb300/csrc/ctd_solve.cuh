@@ -583,17 +583,87 @@ __device__ inline float cta_max(float v, float* red) {
   return m;
 }
 
-// ---------------------------------------------------------------- Chebyshev inner solver
-// The D-scaled operator D^-1 (a1 D + a2 K) has its spectrum in [a1, a1 + a2 mu_max] exactly:
-// K is positive semi-definite with the constants as null space (Neumann) and mu_max bounds the
-// largest generalised eigenvalue of (K, D) (Gershgorin bound computed on the host).  The
-// Chebyshev semi-iteration with these bounds needs no inner products: every iteration is one
-// banded product and two vector updates over all rows in parallel, one __syncthreads.
-struct ChebBuffers {
-  float *r, *e, *d0, *d1;   // [n] residual, accumulated solution, two search vectors
-  float* kb;                // explicit band rows near the two ends, FP32 ([nlead + ntail][2b+1], <= 256)
-  float *F, *X;             // aliases used by the refinement loop (F = r, X = e)
+// ---------------------------------------------------------------- Chebyshev solver
+// The D-scaled operator D^-1 (a1 D + a2 K), D = diag(omega), has its spectrum in
+// [a1, a1 + a2 mu_max] exactly: K is positive semi-definite (the constants span its null space
+// under the Neumann boundary) and mu_max bounds the largest generalised eigenvalue of (K, D)
+// (Gershgorin bound computed on the host).  The Chebyshev semi-iteration with these bounds
+// needs no inner products: an iteration is one banded product and three vector updates.
+//
+// Work split of the CTA (T = blockDim.x threads, tint = T - 32):
+//  * interior thread t < tact owns the R consecutive rows nlead + t R .. nlead + (t + 1) R - 1
+//    (uniform stencil, uniform nodal weight);
+//  * the last warp owns the end rows: the nlead explicit rows at the start and the rows
+//    [e0, n) at the end (the explicit tail rows and the interior rows left over), at most
+//    kChebEndMax, two per lane;
+//  * residual, correction and search direction stay in registers.  Each iteration a thread
+//    publishes only what its neighbours read (an interior thread its first and last B values,
+//    an end lane its rows) into one of two alternating buffers, meets the others at one
+//    __syncthreads and reads its halo back.  Interior rows go in pairs through the packed
+//    FP32x2 instructions of sm_100 and later.
+// Each pass solves for the correction of a double-float residual; passes repeat until the
+// correction falls below 2^-48 of the iterate.
+struct ChebLayout {
+  int R;       // rows per interior thread
+  int tint;    // interior threads (blockDim.x - 32)
+  int tact;    // interior threads that own rows
+  int e0;      // first row of the end region at the tail
+  int nend;    // rows of the end warp
 };
+constexpr int kChebEndMax = 64;
+constexpr int kChebRowOptions = 4;
+constexpr int kChebRegion = 80;   // publication slots of one end region (rows -B .. +B around it)
+
+__host__ __device__ inline int cheb_rows_option(int q) {
+  switch (q) {
+    case 0: return 4;
+    case 1: return 8;
+    case 2: return 12;
+    default: return 20;
+  }
+}
+
+// Smallest R (> b, so that halos come from the immediate neighbours) whose split leaves at
+// most kChebEndMax end rows.  False if none does.
+__host__ __device__ inline bool cheb_layout(int n, int nlead, int ntail, int b, int tint, ChebLayout& L) {
+  const int nint = n - nlead - ntail;
+  if (nint < 0) return false;
+  for (int q = 0; q < kChebRowOptions; ++q) {
+    const int R = cheb_rows_option(q);
+    if (R <= b) continue;
+    int tact = nint / R;
+    if (tact > tint) tact = tint;
+    const int nend = nlead + ntail + (nint - tact * R);
+    if (nend > kChebEndMax) continue;
+    if (tact > 0 && (nlead < b || ntail < b)) return false;   // halos of the outer interior threads
+    L.R = R;
+    L.tint = tint;
+    L.tact = tact;
+    L.e0 = nlead + tact * R;
+    L.nend = nend;
+    return true;
+  }
+  return false;
+}
+
+// Floats of one publication buffer: Hl [b][tint] (first b values of each interior thread),
+// Hr [b][tint] (last b values), then the lead and tail regions in natural row order with b
+// slots of zeros or interior values on either side (kChebRegion each), then four slots that
+// threads without rows write and nobody reads.
+__host__ __device__ inline int cheb_buffer_floats(int b, int tint) { return 2 * b * tint + 2 * kChebRegion + 4; }
+
+struct ChebSmem {
+  float2* q;     // [n] right-hand side staged from global memory (double-float)
+  float* halo;   // [2][S] publication buffers
+  float* kb;     // [kChebEndMax][2b+1] a2 K rows of the end rows (FP32)
+  float* red;    // [64] reduction scratch
+  int S;         // floats per publication buffer
+};
+
+__host__ __device__ inline size_t cheb_floats(int n) {
+  return static_cast<size_t>(n) * 2 + 2 * static_cast<size_t>(cheb_buffer_floats(7, 256 - 32)) +
+         static_cast<size_t>(kChebEndMax) * 15 + 64;
+}
 
 __host__ __device__ inline int cheb_iterations(float a1, float a2, float mu_max, float tau) {
   const float kappa = (a1 + a2 * mu_max) / a1;
@@ -604,140 +674,397 @@ __host__ __device__ inline int cheb_iterations(float a1, float a2, float mu_max,
   return k < 1 ? 1 : k;
 }
 
-// e = A^-1 r approximately (Chebyshev semi-iteration with D scaling), r overwritten.  The band
-// descriptor is copied into registers and the interior stencil held in registers: the vectors
-// live in shared memory and their stores would otherwise force descriptor reloads.
-// Register-resident Chebyshev.  Threads 0 .. blockDim.x-33 own the interior rows in contiguous
-// runs of R (R odd, so a warp's strided shared-memory accesses hit 32 different banks); the
-// last warp's lanes own the explicit end rows (lane l < nlead: row l; lane 16 + l: row
-// n - ntail + l).  Residual, iterate and search direction stay in registers; each iteration
-// publishes the search direction to shared memory once (alternating buffers, zero padded by B
-// on both sides) and reads back only the neighbours it needs.
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+
+// s + c += a * x for double-float a, x: the high products are summed with an error-free
+// transformation (TwoSum, plus the FMA residual of each product) into the FP32 compensation c.
+__device__ __forceinline__ void df_dot_acc(float& s, float& c, float2 a, float2 x) {
+  const float p = a.x * x.x;
+  const float pe = __fmaf_rn(a.x, x.x, -p);
+  const float t = s + p;
+  const float bb = t - s;
+  const float se = (s - (t - bb)) + (p - bb);
+  s = t;
+  c += se + pe;
+  c = __fmaf_rn(a.x, x.y, c);
+  c = __fmaf_rn(a.y, x.x, c);
+}
+
+// q_i - (a1 omega_i x_i + a2 (K x)_i) rounded to FP32, from the row's 2B+1 products (s, c).
+__device__ __forceinline__ float df_residual_finish(float s, float c, dfloat a1w, dfloat a2, float2 xi, float2 qi) {
+  const dfloat kx = df_two_sum(s, c);
+  const dfloat ax = df_add(df_mul(a2, kx), df_mul(a1w, dfloat{xi.x, xi.y}));
+  const dfloat rr = df_add(dfloat{qi.x, qi.y}, df_neg(ax));
+  return rr.hi + rr.lo;
+}
+
+__device__ __forceinline__ void bar_sync_all() { asm volatile("bar.sync 0;" ::: "memory"); }
+
+// End of a refinement pass, executed by every thread: CTA max of the correction and of the
+// iterate, trace, and the decision: 0 next pass, 1 converged, -1 non-finite values.
+__device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& prev, int pass, float rho_pass,
+                                             float* red, unsigned long long* trace, unsigned long long& tsub) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+  }
+  const int tid = threadIdx.x;
+  if ((tid & 31) == 0) { red[tid >> 5] = dmax; red[32 + (tid >> 5)] = xmax; }
+  bar_sync_all();
+  dmax = 0.f;
+  xmax = 0.f;
+  for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) { dmax = fmaxf(dmax, red[q]); xmax = fmaxf(xmax, red[32 + q]); }
+  bar_sync_all();
+  if (trace && tid == 0) {
+    atomicAdd(trace + kTrSolvePasses, 1ull);
+    const unsigned long long t = global_ns();
+    atomicAdd(trace + (pass == 0 ? kTrSolveFirst : kTrSolveRefine), t - tsub);
+    tsub = t;
+  }
+  if (!(dmax <= 3.0e38f) || !(xmax <= 3.0e38f)) return -1;
+  // stop once the next correction would fall below 2^-48 of the iterate
+  const float lim = 3.552713678800501e-15f * xmax;
+  if (dmax <= lim || rho_pass * dmax <= lim) return 1;
+  if (pass > 0 && prev > 0.f && dmax * (dmax / prev) <= lim) return 1;
+  prev = dmax;
+  return 0;
+}
+
+// Interior threads: `its` Chebyshev iterations on their R rows.  Threads without rows run the
+// same code on zeros with dummy slots, so that every warp of the interior group executes the
+// same barrier instructions.
 template <int B, int R>
-__device__ inline void cheb_solve_reg(const ChebBuffers& s, const KCompressed& kref, float a1, float a2, int iters,
-                                      float theta, float delta, float sigma) {
-  const KCompressed k = kref;
-  const int n = k.n;
+__device__ __forceinline__ void cheb_iterate_interior(float (&r)[R], float (&e)[R], float (&w)[R + 2 * B + 2],
+                                                      const float2 (&nst)[2 * B + 1], float2 na1w2, float iwin,
+                                                      int its, float sigma, float inv2d, uint32_t pub_l,
+                                                      uint32_t spl, uint32_t pub_r, uint32_t spr, uint32_t src_l,
+                                                      uint32_t str_l, uint32_t src_r, uint32_t str_r, uint32_t bufb) {
   constexpr int W = 2 * B + 1;
-  float st[W];
-#pragma unroll
-  for (int o = 0; o < W; ++o) st[o] = a2 * k.stencil[o].x;
-  const int ilo = k.nlead, ihi = n - k.ntail;
-  const int tint = blockDim.x - 32;                 // interior threads
-  const bool endlane = threadIdx.x >= tint;
-  const int lane = threadIdx.x - tint;
-  int i0 = 0, cnt = 0;                              // interior run [i0, i0 + cnt)
-  int ie = -1;                                      // end row of an end lane
-  if (!endlane) {
-    i0 = ilo + threadIdx.x * R;
-    cnt = max(0, min(R, ihi - i0));
-  } else if (lane < k.nlead) {
-    ie = lane;
-  } else if (lane >= 16 && lane - 16 < k.ntail) {
-    ie = n - k.ntail + (lane - 16);
-  }
-  // end rows: full band row (a2 K) in shared memory
-  const int nx = k.nlead + k.ntail;
-  for (int t = threadIdx.x; t < nx * W; t += blockDim.x) s.kb[t] = a2 * k.rows[t].x;
-  for (int i = threadIdx.x; i < B; i += blockDim.x) {
-    s.d0[i] = 0.f; s.d0[n + B + i] = 0.f;
-    s.d1[i] = 0.f; s.d1[n + B + i] = 0.f;
-  }
-  const float a1in = a1 * k.omega_in.x, iwin = k.inv_omega_in;
-  float r[R], e[R], d[R];
-#pragma unroll
-  for (int j = 0; j < R; ++j) {
-    r[j] = j < cnt ? s.r[i0 + j] : 0.f;
-    e[j] = 0.f;
-    d[j] = r[j] * iwin / theta;
-  }
-  float re = 0.f, ee = 0.f, de = 0.f, iwe = 0.f, a1e = 0.f;
-  const float* kre = nullptr;
-  if (ie >= 0) {
-    iwe = kc_inv_omega(k, ie);
-    a1e = a1 * kc_omega(k, ie).x;
-    re = s.r[ie];
-    de = re * iwe / theta;
-    kre = s.kb + (ie < ilo ? ie : k.nlead + ie - ihi) * W;
-  }
+  constexpr int OWN = B + 1;
   float rho_old = 1.f / sigma;
-  for (int it = 0; it < iters; ++it) {
-    float* dsh = ((it & 1) ? s.d1 : s.d0) + B;
-    if (!endlane) {
+  for (int it = 0; it < its; ++it) {
+    const uint32_t boff = (it & 1) ? bufb : 0u;
 #pragma unroll
-      for (int j = 0; j < R; ++j)
-        if (j < cnt) dsh[i0 + j] = d[j];
-    } else if (ie >= 0) {
-      dsh[ie] = de;
+    for (int q = 0; q < B; ++q) {
+      sts_f32(pub_l + boff + q * spl, w[OWN + q]);
+      sts_f32(pub_r + boff + q * spr, w[OWN + R - B + q]);
     }
-    __syncthreads();
-    const float rho = 1.f / (2.f * sigma - rho_old);
-    const float c1 = rho * rho_old, c2 = 2.f * rho / delta;
-    if (!endlane) {
-      if (cnt > 0) {
-        // window rows i0 - B .. i0 + R + B - 1; own rows from registers, the rest from the
-        // published vector (rows >= n read the zero padding, rows past it are zero)
-        float win[R + 2 * B];
+    bar_sync_all();
+    const float rho = __fdividef(1.f, 2.f * sigma - rho_old);
+    const float c1 = rho * rho_old, c2 = rho * inv2d * iwin;
 #pragma unroll
-        for (int t = 0; t < B; ++t) {
-          win[t] = dsh[i0 - B + t];
-          const int row = i0 + R + t;
-          win[R + B + t] = row < n + B ? dsh[row] : 0.f;
-        }
+    for (int q = 0; q < B; ++q) {
+      w[1 + q] = lds_f32(src_l + boff + q * str_l);
+      w[R + B + 1 + q] = lds_f32(src_r + boff + q * str_r);
+    }
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int row = i0 + j;
-          win[B + j] = j < cnt ? d[j] : (row < n + B ? dsh[row] : 0.f);
-        }
+    for (int m = 0; m < R / 2; ++m) {
+      float2 acc = make_float2(r[2 * m], r[2 * m + 1]);
+      acc = __ffma2_rn(na1w2, make_float2(w[OWN + 2 * m], w[OWN + 2 * m + 1]), acc);
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-          float acc = a1in * d[j];
+      for (int o = 0; o < W; ++o) acc = __ffma2_rn(nst[o], make_float2(w[2 * m + 1 + o], w[2 * m + 2 + o]), acc);
+      r[2 * m] = acc.x;
+      r[2 * m + 1] = acc.y;
+    }
+    const float2 c1v = make_float2(c1, c1), c2v = make_float2(c2, c2);
 #pragma unroll
-          for (int o = 0; o < W; ++o) acc = __fmaf_rn(st[o], win[j + o], acc);
-          e[j] += d[j];
-          r[j] -= acc;
-          d[j] = __fmaf_rn(c1, d[j], c2 * (r[j] * iwin));
-        }
-      }
-    } else if (ie >= 0) {
-      float acc = a1e * de;
-#pragma unroll
-      for (int o = 0; o < W; ++o) acc = __fmaf_rn(kre[o], dsh[ie + o - B], acc);
-      ee += de;
-      re -= acc;
-      de = __fmaf_rn(c1, de, c2 * (re * iwe));
+    for (int m = 0; m < R / 2; ++m) {
+      const float2 dd = make_float2(w[OWN + 2 * m], w[OWN + 2 * m + 1]);
+      const float2 ev = __fadd2_rn(make_float2(e[2 * m], e[2 * m + 1]), dd);
+      e[2 * m] = ev.x;
+      e[2 * m + 1] = ev.y;
+      const float2 nd = __ffma2_rn(c1v, dd, __fmul2_rn(c2v, make_float2(r[2 * m], r[2 * m + 1])));
+      w[OWN + 2 * m] = nd.x;
+      w[OWN + 2 * m + 1] = nd.y;
     }
     rho_old = rho;
   }
-  if (!endlane) {
+}
+
+// End lanes: `its` Chebyshev iterations on up to two explicit rows each.
+template <int B>
+__device__ __forceinline__ void cheb_iterate_end(float (&er)[2], float (&ee)[2], float (&ed)[2], const int (&erow)[2],
+                                                 const uint32_t (&epub)[2], const uint32_t (&ewin)[2],
+                                                 const uint32_t (&ekb)[2], const float (&ea1w)[2],
+                                                 const float (&eiw)[2], int its, float sigma, float inv2d,
+                                                 uint32_t bufb) {
+  constexpr int W = 2 * B + 1;
+  float rho_old = 1.f / sigma;
+  for (int it = 0; it < its; ++it) {
+    const uint32_t boff = (it & 1) ? bufb : 0u;
 #pragma unroll
-    for (int j = 0; j < R; ++j)
-      if (j < cnt) s.e[i0 + j] = e[j];
-  } else if (ie >= 0) {
-    s.e[ie] = ee;
+    for (int s2 = 0; s2 < 2; ++s2)
+      if (erow[s2] >= 0) sts_f32(epub[s2] + boff, ed[s2]);
+    bar_sync_all();
+    const float rho = __fdividef(1.f, 2.f * sigma - rho_old);
+    const float c1 = rho * rho_old, c2 = rho * inv2d;
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      if (erow[s2] < 0) continue;
+      float acc = ea1w[s2] * ed[s2];
+#pragma unroll
+      for (int o = 0; o < W; ++o)
+        acc = __fmaf_rn(lds_f32(ekb[s2] + 4u * o), o == B ? ed[s2] : lds_f32(ewin[s2] + boff + 4u * o), acc);
+      ee[s2] += ed[s2];
+      er[s2] -= acc;
+      ed[s2] = __fmaf_rn(c1, ed[s2], c2 * (er[s2] * eiw[s2]));
+    }
+    rho_old = rho;
+  }
+}
+
+template <int B, int R>
+__device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, dfloat a1, dfloat a2, float mu_max,
+                             const float2* qg, float2* x, const float2* x0, const ChebSmem& smref,
+                             unsigned long long* trace) {
+  constexpr int W = 2 * B + 1;
+  constexpr int NW = R + 2 * B + 2;   // window: halo rows at [1, B + 1) and [R + B + 1, R + 2B + 1)
+  constexpr int OWN = B + 1;          // own row j at w[OWN + j] (even index: rows pair up)
+  const KCompressed k = kref;
+  const ChebLayout L = Lref;
+  const ChebSmem sm = smref;
+  const int n = k.n, tid = threadIdx.x, T = blockDim.x;
+  unsigned long long tsub = trace ? global_ns() : 0ull;
+
+  // ---- Chebyshev constants (FP32 is enough for the iteration count)
+  const float lmin = a1.hi, lmax = a1.hi + a2.hi * mu_max;
+  const float theta = 0.5f * (lmax + lmin);
+  float delta = 0.5f * (lmax - lmin);
+  if (!(delta > 0.f)) delta = 1e-30f * theta;
+  const float sigma = theta / delta, inv2d = 2.f / delta, c0 = 1.f / theta;
+  int its = cheb_iterations(a1.hi, a2.hi, mu_max, 2.384185791015625e-07f);   // 2^-22 per pass
+  const bool ok = (lmin > 0.f) && its < 100000;
+  if (its > 4096) its = 4096;
+  const float rho_pass = 4.f * fmaxf(2.384185791015625e-07f, (lmax / lmin) * 5.960464477539063e-08f);
+
+  // ---- stage q (and the warm start), zero the end regions, end-row coefficients.  Loads are
+  // issued in groups of eight before the stores so that their latencies overlap.
+  const int reg0 = 2 * B * L.tint;               // lead region: slot B + row
+  const int reg1 = reg0 + kChebRegion;           // tail region: slot B + row - e0 (tact > 0)
+  const int trash = reg1 + kChebRegion;          // written by threads without rows, never read
+  const bool warm = x0 != nullptr;
+  for (int i = tid; i < n; i += 8 * T) {
+    float2 v[8], u[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int ii = i + g * T;
+      v[g] = ii < n ? qg[ii] : make_float2(0.f, 0.f);
+      u[g] = (warm && ii < n) ? x0[ii] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int ii = i + g * T;
+      if (ii < n) {
+        sm.q[ii] = v[g];
+        if (warm) x[ii] = u[g];
+      }
+    }
+  }
+  for (int c = tid; c < 4 * kChebRegion; c += T)
+    sm.halo[(c / (2 * kChebRegion)) * sm.S + reg0 + c % (2 * kChebRegion)] = 0.f;
+  for (int c = tid; c < L.nend * W; c += T) {
+    const int slot = c / W, o = c - slot * W;
+    const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
+    const int j = row + o - B;
+    sm.kb[c] = (j >= 0 && j < n) ? a2.hi * kc_entry(k, row, o - B).x : 0.f;
   }
   __syncthreads();
+
+  const uint32_t hbase = static_cast<uint32_t>(__cvta_generic_to_shared(sm.halo));
+  const uint32_t bufb = 4u * static_cast<uint32_t>(sm.S);
+  if (trace && tid == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveFactor, t - tsub); tsub = t; }
+  float prev = 0.f;
+  bool fail = false;
+
+  if (tid < L.tint) {
+    // ================= interior group
+    const bool active = tid < L.tact;
+    const int i0 = k.nlead + tid * R;
+    const uint32_t kstr = 4u * static_cast<uint32_t>(L.tint);
+    float2 nst[W];
+#pragma unroll
+    for (int o = 0; o < W; ++o) {
+      const float v = -a2.hi * k.stencil[o].x;
+      nst[o] = make_float2(v, v);
+    }
+    const float a1in = a1.hi * k.omega_in.x, iwin = k.inv_omega_in;
+    const float2 na1w2 = make_float2(-a1in, -a1in);
+    const dfloat a1w_in = df_mul(a1, dfloat{k.omega_in.x, k.omega_in.y});
+    // where the first / last B values are published and the halos read; the outer interior
+    // threads use the end regions, threads without rows a trash slot and the zero slots
+    uint32_t pub_l = hbase + 4u * trash, pub_r = hbase + 4u * trash, spl = 0u, spr = 0u;
+    uint32_t src_l = hbase + 4u * reg0, src_r = hbase + 4u * reg0, str_l = 0u, str_r = 0u;
+    if (active) {
+      if (tid == 0) {
+        pub_l = hbase + 4u * (reg0 + B + k.nlead);          // rows nlead .. nlead + B - 1
+        spl = 4u;
+        src_l = hbase + 4u * (reg0 + k.nlead);              // rows nlead - B .. nlead - 1
+        str_l = 4u;
+      } else {
+        pub_l = hbase + 4u * tid;
+        spl = kstr;
+        src_l = hbase + 4u * (B * L.tint + tid - 1);
+        str_l = kstr;
+      }
+      if (tid == L.tact - 1) {
+        pub_r = hbase + 4u * reg1;                          // rows e0 - B .. e0 - 1
+        spr = 4u;
+        src_r = hbase + 4u * (reg1 + B);                    // rows e0 .. e0 + B - 1
+        str_r = 4u;
+      } else {
+        pub_r = hbase + 4u * (B * L.tint + tid);
+        spr = kstr;
+        src_r = hbase + 4u * (tid + 1);
+        str_r = kstr;
+      }
+    }
+    float r[R], e[R], w[NW];
+    for (int pass = 0; pass < 5; ++pass) {
+      const bool cold0 = !warm && pass == 0;
+      unsigned long long tp = trace ? global_ns() : 0ull;
+      // residual of the current iterate (double-float), rounded to FP32
+#pragma unroll
+      for (int j = 0; j < R; ++j) r[j] = 0.f;
+      if (active) {
+        if (cold0) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) { const float2 qq = sm.q[i0 + j]; r[j] = qq.x + qq.y; }
+        } else {
+          float2 sdf[W];
+#pragma unroll
+          for (int o = 0; o < W; ++o) sdf[o] = k.stencil[o];
+          float2 xw[R + 2 * B];
+#pragma unroll
+          for (int t = 0; t < R + 2 * B; ++t) xw[t] = x[i0 - B + t];
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            float s = 0.f, c = 0.f;
+#pragma unroll
+            for (int o = 0; o < W; ++o) df_dot_acc(s, c, sdf[o], xw[j + o]);
+            r[j] = df_residual_finish(s, c, a1w_in, a2, xw[j + B], sm.q[i0 + j]);
+          }
+        }
+      }
+      if (trace) {
+        bar_sync_all();
+        if (tid == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveResidual, t - tp); tp = t; }
+      }
+#pragma unroll
+      for (int j = 0; j < NW; ++j) w[j] = 0.f;
+#pragma unroll
+      for (int j = 0; j < R; ++j) { e[j] = 0.f; w[OWN + j] = r[j] * iwin * c0; }
+      cheb_iterate_interior<B, R>(r, e, w, nst, na1w2, iwin, its, sigma, inv2d, pub_l, spl, pub_r, spr, src_l, str_l,
+                                  src_r, str_r, bufb);
+      if (trace && tid == 0) atomicAdd(trace + kTrSolveInner, global_ns() - tp);
+      // x += e (double-float), size of the correction and of the iterate
+      float dmax = 0.f, xmax = 0.f;
+      if (active) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const float2 xo = cold0 ? make_float2(0.f, 0.f) : x[i0 + j];
+          const dfloat nx = df_add(dfloat{xo.x, xo.y}, dfloat{e[j], 0.f});
+          x[i0 + j] = make_float2(nx.hi, nx.lo);
+          dmax = fmaxf(dmax, fabsf(e[j]));
+          xmax = fmaxf(xmax, fabsf(nx.hi));
+          if (!(fabsf(e[j]) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
+        }
+      }
+      const int stop = cheb_pass_end(dmax, xmax, prev, pass, rho_pass, sm.red, trace, tsub);
+      if (stop) { fail = stop < 0; break; }
+    }
+  } else {
+    // ================= end warp
+    const int lane = tid - L.tint;
+    int erow[2] = {-1, -1};
+    uint32_t epub[2] = {0u, 0u}, ewin[2] = {0u, 0u}, ekb[2] = {0u, 0u};
+    float ea1w[2] = {0.f, 0.f}, eiw[2] = {0.f, 0.f};
+    dfloat ea1wd[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    const uint32_t kbase = static_cast<uint32_t>(__cvta_generic_to_shared(sm.kb));
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int slot = lane + 32 * s2;
+      if (slot < L.nend) {
+        const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
+        erow[s2] = row;
+        const float2 om = kc_omega(k, row);
+        ea1w[s2] = a1.hi * om.x;
+        ea1wd[s2] = df_mul(a1, dfloat{om.x, om.y});
+        eiw[s2] = kc_inv_omega(k, row);
+        const int ps = (L.tact == 0 || row < k.nlead) ? reg0 + B + row : reg1 + B + (row - L.e0);
+        epub[s2] = hbase + 4u * ps;
+        ewin[s2] = hbase + 4u * (ps - B);
+        ekb[s2] = kbase + 4u * (slot * W);
+      }
+    }
+    float er[2], ee[2], ed[2];
+    for (int pass = 0; pass < 5; ++pass) {
+      const bool cold0 = !warm && pass == 0;
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        er[s2] = 0.f;
+        const int row = erow[s2];
+        if (row < 0) continue;
+        if (cold0) {
+          const float2 qq = sm.q[row];
+          er[s2] = qq.x + qq.y;
+        } else {
+          float s = 0.f, c = 0.f;
+          for (int o = 0; o < W; ++o) {
+            const int j = row + o - B;
+            if (j >= 0 && j < n) df_dot_acc(s, c, kc_entry(k, row, o - B), x[j]);
+          }
+          er[s2] = df_residual_finish(s, c, ea1wd[s2], a2, x[row], sm.q[row]);
+        }
+      }
+      if (trace) bar_sync_all();
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) { ee[s2] = 0.f; ed[s2] = er[s2] * eiw[s2] * c0; }
+      cheb_iterate_end<B>(er, ee, ed, erow, epub, ewin, ekb, ea1w, eiw, its, sigma, inv2d, bufb);
+      float dmax = 0.f, xmax = 0.f;
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int row = erow[s2];
+        if (row < 0) continue;
+        const float2 xo = cold0 ? make_float2(0.f, 0.f) : x[row];
+        const dfloat nx = df_add(dfloat{xo.x, xo.y}, dfloat{ee[s2], 0.f});
+        x[row] = make_float2(nx.hi, nx.lo);
+        dmax = fmaxf(dmax, fabsf(ee[s2]));
+        xmax = fmaxf(xmax, fabsf(nx.hi));
+        if (!(fabsf(ee[s2]) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
+      }
+      const int stop = cheb_pass_end(dmax, xmax, prev, pass, rho_pass, sm.red, trace, tsub);
+      if (stop) { fail = stop < 0; break; }
+    }
+  }
+  __syncthreads();
+  return ok && !fail;
 }
 
-template <int B>
-__device__ inline void cheb_solve_b(const ChebBuffers& s, const KCompressed& k, float a1, float a2, int iters,
-                                    float theta, float delta, float sigma) {
-  const int tint = blockDim.x - 32;
-  const int nint = k.n - k.nlead - k.ntail;
-  const int need = (nint + tint - 1) / tint;
-  if (need <= 1) cheb_solve_reg<B, 1>(s, k, a1, a2, iters, theta, delta, sigma);
-  else if (need <= 3) cheb_solve_reg<B, 3>(s, k, a1, a2, iters, theta, delta, sigma);
-  else if (need <= 5) cheb_solve_reg<B, 5>(s, k, a1, a2, iters, theta, delta, sigma);
-  else if (need <= 11) cheb_solve_reg<B, 11>(s, k, a1, a2, iters, theta, delta, sigma);
-  else cheb_solve_reg<B, 19>(s, k, a1, a2, iters, theta, delta, sigma);
-}
-
-static __device__ __noinline__ void cheb_solve(const ChebBuffers& s, const KCompressed& k, float a1, float a2,
-                                               int iters, float theta, float delta, float sigma) {
-  switch (k.b) {
-    case 3: cheb_solve_b<3>(s, k, a1, a2, iters, theta, delta, sigma); break;
-    case 5: cheb_solve_b<5>(s, k, a1, a2, iters, theta, delta, sigma); break;
-    default: cheb_solve_b<7>(s, k, a1, a2, iters, theta, delta, sigma); break;
+static __device__ __noinline__ bool cheb_banded_solve(const KCompressed& k, dfloat a1, dfloat a2, float mu_max,
+                                                      const float2* q, float2* x, const float2* x0,
+                                                      const ChebSmem& sm, unsigned long long* trace) {
+  ChebLayout L;
+  if (!cheb_layout(k.n, k.nlead, k.ntail, k.b, static_cast<int>(blockDim.x) - 32, L)) return false;
+  switch (k.b * 100 + L.R) {
+    case 304: return cheb_solve_t<3, 4>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 308: return cheb_solve_t<3, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 312: return cheb_solve_t<3, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 320: return cheb_solve_t<3, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 508: return cheb_solve_t<5, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 512: return cheb_solve_t<5, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 520: return cheb_solve_t<5, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 708: return cheb_solve_t<7, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 712: return cheb_solve_t<7, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 720: return cheb_solve_t<7, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    default: return false;
   }
 }
 
@@ -790,7 +1117,7 @@ struct SolverStore {
                       // 3: Chebyshev semi-iteration (`ch`)
   CRBuffers cr;
   L0Buffers l0;
-  ChebBuffers ch;
+  ChebSmem ch;
   float mu_max;       // Chebyshev: bound of the largest generalised eigenvalue of (K, D)
   float *F, *X;       // full-length right-hand side / solution of one pass
 };
@@ -800,69 +1127,51 @@ struct SolverStore {
 static __device__ __noinline__ bool banded_solve(const SolverStore& s, const KCompressed& k, dfloat a1, dfloat a2,
                                     const float2* q, float2* x, float* red, unsigned long long* trace = nullptr,
                                     const float2* x0 = nullptr) {
+  if (s.mode == 3) return cheb_banded_solve(k, a1, a2, s.mu_max, q, x, x0, s.ch, trace);
   const int n = k.n, b = k.b;
-  const int npad = s.mode == 3 ? n : (s.mode == 0 ? s.cr.nb : s.l0.nb) * b;
+  const int npad = (s.mode == 0 ? s.cr.nb : s.l0.nb) * b;
   unsigned long long t0 = trace ? global_ns() : 0ull;
   bool ok = true;
-  int cheb_its = 0;
-  float th = 0.f, de = 0.f, sg = 0.f;
   if (s.mode == 0) {
     cr_build(s.cr, k, a1.hi, a2.hi);
     __syncthreads();
     ok = cr_factor(s.cr);
-  } else if (s.mode == 1) {
-    ok = l0_factor(s.l0, k, a1.hi, a2.hi);
   } else {
-    const float lmin = a1.hi, lmax = a1.hi + a2.hi * s.mu_max;
-    th = 0.5f * (lmax + lmin);
-    de = 0.5f * (lmax - lmin);
-    if (!(de > 0.f)) de = 1e-30f * th;
-    sg = th / de;
-    cheb_its = cheb_iterations(a1.hi, a2.hi, s.mu_max, 2.384185791015625e-07f);   // 2^-22
-    ok = (lmin > 0.f) && cheb_its < 100000;
-    if (cheb_its > 4096) cheb_its = 4096;
+    ok = l0_factor(s.l0, k, a1.hi, a2.hi);
   }
   if (trace && threadIdx.x == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveFactor, t - t0); t0 = t; }
-  // per-pass contraction of the error: the Chebyshev bound 2^-22, or FP32 rounding times cond
-  const float kappa = s.mode == 3 ? (a1.hi + a2.hi * s.mu_max) / a1.hi : 1.f;
-  const float rho_pass = 4.f * fmaxf(2.384185791015625e-07f, kappa * 5.960464477539063e-08f);
-  bool warm = x0 != nullptr && s.mode == 3;
-  if (warm) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = x0[i];
-    __syncthreads();
-  } else {
-    for (int i = threadIdx.x; i < npad; i += blockDim.x) s.F[i] = (i < n) ? q[i].x : 0.f;
-    __syncthreads();
-    if (s.mode == 0) cr_solve(s.cr);
-    else if (s.mode == 1) l0_solve(s.l0, k, a1.hi, a2.hi);
-    else cheb_solve(s.ch, k, a1.hi, a2.hi, cheb_its, th, de, sg);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = make_float2(s.X[i], 0.f);
-    __syncthreads();
-  }
+  for (int i = threadIdx.x; i < npad; i += blockDim.x) s.F[i] = (i < n) ? q[i].x : 0.f;
+  __syncthreads();
+  if (s.mode == 0) cr_solve(s.cr);
+  else l0_solve(s.l0, k, a1.hi, a2.hi);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = make_float2(s.X[i], 0.f);
+  __syncthreads();
   if (trace && threadIdx.x == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveFirst, t - t0); t0 = t; }
   float prev = 0.f;
   for (int it = 0; it < 4; ++it) {
     // r = q - (a1 omega x + a2 K x) in double-float
+    unsigned long long tp = trace ? global_ns() : 0ull;
     residual_df(k, a1, a2, q, x, s.F, npad);
     __syncthreads();
+    if (trace && threadIdx.x == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveResidual, t - tp); tp = t; }
     if (s.mode == 0) cr_solve(s.cr);
-    else if (s.mode == 1) l0_solve(s.l0, k, a1.hi, a2.hi);
-    else cheb_solve(s.ch, k, a1.hi, a2.hi, cheb_its, th, de, sg);
+    else l0_solve(s.l0, k, a1.hi, a2.hi);
+    if (trace && threadIdx.x == 0) atomicAdd(trace + kTrSolveInner, global_ns() - tp);
     float dmax = 0.f, xmax = 0.f;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const dfloat nx = df_add(dfloat{x[i].x, x[i].y}, dfloat{s.X[i], 0.f});
       x[i] = make_float2(nx.hi, nx.lo);
       dmax = fmaxf(dmax, fabsf(s.X[i]));
+      if (!(fabsf(s.X[i]) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
       xmax = fmaxf(xmax, fabsf(nx.hi));
     }
     dmax = cta_max(dmax, red);
     xmax = cta_max(xmax, red);
     if (trace && threadIdx.x == 0) atomicAdd(trace + kTrSolvePasses, 1ull);
-    if (!(dmax == dmax) || !(xmax <= 3.0e38f)) return false;   // NaN / Inf
+    if (!(dmax <= 3.0e38f) || !(xmax <= 3.0e38f)) return false;   // NaN / Inf
     // the refinement contracts the error by rho ~ dmax / prev per pass; stop once the next
     // correction would fall below 2^-48 of the iterate (or this one already did)
     if (dmax <= 3.552713678800501e-15f * xmax) break;
-    if (s.mode == 3 && rho_pass * dmax <= 3.552713678800501e-15f * xmax) break;
     if (it > 0 && prev > 0.f && dmax * (dmax / prev) <= 3.552713678800501e-15f * xmax) break;
     prev = dmax;
   }
@@ -880,24 +1189,19 @@ __host__ __device__ inline size_t l0_global_floats(int n, int b) {
   return static_cast<size_t>(nb) * b * 3;
 }
 
-__host__ __device__ inline size_t cheb_floats(int n) { return static_cast<size_t>(n) * 4 + 32 + 256; }
-
 // Bind solver storage.  mode 0: factors at fbase; mode 1: level-1 factors at fbase, full vectors
-// at gbase; mode 3: Chebyshev vectors at fbase.
+// at gbase; mode 3: Chebyshev right-hand side, publication buffers and reduction scratch at fbase.
 __device__ inline SolverStore solver_bind(int mode, float* fbase, float* gbase, int n, int b, float mu_max = 0.f) {
   SolverStore s;
   s.mode = mode;
   s.mu_max = mu_max;
+  s.F = s.X = nullptr;
   if (mode == 3) {
-    s.ch.r = fbase;
-    s.ch.e = fbase + n;
-    s.ch.d0 = fbase + 2 * n;            // n + 2B published search direction (B <= 7)
-    s.ch.d1 = fbase + 3 * n + 16;
-    s.ch.kb = fbase + 4 * n + 32;
-    s.ch.F = s.ch.r;
-    s.ch.X = s.ch.e;
-    s.F = s.ch.r;
-    s.X = s.ch.e;
+    s.ch.q = reinterpret_cast<float2*>(fbase);
+    s.ch.S = cheb_buffer_floats(b, static_cast<int>(blockDim.x) - 32);
+    s.ch.halo = fbase + 2 * static_cast<size_t>(n);
+    s.ch.kb = s.ch.halo + 2 * s.ch.S;
+    s.ch.red = s.ch.kb + kChebEndMax * 15;
   } else if (mode == 0) {
     s.cr = cr_bind(fbase, n, b);
     s.F = s.cr.F;

@@ -263,7 +263,7 @@ class Solver:
                "probe_trace")
         d = dict(zip(self.TRACE_PHASES, out[:len(self.TRACE_PHASES)].tolist()))
         d.update(solve_factor=out[8], solve_first=out[9], solve_refine=out[10], solve_passes=out[11] * 1e9,
-                 gram=out[12], contract=out[13])
+                 gram=out[12], contract=out[13], solve_residual=out[14], solve_inner=out[15])
         return d
 
     def probe_solve(self, x: int, alpha1: float, alpha2: float, q: np.ndarray) -> np.ndarray:
