@@ -654,15 +654,18 @@ __host__ __device__ inline int cheb_buffer_floats(int b, int tint) { return 2 * 
 
 struct ChebSmem {
   float2* q;     // [n] right-hand side staged from global memory (double-float)
+  float2* kbd;   // [kChebEndMax][2b+1] K rows of the end rows (double-float)
+  float2* st;    // [2b+1] interior stencil of K (double-float)
   float* halo;   // [2][S] publication buffers
-  float* kb;     // [kChebEndMax][2b+1] a2 K rows of the end rows (FP32)
+  float* kb;     // [kChebEndMax][2b+1] a2 K + a1 omega rows of the end rows (FP32)
+  float* rs;     // [n] residual / correction of the interior rows (FP32)
   float* red;    // [64] reduction scratch
   int S;         // floats per publication buffer
 };
 
 __host__ __device__ inline size_t cheb_floats(int n) {
-  return static_cast<size_t>(n) * 2 + 2 * static_cast<size_t>(cheb_buffer_floats(7, 256 - 32)) +
-         static_cast<size_t>(kChebEndMax) * 15 + 64;
+  return static_cast<size_t>(n) * 3 + static_cast<size_t>(kChebEndMax) * 15 * 3 + 32 +
+         2 * static_cast<size_t>(cheb_buffer_floats(7, 256 - 32)) + 64;
 }
 
 __host__ __device__ inline int cheb_iterations(float a1, float a2, float mu_max, float tau) {
@@ -705,12 +708,77 @@ __device__ __forceinline__ float df_residual_finish(float s, float c, dfloat a1w
   return rr.hi + rr.lo;
 }
 
+// ---- two double-float values side by side (rows i, i + 1), FP32x2 instructions; the same
+// operation order as the scalar dfloat routines, so the results are identical.
+struct df2 { float2 hi, lo; };
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ df2 df2_two_sum(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  const float2 bb = f2_sub(s, a);
+  const float2 e = __fadd2_rn(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df2 df2_fast_two_sum(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return {s, f2_sub(b, f2_sub(s, a))};
+}
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b) {
+  df2 s = df2_two_sum(a.hi, b.hi);
+  const df2 t = df2_two_sum(a.lo, b.lo);
+  s.lo = __fadd2_rn(s.lo, t.hi);
+  s = df2_fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd2_rn(s.lo, t.lo);
+  return df2_fast_two_sum(s.hi, s.lo);
+}
+// a * b for a double-float scalar a
+__device__ __forceinline__ df2 df2_mul_s(dfloat a, df2 b) {
+  const float2 ah = make_float2(a.hi, a.hi), al = make_float2(a.lo, a.lo);
+  const float2 p = __fmul2_rn(ah, b.hi);
+  float2 e = __ffma2_rn(ah, b.hi, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(ah, b.lo, e);
+  e = __ffma2_rn(al, b.hi, e);
+  return df2_fast_two_sum(p, e);
+}
+// df_dot_acc for two rows at once: s + c += a * x
+__device__ __forceinline__ void df2_dot_acc(float2& s, float2& c, float2 a, float2 xh, float2 xl) {
+  const float2 ah = make_float2(a.x, a.x), al = make_float2(a.y, a.y);
+  const float2 p = __fmul2_rn(ah, xh);
+  const float2 pe = __ffma2_rn(ah, xh, make_float2(-p.x, -p.y));
+  const float2 t = __fadd2_rn(s, p);
+  const float2 bb = f2_sub(t, s);
+  const float2 se = __fadd2_rn(f2_sub(s, f2_sub(t, bb)), f2_sub(p, bb));
+  s = t;
+  c = __fadd2_rn(c, __fadd2_rn(se, pe));
+  c = __ffma2_rn(ah, xl, c);
+  c = __ffma2_rn(al, xh, c);
+}
+
 __device__ __forceinline__ void bar_sync_all() { asm volatile("bar.sync 0;" ::: "memory"); }
 
+// 8-byte global -> shared copy that bypasses registers; completed by cp_async_wait_all.
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src_gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem))),
+               "l"(src_gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// Error bound of one pass of `its` Chebyshev iterations (x4 margin), FP32 rounding included.
+__device__ __forceinline__ float cheb_pass_bound(float rho, int its, float kappa) {
+  const float cheb = 2.f * exp2f(static_cast<float>(its) * log2f(rho));
+  return 4.f * fmaxf(cheb, kappa * 5.960464477539063e-08f);
+}
+
 // End of a refinement pass, executed by every thread: CTA max of the correction and of the
-// iterate, trace, and the decision: 0 next pass, 1 converged, -1 non-finite values.
-__device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& prev, int pass, float rho_pass,
-                                             float* red, unsigned long long* trace, unsigned long long& tsub) {
+// iterate, trace, and the decision: 0 next pass (with `its` iterations), 1 converged, -1
+// non-finite values.  The error left after the pass is at most bound * dmax; the pass stops
+// the solve once that is below 2^-48 of the iterate, else the next pass gets just enough
+// iterations to get there (never fewer than the FP32 rounding floor allows).
+__device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& bound, int& its, int pass, float a1,
+                                             float a2, float mu_max, float rho, float kappa, float* red,
+                                             unsigned long long* trace, unsigned long long& tsub) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -730,23 +798,26 @@ __device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& prev
     tsub = t;
   }
   if (!(dmax <= 3.0e38f) || !(xmax <= 3.0e38f)) return -1;
-  // stop once the next correction would fall below 2^-48 of the iterate
-  const float lim = 3.552713678800501e-15f * xmax;
-  if (dmax <= lim || rho_pass * dmax <= lim) return 1;
-  if (pass > 0 && prev > 0.f && dmax * (dmax / prev) <= lim) return 1;
-  prev = dmax;
+  const float lim = 3.552713678800501e-15f * xmax;   // 2^-48 of the iterate
+  if (dmax <= lim || bound * dmax <= lim) return 1;
+  const float need = lim / (4.f * bound * dmax);     // reduction the next pass must reach
+  const float floor32 = 4.f * kappa * 5.960464477539063e-08f;
+  const float tau = need > floor32 ? fminf(need, 0.5f) : 2.384185791015625e-07f;
+  its = cheb_iterations(a1, a2, mu_max, tau);
+  if (its > 4096) its = 4096;
+  bound = cheb_pass_bound(rho, its, kappa);
   return 0;
 }
 
 // Interior threads: `its` Chebyshev iterations on their R rows.  Threads without rows run the
 // same code on zeros with dummy slots, so that every warp of the interior group executes the
-// same barrier instructions.
+// same barrier instructions.  nst: -(a1 omega + a2 K) stencil, packed.
 template <int B, int R>
 __device__ __forceinline__ void cheb_iterate_interior(float (&r)[R], float (&e)[R], float (&w)[R + 2 * B + 2],
-                                                      const float2 (&nst)[2 * B + 1], float2 na1w2, float iwin,
-                                                      int its, float sigma, float inv2d, uint32_t pub_l,
-                                                      uint32_t spl, uint32_t pub_r, uint32_t spr, uint32_t src_l,
-                                                      uint32_t str_l, uint32_t src_r, uint32_t str_r, uint32_t bufb) {
+                                                      const float2 (&nst)[2 * B + 1], float iwin, int its,
+                                                      float sigma, float inv2d, uint32_t pub_l, uint32_t spl,
+                                                      uint32_t pub_r, uint32_t spr, uint32_t src_l, uint32_t str_l,
+                                                      uint32_t src_r, uint32_t str_r, uint32_t bufb) {
   constexpr int W = 2 * B + 1;
   constexpr int OWN = B + 1;
   float rho_old = 1.f / sigma;
@@ -768,7 +839,6 @@ __device__ __forceinline__ void cheb_iterate_interior(float (&r)[R], float (&e)[
 #pragma unroll
     for (int m = 0; m < R / 2; ++m) {
       float2 acc = make_float2(r[2 * m], r[2 * m + 1]);
-      acc = __ffma2_rn(na1w2, make_float2(w[OWN + 2 * m], w[OWN + 2 * m + 1]), acc);
 #pragma unroll
       for (int o = 0; o < W; ++o) acc = __ffma2_rn(nst[o], make_float2(w[2 * m + 1 + o], w[2 * m + 2 + o]), acc);
       r[2 * m] = acc.x;
@@ -789,13 +859,13 @@ __device__ __forceinline__ void cheb_iterate_interior(float (&r)[R], float (&e)[
   }
 }
 
-// End lanes: `its` Chebyshev iterations on up to two explicit rows each.
+// End lanes: `its` Chebyshev iterations on up to two explicit rows each (row coefficients in
+// shared memory, a1 omega folded into the diagonal).
 template <int B>
 __device__ __forceinline__ void cheb_iterate_end(float (&er)[2], float (&ee)[2], float (&ed)[2], const int (&erow)[2],
                                                  const uint32_t (&epub)[2], const uint32_t (&ewin)[2],
-                                                 const uint32_t (&ekb)[2], const float (&ea1w)[2],
-                                                 const float (&eiw)[2], int its, float sigma, float inv2d,
-                                                 uint32_t bufb) {
+                                                 const uint32_t (&ekb)[2], const float (&eiw)[2], int its,
+                                                 float sigma, float inv2d, uint32_t bufb) {
   constexpr int W = 2 * B + 1;
   float rho_old = 1.f / sigma;
   for (int it = 0; it < its; ++it) {
@@ -809,7 +879,7 @@ __device__ __forceinline__ void cheb_iterate_end(float (&er)[2], float (&ee)[2],
 #pragma unroll
     for (int s2 = 0; s2 < 2; ++s2) {
       if (erow[s2] < 0) continue;
-      float acc = ea1w[s2] * ed[s2];
+      float acc = 0.f;
 #pragma unroll
       for (int o = 0; o < W; ++o)
         acc = __fmaf_rn(lds_f32(ekb[s2] + 4u * o), o == B ? ed[s2] : lds_f32(ewin[s2] + boff + 4u * o), acc);
@@ -840,48 +910,49 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
   float delta = 0.5f * (lmax - lmin);
   if (!(delta > 0.f)) delta = 1e-30f * theta;
   const float sigma = theta / delta, inv2d = 2.f / delta, c0 = 1.f / theta;
-  int its = cheb_iterations(a1.hi, a2.hi, mu_max, 2.384185791015625e-07f);   // 2^-22 per pass
+  const float kappa = lmax / lmin;
+  const float sk = sqrtf(kappa), crho = (sk - 1.f) / (sk + 1.f);
+  int its = cheb_iterations(a1.hi, a2.hi, mu_max, 2.384185791015625e-07f);   // 2^-22 for a first pass
   const bool ok = (lmin > 0.f) && its < 100000;
   if (its > 4096) its = 4096;
-  const float rho_pass = 4.f * fmaxf(2.384185791015625e-07f, (lmax / lmin) * 5.960464477539063e-08f);
+  float bound = cheb_pass_bound(crho, its, kappa);
 
-  // ---- stage q (and the warm start), zero the end regions, end-row coefficients.  Loads are
-  // issued in groups of eight before the stores so that their latencies overlap.
+  // ---- stage q, the warm start, the stencil and the end rows (double-float) with async copies
   const int reg0 = 2 * B * L.tint;               // lead region: slot B + row
   const int reg1 = reg0 + kChebRegion;           // tail region: slot B + row - e0 (tact > 0)
   const int trash = reg1 + kChebRegion;          // written by threads without rows, never read
   const bool warm = x0 != nullptr;
-  for (int i = tid; i < n; i += 8 * T) {
-    float2 v[8], u[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const int ii = i + g * T;
-      v[g] = ii < n ? qg[ii] : make_float2(0.f, 0.f);
-      u[g] = (warm && ii < n) ? x0[ii] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      const int ii = i + g * T;
-      if (ii < n) {
-        sm.q[ii] = v[g];
-        if (warm) x[ii] = u[g];
-      }
-    }
+  for (int i = tid; i < n; i += T) {
+    cp_async8(sm.q + i, qg + i);
+    if (warm) cp_async8(x + i, x0 + i);
+  }
+  if (tid < W) cp_async8(sm.st + tid, k.stencil + tid);
+  for (int c = tid; c < L.nend * W; c += T) {
+    const int slot = c / W, o = c - slot * W;
+    const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
+    const float2* src = row < k.nlead ? k.rows + row * W + o
+                        : row >= n - k.ntail ? k.rows + (k.nlead + row - (n - k.ntail)) * W + o
+                                             : k.stencil + o;
+    cp_async8(sm.kbd + c, src);
   }
   for (int c = tid; c < 4 * kChebRegion; c += T)
     sm.halo[(c / (2 * kChebRegion)) * sm.S + reg0 + c % (2 * kChebRegion)] = 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+  // FP32 operator rows of the end rows: a2 K + a1 omega on the diagonal, zero outside [0, n)
   for (int c = tid; c < L.nend * W; c += T) {
     const int slot = c / W, o = c - slot * W;
     const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
     const int j = row + o - B;
-    sm.kb[c] = (j >= 0 && j < n) ? a2.hi * kc_entry(k, row, o - B).x : 0.f;
+    float v = (j >= 0 && j < n) ? a2.hi * sm.kbd[c].x : 0.f;
+    if (o == B) v += a1.hi * kc_omega(k, row).x;
+    sm.kb[c] = v;
   }
   __syncthreads();
 
   const uint32_t hbase = static_cast<uint32_t>(__cvta_generic_to_shared(sm.halo));
   const uint32_t bufb = 4u * static_cast<uint32_t>(sm.S);
   if (trace && tid == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveFactor, t - tsub); tsub = t; }
-  float prev = 0.f;
   bool fail = false;
 
   if (tid < L.tint) {
@@ -889,14 +960,13 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
     const bool active = tid < L.tact;
     const int i0 = k.nlead + tid * R;
     const uint32_t kstr = 4u * static_cast<uint32_t>(L.tint);
+    const float a1in = a1.hi * k.omega_in.x, iwin = k.inv_omega_in;
     float2 nst[W];
 #pragma unroll
     for (int o = 0; o < W; ++o) {
-      const float v = -a2.hi * k.stencil[o].x;
+      const float v = -(a2.hi * sm.st[o].x + (o == B ? a1in : 0.f));
       nst[o] = make_float2(v, v);
     }
-    const float a1in = a1.hi * k.omega_in.x, iwin = k.inv_omega_in;
-    const float2 na1w2 = make_float2(-a1in, -a1in);
     const dfloat a1w_in = df_mul(a1, dfloat{k.omega_in.x, k.omega_in.y});
     // where the first / last B values are published and the halos read; the outer interior
     // threads use the end regions, threads without rows a trash slot and the zero slots
@@ -927,32 +997,45 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
       }
     }
     float r[R], e[R], w[NW];
-    for (int pass = 0; pass < 5; ++pass) {
+    for (int pass = 0; pass < 6; ++pass) {
       const bool cold0 = !warm && pass == 0;
       unsigned long long tp = trace ? global_ns() : 0ull;
-      // residual of the current iterate (double-float), rounded to FP32
-#pragma unroll
-      for (int j = 0; j < R; ++j) r[j] = 0.f;
+      // residual of the current iterate (double-float), rounded to FP32, through sm.rs: the
+      // row loop stays rolled (a fully unrolled one is tens of KB of code, fetched anew on
+      // every pass)
       if (active) {
         if (cold0) {
-#pragma unroll
-          for (int j = 0; j < R; ++j) { const float2 qq = sm.q[i0 + j]; r[j] = qq.x + qq.y; }
+#pragma unroll 1
+          for (int j = 0; j < R; ++j) { const float2 qq = sm.q[i0 + j]; sm.rs[i0 + j] = qq.x + qq.y; }
         } else {
           float2 sdf[W];
 #pragma unroll
-          for (int o = 0; o < W; ++o) sdf[o] = k.stencil[o];
-          float2 xw[R + 2 * B];
+          for (int o = 0; o < W; ++o) sdf[o] = sm.st[o];
+#pragma unroll 1
+          for (int m = 0; m < R / 2; ++m) {
+            const int i = i0 + 2 * m;
+            float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+            float2 xa = x[i - B];
 #pragma unroll
-          for (int t = 0; t < R + 2 * B; ++t) xw[t] = x[i0 - B + t];
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            float s = 0.f, c = 0.f;
-#pragma unroll
-            for (int o = 0; o < W; ++o) df_dot_acc(s, c, sdf[o], xw[j + o]);
-            r[j] = df_residual_finish(s, c, a1w_in, a2, xw[j + B], sm.q[i0 + j]);
+            for (int o = 0; o < W; ++o) {
+              const float2 xb = x[i - B + o + 1];
+              df2_dot_acc(s, c, sdf[o], make_float2(xa.x, xb.x), make_float2(xa.y, xb.y));
+              xa = xb;
+            }
+            const float2 x0v = x[i], x1v = x[i + 1], q0 = sm.q[i], q1 = sm.q[i + 1];
+            const df2 kx = df2_two_sum(s, c);
+            const df2 ax = df2_add(df2_mul_s(a2, kx),
+                                   df2_mul_s(a1w_in, df2{make_float2(x0v.x, x1v.x), make_float2(x0v.y, x1v.y)}));
+            const df2 rr = df2_add(df2{make_float2(q0.x, q1.x), make_float2(q0.y, q1.y)},
+                                   df2{make_float2(-ax.hi.x, -ax.hi.y), make_float2(-ax.lo.x, -ax.lo.y)});
+            const float2 rv = __fadd2_rn(rr.hi, rr.lo);
+            sm.rs[i] = rv.x;
+            sm.rs[i + 1] = rv.y;
           }
         }
       }
+#pragma unroll
+      for (int j = 0; j < R; ++j) r[j] = active ? sm.rs[i0 + j] : 0.f;
       if (trace) {
         bar_sync_all();
         if (tid == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveResidual, t - tp); tp = t; }
@@ -961,23 +1044,27 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
       for (int j = 0; j < NW; ++j) w[j] = 0.f;
 #pragma unroll
       for (int j = 0; j < R; ++j) { e[j] = 0.f; w[OWN + j] = r[j] * iwin * c0; }
-      cheb_iterate_interior<B, R>(r, e, w, nst, na1w2, iwin, its, sigma, inv2d, pub_l, spl, pub_r, spr, src_l, str_l,
-                                  src_r, str_r, bufb);
+      cheb_iterate_interior<B, R>(r, e, w, nst, iwin, its, sigma, inv2d, pub_l, spl, pub_r, spr, src_l, str_l, src_r,
+                                  str_r, bufb);
       if (trace && tid == 0) atomicAdd(trace + kTrSolveInner, global_ns() - tp);
       // x += e (double-float), size of the correction and of the iterate
       float dmax = 0.f, xmax = 0.f;
       if (active) {
 #pragma unroll
+        for (int j = 0; j < R; ++j) sm.rs[i0 + j] = e[j];
+#pragma unroll 1
         for (int j = 0; j < R; ++j) {
+          const float ej = sm.rs[i0 + j];
           const float2 xo = cold0 ? make_float2(0.f, 0.f) : x[i0 + j];
-          const dfloat nx = df_add(dfloat{xo.x, xo.y}, dfloat{e[j], 0.f});
+          const dfloat nx = df_add(dfloat{xo.x, xo.y}, dfloat{ej, 0.f});
           x[i0 + j] = make_float2(nx.hi, nx.lo);
-          dmax = fmaxf(dmax, fabsf(e[j]));
+          dmax = fmaxf(dmax, fabsf(ej));
           xmax = fmaxf(xmax, fabsf(nx.hi));
-          if (!(fabsf(e[j]) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
+          if (!(fabsf(ej) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
         }
       }
-      const int stop = cheb_pass_end(dmax, xmax, prev, pass, rho_pass, sm.red, trace, tsub);
+      const int stop = cheb_pass_end(dmax, xmax, bound, its, pass, a1.hi, a2.hi, mu_max, crho, kappa, sm.red, trace,
+                                     tsub);
       if (stop) { fail = stop < 0; break; }
     }
   } else {
@@ -985,7 +1072,8 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
     const int lane = tid - L.tint;
     int erow[2] = {-1, -1};
     uint32_t epub[2] = {0u, 0u}, ewin[2] = {0u, 0u}, ekb[2] = {0u, 0u};
-    float ea1w[2] = {0.f, 0.f}, eiw[2] = {0.f, 0.f};
+    int eslot[2] = {0, 0};
+    float eiw[2] = {0.f, 0.f};
     dfloat ea1wd[2] = {{0.f, 0.f}, {0.f, 0.f}};
     const uint32_t kbase = static_cast<uint32_t>(__cvta_generic_to_shared(sm.kb));
 #pragma unroll
@@ -994,8 +1082,8 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
       if (slot < L.nend) {
         const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
         erow[s2] = row;
+        eslot[s2] = slot;
         const float2 om = kc_omega(k, row);
-        ea1w[s2] = a1.hi * om.x;
         ea1wd[s2] = df_mul(a1, dfloat{om.x, om.y});
         eiw[s2] = kc_inv_omega(k, row);
         const int ps = (L.tact == 0 || row < k.nlead) ? reg0 + B + row : reg1 + B + (row - L.e0);
@@ -1005,7 +1093,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
       }
     }
     float er[2], ee[2], ed[2];
-    for (int pass = 0; pass < 5; ++pass) {
+    for (int pass = 0; pass < 6; ++pass) {
       const bool cold0 = !warm && pass == 0;
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2) {
@@ -1017,9 +1105,11 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
           er[s2] = qq.x + qq.y;
         } else {
           float s = 0.f, c = 0.f;
+          const float2* kr = sm.kbd + eslot[s2] * W;
+#pragma unroll
           for (int o = 0; o < W; ++o) {
             const int j = row + o - B;
-            if (j >= 0 && j < n) df_dot_acc(s, c, kc_entry(k, row, o - B), x[j]);
+            if (j >= 0 && j < n) df_dot_acc(s, c, kr[o], x[j]);
           }
           er[s2] = df_residual_finish(s, c, ea1wd[s2], a2, x[row], sm.q[row]);
         }
@@ -1027,7 +1117,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
       if (trace) bar_sync_all();
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2) { ee[s2] = 0.f; ed[s2] = er[s2] * eiw[s2] * c0; }
-      cheb_iterate_end<B>(er, ee, ed, erow, epub, ewin, ekb, ea1w, eiw, its, sigma, inv2d, bufb);
+      cheb_iterate_end<B>(er, ee, ed, erow, epub, ewin, ekb, eiw, its, sigma, inv2d, bufb);
       float dmax = 0.f, xmax = 0.f;
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2) {
@@ -1040,7 +1130,8 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
         xmax = fmaxf(xmax, fabsf(nx.hi));
         if (!(fabsf(ee[s2]) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
       }
-      const int stop = cheb_pass_end(dmax, xmax, prev, pass, rho_pass, sm.red, trace, tsub);
+      const int stop = cheb_pass_end(dmax, xmax, bound, its, pass, a1.hi, a2.hi, mu_max, crho, kappa, sm.red, trace,
+                                     tsub);
       if (stop) { fail = stop < 0; break; }
     }
   }
@@ -1198,10 +1289,13 @@ __device__ inline SolverStore solver_bind(int mode, float* fbase, float* gbase, 
   s.F = s.X = nullptr;
   if (mode == 3) {
     s.ch.q = reinterpret_cast<float2*>(fbase);
+    s.ch.kbd = s.ch.q + n;
+    s.ch.st = s.ch.kbd + kChebEndMax * 15;
     s.ch.S = cheb_buffer_floats(b, static_cast<int>(blockDim.x) - 32);
-    s.ch.halo = fbase + 2 * static_cast<size_t>(n);
+    s.ch.halo = reinterpret_cast<float*>(s.ch.st + 16);
     s.ch.kb = s.ch.halo + 2 * s.ch.S;
-    s.ch.red = s.ch.kb + kChebEndMax * 15;
+    s.ch.rs = s.ch.kb + kChebEndMax * 15;
+    s.ch.red = s.ch.rs + n;
   } else if (mode == 0) {
     s.cr = cr_bind(fbase, n, b);
     s.F = s.cr.F;
