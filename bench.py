@@ -5,7 +5,10 @@ eps = 0.01, S = 2, dt = 1e-3, up to 50 modes, seeded rank-8 cosine initial condi
 "step" is one full time step of the CTD solver (greedy enrichment with fixed-point sweeps and
 the full-grid nonlinear contraction), launched through the C ABI.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference]
+
+The headline is the mixed form (split-BF16 tensor-core contraction, FP64-accurate solves,
+Gram products and energy); the plain FP64 form is timed beside it ("compare").
 
 Prints one JSON line.  Under torchrun (N > 1) every rank advances its own replica (weak
 scaling, no collective on the data path); rank 0 prints.
@@ -168,12 +171,80 @@ def replica_units(steps: int, world: int) -> int:
 def algorithmic_flops(w, precision: str, Mk: int, half_sweeps: int) -> float:
     """Work of the nonlinear contraction per launch (the method's own arithmetic):
     FP64 path: materialising w(u^k) (2 Mk N flops, once per step) + one FP64 multiply-add per
-    grid point and half-sweep; tensor-core path: the rank-Mk reconstruction 2 Mk N per
-    half-sweep (one pass, before the 3-product split)."""
+    grid point and half-sweep; tensor-core path: the rank-Mk reconstruction of the split
+    operands, 2 (3 Mk) N per half-sweep."""
     N = float(w.grid_points)
     if precision == "fp64":
         return 2.0 * Mk * N * (w.dim - 1) + half_sweeps * 2.0 * N
-    return half_sweeps * 2.0 * Mk * N
+    return half_sweeps * 2.0 * 3 * Mk * N
+
+
+def contraction_roof_us(w, Mk: float, pk: dict) -> dict:
+    """Roofline time of one half-sweep's tensor-core contraction: the larger of the split
+    reconstruction on the tensor cores (2 * 3Mk * N flops at the sustained BF16 peak) and the
+    fused epilogue on the FP32 pipes (3 instructions per grid point: u*u, fma for u^3 - u, fma
+    into the weighted row sum; 152 SMs x 128 lanes x the SM clock)."""
+    N = float(w.grid_points)
+    t_tensor = 2.0 * 3 * Mk * N / (pk["bf16_tflops_sustained"] * 1e12)
+    lanes_per_s = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+    t_alu = 3.0 * N / lanes_per_s
+    bound = "tensor" if t_tensor >= t_alu else "alu"
+    return {"roof_us": 1e6 * max(t_tensor, t_alu), "bound": bound, "tensor_us": 1e6 * t_tensor, "alu_us": 1e6 * t_alu}
+
+
+def source_hash() -> str:
+    """Digest of the CUDA sources and the C ABI header (ties stored ncu counters to a build)."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in ("paper_2410_15519_gb300/csrc", "include"):
+        for f in sorted(os.listdir(os.path.join(ROOT, d))):
+            if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+                h.update(f.encode())
+                h.update(open(os.path.join(ROOT, d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu capture, if it was taken
+    on the current sources (else None)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(f"{workload}/{precision}")
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def timed_run(ctd, torch, w, precision, steps, warmup, flush, clocks=None):
+    """Advance `steps` time steps after `warmup`; one step kernel launch each, bracketed by CUDA
+    events on the solver's stream, L2 flushed between steps."""
+    prec = ctd.PREC_FP64 if precision == "fp64" else ctd.PREC_SPLIT_BF16
+    solver = ctd.Solver(ctd.config_from_workload(w, precision=prec))
+    stream = solver.stream
+    solver.set_initial_modes(workloads.initial_modes(w))
+    for _ in range(warmup):
+        solver.step(1, stats=False)
+    torch.cuda.synchronize()
+    rank0 = solver.get_modes()[0].shape[1]
+    if clocks:
+        clocks.start()
+    times_ms, stats = [], []
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = solver.step(1)[0]
+        ev1.record(stream)
+        ev1.synchronize()
+        times_ms.append(ev0.elapsed_time(ev1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    return solver, times_ms, stats, rank0, clk
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -184,48 +255,28 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build.build()
     w = workloads.preset(args.workload, seed=workloads.preset(args.workload).seed + rank)
-    prec = ctd.PREC_FP64 if args.precision == "fp64" else ctd.PREC_SPLIT_BF16
-    cfg = ctd.config_from_workload(w, precision=prec)
-    solver = ctd.Solver(cfg)
-    stream = solver.stream
-    A0 = workloads.initial_modes(w)
-    solver.set_initial_modes(A0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        solver.step(1, stats=False)
-    torch.cuda.synchronize()
-    rank0 = solver.get_modes()[0].shape[1]
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank)
-    clocks.start()
-    times_ms, stats, flops = [], [], 0.0
-    torch.cuda.synchronize()
+    solver, times_ms, stats, rank0, clk = timed_run(ctd, torch, w, args.precision, args.steps, args.warmup, flush,
+                                                     clocks)
     if world > 1:
         torch.distributed.barrier()
-    Mk = None
-    for k in range(args.steps):
-        flush.zero_()                                   # evict L2 between timed steps
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        st = solver.step(1)[0]                          # one launch of the step kernel
-        ev1.record(stream)
-        ev1.synchronize()
-        times_ms.append(ev0.elapsed_time(ev1))
-        stats.append(st)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
     total_ms = max_over_ranks(sum(times_ms), world)
     # rank of u^k entering each timed step: the previous step's output rank
     ranks_in = [rank0] + [st["modes"] for st in stats[:-1]]
-    for st, mk in zip(stats, ranks_in):
-        flops += algorithmic_flops(w, args.precision, mk, st["als_sweeps"] * w.dim)
-    per_launch_ms = total_ms / args.steps
-    out = dict(times_ms=times_ms, total_ms=total_ms, per_launch_ms=per_launch_ms, stats=stats, clocks=clk,
-               flops_per_launch=flops / args.steps)
+    flops = sum(algorithmic_flops(w, args.precision, mk, st["als_sweeps"] * w.dim) for st, mk in zip(stats, ranks_in))
+    out = dict(times_ms=times_ms, total_ms=total_ms, per_launch_ms=total_ms / args.steps, stats=stats, clocks=clk,
+               flops_per_launch=flops / args.steps, mk_mean=sum(ranks_in) / len(ranks_in))
+    # per-phase device time of a few more steps (global-timer trace of CTA 0)
+    solver.trace(True)
+    tr_steps = 3
+    st_tr = solver.step(tr_steps)
+    tr = solver.trace(False)
+    hs = sum(s["als_sweeps"] for s in st_tr) * w.dim
+    out["phase_us_per_half_sweep"] = {k: 1e6 * v / max(1, hs) for k, v in tr.items()
+                                      if k in ("gram_contract", "gram", "contract", "rhs", "solve", "converge")}
     # end to end through the C ABI with host buffers: H2D of u^k, step, D2H of u^{k+1}
     n_e2e = min(args.steps, args.e2e_steps)
     modes_host = solver.get_modes()
@@ -233,7 +284,7 @@ def run_gpu(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for k in range(n_e2e):
         bi += sum(m.nbytes for m in modes_host)
-        solver.set_initial_modes(modes_host, first_step=args.warmup + args.steps + k)
+        solver.set_initial_modes(modes_host, first_step=args.warmup + args.steps + tr_steps + k)
         solver.step(1)
         modes_host = solver.get_modes()
         bo += sum(m.nbytes for m in modes_host)
@@ -242,11 +293,23 @@ def run_gpu(args, rank, world, local_rank):
     out["e2e"] = dict(steps=n_e2e, seconds=e2e_s, h2d=bi / max(1, n_e2e), d2h=bo / max(1, n_e2e))
     solver.close()
     # first-step result from the initial condition (accuracy check against the oracle)
-    s2 = ctd.Solver(cfg)
-    s2.set_initial_modes(A0)
+    prec = ctd.PREC_FP64 if args.precision == "fp64" else ctd.PREC_SPLIT_BF16
+    s2 = ctd.Solver(ctd.config_from_workload(w, precision=prec))
+    s2.set_initial_modes(workloads.initial_modes(w))
     s2.step(1)
     out["first_step_modes"] = s2.get_modes()
     s2.close()
+    # the other arithmetic side by side (the mixed form against the plain FP64 form)
+    if args.compare_steps > 0 and rank == 0:
+        other = "fp64" if args.precision == "mixed" else "mixed"
+        s3, t3, st3, _, _ = timed_run(ctd, torch, w, other, args.compare_steps, args.warmup, flush)
+        s3.close()
+        s4 = ctd.Solver(ctd.config_from_workload(w, precision=ctd.PREC_FP64 if other == "fp64" else ctd.PREC_SPLIT_BF16))
+        s4.set_initial_modes(workloads.initial_modes(w))
+        s4.step(1)
+        out["compare"] = dict(precision=other, steps=len(t3), ms_per_step=sum(t3) / len(t3),
+                              als_sweeps_per_step=[s["als_sweeps"] for s in st3], first_step_modes=s4.get_modes())
+        s4.close()
     return w, out
 
 
@@ -256,9 +319,11 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="c1")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--compare-steps", type=int, default=10,
+                    help="steps of the other arithmetic (FP64 vs mixed) timed for the side-by-side numbers")
     ap.add_argument("--oracle-budget", type=float, default=25.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -270,6 +335,7 @@ def main():
     config = {"workload": f"{w.name}: {w.dim}D {'x'.join(map(str, w.n))} nodes, s={w.s} p={w.p}, eps={w.eps}, "
                           f"S={w.S}, dt={w.dt}, M_max={w.M_max}, tol_als={w.tol_als}, tol_enrich={w.tol_enrich}",
               "grid_points": w.grid_points, "ic": f"rank-{w.ic_rank} seeded cosine modes",
+              "precision": args.precision,
               "l2": "256 MB buffer written between timed steps (L2 flush)"}
 
     if args.impl == "reference":
@@ -303,9 +369,10 @@ def main():
     pk, pk_kind = peaks()
     value = replica_units(args.steps, world) / (res["total_ms"] / 1e3)
     achieved = res["flops_per_launch"] / (res["per_launch_ms"] / 1e3) / 1e12
+    traffic = stored_traffic(args.workload, args.precision)
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None,
+                "frac": achieved / 1.25, "traffic": traffic,
                 "peak_kind": "nominal FP64 rate of the part (152 SMs x 2 FP64 FMA/clk x ~2.07 GHz); "
                              "measured 1.0 TFLOP/s by a throughput probe",
                 "kernel": "ctd::step_kernel (whole persistent time step)"}
@@ -313,10 +380,11 @@ def main():
     else:
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_kind": f"bf16 sustained, {pk_kind}",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": f"bf16 sustained, {pk_kind} (of measured)",
                 "kernel": "ctd::step_kernel (whole persistent time step)"}
         dtype = "bf16x3-split/f32-acc; solves, Gram products, energy FP64-accurate"
     e2e = res["e2e"]
+    ph = res["phase_us_per_half_sweep"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config,
@@ -324,9 +392,23 @@ def main():
             "modes_per_step": [s["modes"] for s in res["stats"]],
             "als_sweeps_per_step": [s["als_sweeps"] for s in res["stats"]],
             "half_sweeps_per_s": sum(s["als_sweeps"] for s in res["stats"]) * wk.dim / (res["total_ms"] / 1e3),
+            "phase_us_per_half_sweep": ph,
             "roofline": roof, "clocks": res["clocks"], "gpu_launches": args.steps,
             "e2e": {"value": world * e2e["steps"] / e2e["seconds"], "unit": UNIT,
                     "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"])}}
+    if args.precision == "mixed" and ph.get("contract"):
+        cr = contraction_roof_us(wk, res["mk_mean"], pk)
+        line["contraction_roofline"] = {
+            "phase_us": ph["contract"], "roof_us": cr["roof_us"], "bound": cr["bound"],
+            "frac": cr["roof_us"] / ph["contract"], "tensor_us": cr["tensor_us"], "alu_us": cr["alu_us"],
+            "note": "one half-sweep's tensor-core contraction as timed by CTA 0's global-timer trace "
+                    "(until its own tiles are done); roof = max(split MMA at sustained BF16 peak, "
+                    "3 FP32 instructions per grid point)"}
+    if "compare" in res:
+        c = res["compare"]
+        line["compare"] = {"precision": c["precision"], "steps": c["steps"], "ms_per_step": c["ms_per_step"],
+                           "value": 1e3 / c["ms_per_step"], "unit": UNIT,
+                           "als_sweeps_per_step": c["als_sweeps_per_step"]}
     if not args.no_cpu_baseline:
         ores, omodes = run_oracle(args.workload, 1, args.oracle_budget)
         tv = ores["steps"] / sum(ores["times"])
@@ -336,6 +418,9 @@ def main():
         if omodes is not None:
             from oracle import ctd as octd
             line["first_step_err_u_vs_oracle"] = octd.rel_l2_between(res["first_step_modes"], omodes)
+            if "compare" in res:
+                line["compare"]["first_step_err_u_vs_oracle"] = octd.rel_l2_between(res["compare"]["first_step_modes"],
+                                                                                    omodes)
     print(json.dumps(line))
 
 
