@@ -263,6 +263,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
   trace_mark(P, tmark, kTrPrologue);
 
   int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0;
+  double amp0 = 0.0;   // amplitude max|(x)v| of the step's leading mode
   bool stopped = false;
   const int n_modes = P.fixed_modes > 0 ? P.fixed_modes : P.M_max;
   const int n_it = P.fixed_als > 0 ? P.fixed_als : P.I_max;
@@ -357,16 +358,20 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
         __syncthreads();
       }
       if (P.fixed_als == 0 && delta <= P.tol_als) break;
-      // Tensor-core arithmetic: the contraction's FP32 rounding sets a floor on the relative
-      // change of a small mode; once the change is below 1e-6 and no longer decreasing,
-      // further sweeps only move the mode within that floor.
-      if (P.precision != 0 && P.fixed_als == 0 && it >= 3 && delta <= 1e-6 && delta >= 0.5 * delta_prev) {
+      // Tensor-core arithmetic: the contraction's FP32 rounding sets a floor on how far a mode
+      // can still move.  Once the change of the mode, measured against the step's leading mode
+      // (delta * amp against amp_lead; delta alone for the leading mode), is below 1e-6 and
+      // no longer shrinking, further sweeps only move the mode within that floor.
+      const double amp_lead = m == 0 ? amp : amp0;
+      if (P.precision != 0 && P.fixed_als == 0 && it >= 3 && delta * amp <= 1e-6 * amp_lead &&
+          delta >= 0.5 * delta_prev) {
         delta = P.tol_als;
         break;
       }
       delta_prev = delta;
     }
     if (it > n_it) it = n_it;
+    if (m == 0) amp0 = amp;
     sweeps_max = max(sweeps_max, it);
     if (!zero_mode && P.fixed_als == 0 && !(delta <= P.tol_als)) not_conv = 1;
     if (zero_mode) amp = 0.0;

@@ -34,12 +34,19 @@ __device__ __forceinline__ dfloat df_of(double x) { return df_from_double(x); }
 
 // K v at row i of dimension d (double-float), K read from the compressed band
 __device__ inline dfloat kv_row(const KCompressed& k, const float2* v, int i) {
-  dfloat acc = {0.f, 0.f};
-  const int j0 = max(0, i - k.b), j1 = min(k.n - 1, i + k.b);
-  for (int j = j0; j <= j1; ++j) {
-    const float2 kij = kc_entry(k, i, j - i);
-    acc = df_fma(acc, dfloat{kij.x, kij.y}, ld_df(v + j));
+  constexpr int kW = 2 * 7 + 1;   // widest band (s = 3)
+  float2 kv[kW], vv[kW];
+#pragma unroll
+  for (int o = 0; o < kW; ++o) {   // all loads first, so that their latencies overlap
+    const int j = i + o - k.b;
+    const bool ok = o <= 2 * k.b && j >= 0 && j < k.n;
+    kv[o] = ok ? kc_entry(k, i, o - k.b) : make_float2(0.f, 0.f);
+    vv[o] = ok ? v[j] : make_float2(0.f, 0.f);
   }
+  dfloat acc = {0.f, 0.f};
+#pragma unroll
+  for (int o = 0; o < kW; ++o)
+    if (o <= 2 * k.b) acc = df_fma(acc, dfloat{kv[o].x, kv[o].y}, dfloat{vv[o].x, vv[o].y});
   return acc;
 }
 
@@ -109,19 +116,24 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
         const int s = g + k * groups;
         if (s >= nslots) break;
         dfloat a = acc[k];
-        if (s == 0) {
-          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sv + i - c0), ld_df(sdv + i - c0));
-        } else if (s == 1) {
-          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sv + i - c0), ld_df(skv + i - c0));
-        } else if (s < 2 + M) {
-          const float2* col = dd.bank[cb] + static_cast<size_t>(s - 2) * dd.n;
-          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sdv + i - c0), ld_df(col + i));
-        } else if (s < 2 + 2 * M) {
-          const float2* col = dd.KB + static_cast<size_t>(s - 2 - M) * dd.n;
-          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sv + i - c0), ld_df(col + i));
-        } else {
-          const float2* col = dd.bank[pb] + static_cast<size_t>(s - 2 - 2 * M) * dd.n;
-          for (int i = c0 + lane; i < c1; i += tp) a = df_fma(a, ld_df(sdv + i - c0), ld_df(col + i));
+        // the slot's two vectors: shared-memory staging (v, omega v, K v) or a factor column
+        const float2 *lhs, *rhs;
+        if (s == 0) { lhs = sv; rhs = sdv; }
+        else if (s == 1) { lhs = sv; rhs = skv; }
+        else if (s < 2 + M) { lhs = sdv; rhs = dd.bank[cb] + static_cast<size_t>(s - 2) * dd.n + c0; }
+        else if (s < 2 + 2 * M) { lhs = sv; rhs = dd.KB + static_cast<size_t>(s - 2 - M) * dd.n + c0; }
+        else { lhs = sdv; rhs = dd.bank[pb] + static_cast<size_t>(s - 2 - 2 * M) * dd.n + c0; }
+        for (int i = lane; i < c1 - c0; i += 4 * tp) {
+          float2 l4[4], r4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {   // four rows' loads first, so that their latencies overlap
+            const int ii = i + u * tp;
+            const bool ok = ii < c1 - c0;
+            l4[u] = ok ? lhs[ii] : make_float2(0.f, 0.f);
+            r4[u] = ok ? rhs[ii] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a = df_fma(a, dfloat{l4[u].x, l4[u].y}, dfloat{r4[u].x, r4[u].y});
         }
         acc[k] = a;
       }
