@@ -299,18 +299,52 @@ def run_gpu(args, rank, world, local_rank):
     s2.step(1)
     out["first_step_modes"] = s2.get_modes()
     s2.close()
-    # the other arithmetic side by side (the mixed form against the plain FP64 form)
+    # the other arithmetic side by side (the mixed form against the plain FP64 form): its speed,
+    # and both forms advanced K steps from the initial condition (field error, energy law)
     if args.compare_steps > 0 and rank == 0:
         other = "fp64" if args.precision == "mixed" else "mixed"
         s3, t3, st3, _, _ = timed_run(ctd, torch, w, other, args.compare_steps, args.warmup, flush)
         s3.close()
-        s4 = ctd.Solver(ctd.config_from_workload(w, precision=ctd.PREC_FP64 if other == "fp64" else ctd.PREC_SPLIT_BF16))
-        s4.set_initial_modes(workloads.initial_modes(w))
-        s4.step(1)
+        traj = {}
+        for prec_name in (args.precision, other):
+            sv = ctd.Solver(ctd.config_from_workload(
+                w, precision=ctd.PREC_FP64 if prec_name == "fp64" else ctd.PREC_SPLIT_BF16))
+            sv.set_initial_modes(workloads.initial_modes(w))
+            energies = [sv.energy()]
+            first = None
+            for k in range(args.compare_steps):
+                sv.step(1)
+                energies.append(sv.energy())
+                if k == 0:
+                    first = sv.get_modes()
+            traj[prec_name] = dict(modes=sv.get_modes(), energies=energies, first=first)
+            sv.close()
+        mixed, fp64 = traj["mixed"], traj["fp64"]
         out["compare"] = dict(precision=other, steps=len(t3), ms_per_step=sum(t3) / len(t3),
-                              als_sweeps_per_step=[s["als_sweeps"] for s in st3], first_step_modes=s4.get_modes())
-        s4.close()
+                              als_sweeps_per_step=[s["als_sweeps"] for s in st3],
+                              first_step_modes=traj[other]["first"],
+                              u_rel_l2_mixed_vs_fp64=sep_rel_l2(mixed["modes"], fp64["modes"]),
+                              energy_rel_diff_mixed_vs_fp64=abs(mixed["energies"][-1] - fp64["energies"][-1]) /
+                              abs(fp64["energies"][-1]),
+                              energy_nonincreasing={k: all(e1 <= e0 + 1e-10 * abs(e0) for e0, e1 in
+                                                           zip(v["energies"], v["energies"][1:]))
+                                                    for k, v in traj.items()},
+                              energy_first_last={k: [v["energies"][0], v["energies"][-1]] for k, v in traj.items()})
     return w, out
+
+
+def sep_rel_l2(A, B):
+    """Relative nodal L2 distance ||u_A - u_B|| / ||u_B|| of two separated fields (factor d of
+    field X: n_d x rank array), from their grid values rebuilt in FP64 on the GPU (a Gram-matrix
+    form would cancel catastrophically at the differences measured here)."""
+    import torch
+    def grid(X):
+        t = [torch.as_tensor(x, dtype=torch.float64, device="cuda") for x in X]
+        if len(t) == 2:
+            return t[0] @ t[1].T
+        return torch.einsum("im,jm,km->ijk", *t)
+    ua, ub = grid(A), grid(B)
+    return float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub))
 
 
 def main():
@@ -408,7 +442,12 @@ def main():
         c = res["compare"]
         line["compare"] = {"precision": c["precision"], "steps": c["steps"], "ms_per_step": c["ms_per_step"],
                            "value": 1e3 / c["ms_per_step"], "unit": UNIT,
-                           "als_sweeps_per_step": c["als_sweeps_per_step"]}
+                           "als_sweeps_per_step": c["als_sweeps_per_step"],
+                           "u_rel_l2_mixed_vs_fp64": c["u_rel_l2_mixed_vs_fp64"],
+                           "energy_rel_diff_mixed_vs_fp64": c["energy_rel_diff_mixed_vs_fp64"],
+                           "energy_nonincreasing": c["energy_nonincreasing"],
+                           "energy_first_last": c["energy_first_last"],
+                           "note": f"both forms advanced {args.compare_steps} steps from the initial condition"}
     if not args.no_cpu_baseline:
         ores, omodes = run_oracle(args.workload, 1, args.oracle_budget)
         tv = ores["steps"] / sum(ores["times"])
