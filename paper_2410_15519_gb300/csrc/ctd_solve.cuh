@@ -840,7 +840,15 @@ __device__ __forceinline__ void cheb_iterate_interior(float (&r)[R], float (&e)[
     for (int m = 0; m < R / 2; ++m) {
       float2 acc = make_float2(r[2 * m], r[2 * m + 1]);
 #pragma unroll
-      for (int o = 0; o < W; ++o) acc = __ffma2_rn(nst[o], make_float2(w[2 * m + 1 + o], w[2 * m + 2 + o]), acc);
+      // symmetric stencil: the pair sums d_{j-B+o} + d_{j+B-o} go through the adder, leaving
+      // B + 1 multiply-adds per row pair
+      acc = __ffma2_rn(nst[B], make_float2(w[2 * m + 1 + B], w[2 * m + 2 + B]), acc);
+#pragma unroll
+      for (int o = 0; o < B; ++o) {
+        const float2 sum = __fadd2_rn(make_float2(w[2 * m + 1 + o], w[2 * m + 2 + o]),
+                                      make_float2(w[2 * m + 1 + 2 * B - o], w[2 * m + 2 + 2 * B - o]));
+        acc = __ffma2_rn(nst[o], sum, acc);
+      }
       r[2 * m] = acc.x;
       r[2 * m + 1] = acc.y;
     }
@@ -961,10 +969,13 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
     const int i0 = k.nlead + tid * R;
     const uint32_t kstr = 4u * static_cast<uint32_t>(L.tint);
     const float a1in = a1.hi * k.omega_in.x, iwin = k.inv_omega_in;
+    // -(a1 omega + a2 K) stencil in FP32, symmetrised (K is symmetric; this operator only
+    // drives the inner iterations, the residual uses the stored double-float stencil)
     float2 nst[W];
 #pragma unroll
     for (int o = 0; o < W; ++o) {
-      const float v = -(a2.hi * sm.st[o].x + (o == B ? a1in : 0.f));
+      const int om = W - 1 - o;
+      const float v = o == B ? -(a2.hi * sm.st[o].x + a1in) : -(a2.hi * 0.5f * (sm.st[o].x + sm.st[om].x));
       nst[o] = make_float2(v, v);
     }
     const dfloat a1w_in = df_mul(a1, dfloat{k.omega_in.x, k.omega_in.y});
