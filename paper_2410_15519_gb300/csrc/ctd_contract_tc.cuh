@@ -236,14 +236,19 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
 __device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, int d, float* w, int npad) {
   const Dim& dd = P.d[d];
   const float s = static_cast<float>(4.0 * P.a0);
-  for (int i = threadIdx.x; i < npad; i += blockDim.x) {
-    float v = 0.f;
-    if (i < dd.n) {
-      const float2 x = dd.v[i];
-      const float2 om = kc_omega(kc, i);
-      v = s * om.x * (x.x + x.y);
+  constexpr int kGroup = 8;   // loads of eight entries first, so that their latencies overlap
+  for (int i0 = threadIdx.x; i0 < npad; i0 += kGroup * blockDim.x) {
+    float2 x[kGroup];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      const int i = i0 + g * blockDim.x;
+      x[g] = i < dd.n ? dd.v[i] : make_float2(0.f, 0.f);
     }
-    w[i] = v;
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+      const int i = i0 + g * blockDim.x;
+      if (i < npad) w[i] = i < dd.n ? s * kc_omega(kc, i).x * (x[g].x + x[g].y) : 0.f;
+    }
   }
 }
 
@@ -419,7 +424,10 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         wt = wl + (col0 - jm * td.n_last_pad);
         wscale = wm[jm];
       }
-      float at0 = 0.f, at1 = 0.f, at2 = 0.f, at3 = 0.f;
+      // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
+      // instruction; four interleaved sums (columns 0, 1, 2, 3 mod 4)
+      float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+      const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
       for (int q = 0; q < kTcN / 32; ++q) {
         float v[32];
@@ -432,14 +440,12 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const float4 ww = w4[c];
-          const float u0 = v[4 * c], u1 = v[4 * c + 1], u2 = v[4 * c + 2], u3 = v[4 * c + 3];
-          at0 = __fmaf_rn(u0 * __fmaf_rn(u0, u0, -1.f), ww.x, at0);
-          at1 = __fmaf_rn(u1 * __fmaf_rn(u1, u1, -1.f), ww.y, at1);
-          at2 = __fmaf_rn(u2 * __fmaf_rn(u2, u2, -1.f), ww.z, at2);
-          at3 = __fmaf_rn(u3 * __fmaf_rn(u3, u3, -1.f), ww.w, at3);
+          const float2 u01 = make_float2(v[4 * c], v[4 * c + 1]), u23 = make_float2(v[4 * c + 2], v[4 * c + 3]);
+          a01 = __ffma2_rn(__fmul2_rn(u01, __ffma2_rn(u01, u01, m1)), make_float2(ww.x, ww.y), a01);
+          a23 = __ffma2_rn(__fmul2_rn(u23, __ffma2_rn(u23, u23, m1)), make_float2(ww.z, ww.w), a23);
         }
       }
-      const float at = (at0 + at1) + (at2 + at3);
+      const float at = (a01.x + a01.y) + (a23.x + a23.y);
       tc_fence_before();
       mbar_arrive(&sh->acc_empty[ab]);
       acc = __fmaf_rn(wscale, at, acc);

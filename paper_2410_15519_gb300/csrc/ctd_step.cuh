@@ -242,6 +242,20 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
   const int groups = kThreads / tpr, g = threadIdx.x / tpr, lane = threadIdx.x % tpr;
   const dfloat ct = ld_df(&P.ct_df), ck = ld_df(&P.ck_df), L = ld_df(&P.L_df);
   const int C = P.rchunks[x];
+  // contraction partials per row block (tensor-core path): a slice of rows shorter than a
+  // block spans at most two row blocks; computed once (rb_lo < 0: per row)
+  int rb_lo = 0, cr_lo = 0, cr_hi = 0;
+  if (P.precision != 0) {
+    const TcDir& td = X.dirs[x];
+    const long long T = static_cast<long long>(td.nrb) * td.ntc;
+    rb_lo = lo / kTcM;
+    const int rb_hi = (hi - 1) / kTcM;
+    cr_lo = tile_owner(T, gridDim.x, static_cast<long long>(rb_lo) * td.ntc + td.ntc - 1) -
+            tile_owner(T, gridDim.x, static_cast<long long>(rb_lo) * td.ntc) + 1;
+    cr_hi = tile_owner(T, gridDim.x, static_cast<long long>(rb_hi) * td.ntc + td.ntc - 1) -
+            tile_owner(T, gridDim.x, static_cast<long long>(rb_hi) * td.ntc) + 1;
+    if (rb_hi > rb_lo + 1) rb_lo = -1;
+  }
   for (int i0 = lo; i0 < hi; i0 += groups) {
     const int i = i0 + g;
     const bool live = i < hi;
@@ -271,12 +285,24 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         R = df_of((r0 + r1) + (r2 + r3));
       } else {
         const TcDir& td = X.dirs[x];
-        const long long T = static_cast<long long>(td.nrb) * td.ntc;
         const int rb = i / kTcM;
-        const int Cr = tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
-                       tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc) + 1;
+        int Cr;
+        if (rb_lo < 0) {
+          const long long T = static_cast<long long>(td.nrb) * td.ntc;
+          Cr = tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
+               tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc) + 1;
+        } else {
+          Cr = rb == rb_lo ? cr_lo : cr_hi;
+        }
+        const float* rp = X.rpart32 + static_cast<size_t>(i) * td.cmax;
+        float part[8];   // loads first, so that their latencies overlap
+#pragma unroll
+        for (int k = 0; k < 8; ++k) part[k] = k < Cr ? rp[k] : 0.f;
         R = {0.f, 0.f};
-        for (int k = 0; k < Cr; ++k) R = df_add(R, dfloat{X.rpart32[static_cast<size_t>(i) * td.cmax + k], 0.f});
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k < Cr) R = df_add(R, dfloat{part[k], 0.f});
+        for (int k = 8; k < Cr; ++k) R = df_add(R, dfloat{rp[k], 0.f});
       }
       const float2 om2 = kc_omega(X.kc[x], i);
       const dfloat om = {om2.x, om2.y};
@@ -362,8 +388,22 @@ static __device__ __noinline__ void load_weights_fp64(const StepParams& P, const
   for (int d = 0; d < P.dim; ++d) {
     if (d == x) continue;
     const Dim& dd = P.d[d];
-    for (int i = threadIdx.x; i < dd.n; i += blockDim.x)
-      wv[d * kMaxN + i] = dd.omega[i] * f2_to_double(dd.v[i]);
+    constexpr int kGroup = 8;   // loads first, so that their latencies overlap
+    for (int i0 = threadIdx.x; i0 < dd.n; i0 += kGroup * blockDim.x) {
+      double om[kGroup];
+      float2 v[kGroup];
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g) {
+        const int i = i0 + g * blockDim.x;
+        om[g] = i < dd.n ? dd.omega[i] : 0.0;
+        v[g] = i < dd.n ? dd.v[i] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int g = 0; g < kGroup; ++g) {
+        const int i = i0 + g * blockDim.x;
+        if (i < dd.n) wv[d * kMaxN + i] = om[g] * f2_to_double(v[g]);
+      }
+    }
   }
   __syncthreads();
 }
