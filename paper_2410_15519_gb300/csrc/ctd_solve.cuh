@@ -602,7 +602,7 @@ __device__ inline float cta_max(float v, float* red) {
 //    __syncthreads and reads its halo back.  Interior rows go in pairs through the packed
 //    FP32x2 instructions of sm_100 and later.
 // Each pass solves for the correction of a double-float residual; passes repeat until the
-// correction falls below 2^-48 of the iterate.
+// remaining error is bounded by 2^-46 of the iterate.
 struct ChebLayout {
   int R;       // rows per interior thread
   int tint;    // interior threads (blockDim.x - 32)
@@ -774,7 +774,7 @@ __device__ __forceinline__ float cheb_pass_bound(float rho, int its, float kappa
 // End of a refinement pass, executed by every thread: CTA max of the correction and of the
 // iterate, trace, and the decision: 0 next pass (with `its` iterations), 1 converged, -1
 // non-finite values.  The error left after the pass is at most bound * dmax; the pass stops
-// the solve once that is below 2^-48 of the iterate, else the next pass gets just enough
+// the solve once that is below 2^-46 of the iterate, else the next pass gets just enough
 // iterations to get there (never fewer than the FP32 rounding floor allows).
 __device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& bound, int& its, int pass, float a1,
                                              float a2, float mu_max, float rho, float kappa, float* red,
@@ -798,9 +798,9 @@ __device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& boun
     tsub = t;
   }
   if (!(dmax <= 3.0e38f) || !(xmax <= 3.0e38f)) return -1;
-  const float lim = 3.552713678800501e-15f * xmax;   // 2^-48 of the iterate
+  const float lim = 1.4210854715202004e-14f * xmax;   // 2^-46 of the iterate
   if (dmax <= lim || bound * dmax <= lim) return 1;
-  const float need = lim / (4.f * bound * dmax);     // reduction the next pass must reach
+  const float need = lim / (2.f * bound * dmax);      // reduction the next pass must reach
   const float floor32 = 4.f * kappa * 5.960464477539063e-08f;
   const float tau = need > floor32 ? fminf(need, 0.5f) : 2.384185791015625e-07f;
   its = cheb_iterations(a1, a2, mu_max, tau);
