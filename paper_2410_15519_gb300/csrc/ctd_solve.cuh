@@ -604,6 +604,8 @@ __device__ inline float cta_max(float v, float* red) {
 // Each pass solves for the correction of a double-float residual; passes repeat until the
 // remaining error is bounded by 2^-46 of the iterate.
 struct ChebLayout {
+  int nl;      // lead rows of the end warp: the explicit ones, plus one so that interior rows
+               // start at an even index (row pairs are 16-byte aligned in shared memory)
   int R;       // rows per interior thread
   int tint;    // interior threads (blockDim.x - 32)
   int tact;    // interior threads that own rows
@@ -626,20 +628,23 @@ __host__ __device__ inline int cheb_rows_option(int q) {
 // Smallest R (> b, so that halos come from the immediate neighbours) whose split leaves at
 // most kChebEndMax end rows.  False if none does.
 __host__ __device__ inline bool cheb_layout(int n, int nlead, int ntail, int b, int tint, ChebLayout& L) {
-  const int nint = n - nlead - ntail;
+  int nl = nlead + (nlead & 1);
+  if (nl + ntail > n) nl = nlead;
+  const int nint = n - nl - ntail;
   if (nint < 0) return false;
   for (int q = 0; q < kChebRowOptions; ++q) {
     const int R = cheb_rows_option(q);
     if (R <= b) continue;
     int tact = nint / R;
     if (tact > tint) tact = tint;
-    const int nend = nlead + ntail + (nint - tact * R);
+    const int nend = nl + ntail + (nint - tact * R);
     if (nend > kChebEndMax) continue;
-    if (tact > 0 && (nlead < b || ntail < b)) return false;   // halos of the outer interior threads
+    if (tact > 0 && (nl < b + 1 || ntail < b || (nl & 1))) return false;   // halos, alignment
+    L.nl = nl;
     L.R = R;
     L.tint = tint;
     L.tact = tact;
-    L.e0 = nlead + tact * R;
+    L.e0 = nl + tact * R;
     L.nend = nend;
     return true;
   }
@@ -664,7 +669,7 @@ struct ChebSmem {
 };
 
 __host__ __device__ inline size_t cheb_floats(int n) {
-  return static_cast<size_t>(n) * 3 + static_cast<size_t>(kChebEndMax) * 15 * 3 + 32 +
+  return static_cast<size_t>((n + 3) & ~3) * 3 + static_cast<size_t>(kChebEndMax) * 15 * 3 + 32 +
          2 * static_cast<size_t>(cheb_buffer_floats(7, 256 - 32)) + 64;
 }
 
@@ -839,7 +844,6 @@ __device__ __forceinline__ void cheb_iterate_interior(float (&r)[R], float (&e)[
 #pragma unroll
     for (int m = 0; m < R / 2; ++m) {
       float2 acc = make_float2(r[2 * m], r[2 * m + 1]);
-#pragma unroll
       // symmetric stencil: the pair sums d_{j-B+o} + d_{j+B-o} go through the adder, leaving
       // B + 1 multiply-adds per row pair
       acc = __ffma2_rn(nst[B], make_float2(w[2 * m + 1 + B], w[2 * m + 2 + B]), acc);
@@ -937,7 +941,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
   if (tid < W) cp_async8(sm.st + tid, k.stencil + tid);
   for (int c = tid; c < L.nend * W; c += T) {
     const int slot = c / W, o = c - slot * W;
-    const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
+    const int row = slot < L.nl ? slot : L.e0 + (slot - L.nl);
     const float2* src = row < k.nlead ? k.rows + row * W + o
                         : row >= n - k.ntail ? k.rows + (k.nlead + row - (n - k.ntail)) * W + o
                                              : k.stencil + o;
@@ -950,7 +954,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
   // FP32 operator rows of the end rows: a2 K + a1 omega on the diagonal, zero outside [0, n)
   for (int c = tid; c < L.nend * W; c += T) {
     const int slot = c / W, o = c - slot * W;
-    const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
+    const int row = slot < L.nl ? slot : L.e0 + (slot - L.nl);
     const int j = row + o - B;
     float v = (j >= 0 && j < n) ? a2.hi * sm.kbd[c].x : 0.f;
     if (o == B) v += a1.hi * kc_omega(k, row).x;
@@ -966,7 +970,8 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
   if (tid < L.tint) {
     // ================= interior group
     const bool active = tid < L.tact;
-    const int i0 = k.nlead + tid * R;
+    const int i0 = L.nl + tid * R;
+    const int npairs = (L.e0 - L.nl) / 2;   // interior row pairs
     const uint32_t kstr = 4u * static_cast<uint32_t>(L.tint);
     const float a1in = a1.hi * k.omega_in.x, iwin = k.inv_omega_in;
     // -(a1 omega + a2 K) stencil in FP32, symmetrised (K is symmetric; this operator only
@@ -985,9 +990,9 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
     uint32_t src_l = hbase + 4u * reg0, src_r = hbase + 4u * reg0, str_l = 0u, str_r = 0u;
     if (active) {
       if (tid == 0) {
-        pub_l = hbase + 4u * (reg0 + B + k.nlead);          // rows nlead .. nlead + B - 1
+        pub_l = hbase + 4u * (reg0 + B + L.nl);             // rows nl .. nl + B - 1
         spl = 4u;
-        src_l = hbase + 4u * (reg0 + k.nlead);              // rows nlead - B .. nlead - 1
+        src_l = hbase + 4u * (reg0 + L.nl);                 // rows nl - B .. nl - 1
         str_l = 4u;
       } else {
         pub_l = hbase + 4u * tid;
@@ -1011,45 +1016,57 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
     for (int pass = 0; pass < 6; ++pass) {
       const bool cold0 = !warm && pass == 0;
       unsigned long long tp = trace ? global_ns() : 0ull;
-      // residual of the current iterate (double-float), rounded to FP32, through sm.rs: the
-      // row loop stays rolled (a fully unrolled one is tens of KB of code, fetched anew on
-      // every pass)
-      if (active) {
-        if (cold0) {
+      // Residual of the current iterate (double-float), rounded to FP32, into sm.rs[row - nl].
+      // Here consecutive threads take consecutive row pairs (16-byte aligned): conflict-free
+      // shared-memory accesses; the loop stays rolled (unrolled, it is tens of KB of code
+      // fetched anew on every pass).
+      if (cold0) {
 #pragma unroll 1
-          for (int j = 0; j < R; ++j) { const float2 qq = sm.q[i0 + j]; sm.rs[i0 + j] = qq.x + qq.y; }
-        } else {
-          float2 sdf[W];
+        for (int p = tid; p < npairs; p += L.tint) {
+          const int i = L.nl + 2 * p;
+          const float4 qq = *reinterpret_cast<const float4*>(sm.q + i);
+          *reinterpret_cast<float2*>(sm.rs + 2 * p) = make_float2(qq.x + qq.y, qq.z + qq.w);
+        }
+      } else {
+        float2 sdf[W];
 #pragma unroll
-          for (int o = 0; o < W; ++o) sdf[o] = sm.st[o];
+        for (int o = 0; o < W; ++o) sdf[o] = sm.st[o];
 #pragma unroll 1
-          for (int m = 0; m < R / 2; ++m) {
-            const int i = i0 + 2 * m;
-            float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-            float2 xa = x[i - B];
+        for (int p = tid; p < npairs; p += L.tint) {
+          const int i = L.nl + 2 * p;
+          float2 xw[2 * B + 4];   // rows i - B - 1 .. i + B + 2
 #pragma unroll
-            for (int o = 0; o < W; ++o) {
-              const float2 xb = x[i - B + o + 1];
-              df2_dot_acc(s, c, sdf[o], make_float2(xa.x, xb.x), make_float2(xa.y, xb.y));
-              xa = xb;
-            }
-            const float2 x0v = x[i], x1v = x[i + 1], q0 = sm.q[i], q1 = sm.q[i + 1];
-            const df2 kx = df2_two_sum(s, c);
-            const df2 ax = df2_add(df2_mul_s(a2, kx),
-                                   df2_mul_s(a1w_in, df2{make_float2(x0v.x, x1v.x), make_float2(x0v.y, x1v.y)}));
-            const df2 rr = df2_add(df2{make_float2(q0.x, q1.x), make_float2(q0.y, q1.y)},
-                                   df2{make_float2(-ax.hi.x, -ax.hi.y), make_float2(-ax.lo.x, -ax.lo.y)});
-            const float2 rv = __fadd2_rn(rr.hi, rr.lo);
-            sm.rs[i] = rv.x;
-            sm.rs[i + 1] = rv.y;
+          for (int c = 0; c < B + 2; ++c) {
+            const float4 v = *reinterpret_cast<const float4*>(x + i - B - 1 + 2 * c);
+            xw[2 * c] = make_float2(v.x, v.y);
+            xw[2 * c + 1] = make_float2(v.z, v.w);
           }
+          const float4 qq = *reinterpret_cast<const float4*>(sm.q + i);
+          float2 s2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int o = 0; o < W; ++o) {
+            const float2 xa = xw[o + 1], xb = xw[o + 2];
+            df2_dot_acc(s2, c2, sdf[o], make_float2(xa.x, xb.x), make_float2(xa.y, xb.y));
+          }
+          const float2 x0v = xw[B + 1], x1v = xw[B + 2];
+          const df2 kx = df2_two_sum(s2, c2);
+          const df2 ax = df2_add(df2_mul_s(a2, kx),
+                                 df2_mul_s(a1w_in, df2{make_float2(x0v.x, x1v.x), make_float2(x0v.y, x1v.y)}));
+          const df2 rr = df2_add(df2{make_float2(qq.x, qq.z), make_float2(qq.y, qq.w)},
+                                 df2{make_float2(-ax.hi.x, -ax.hi.y), make_float2(-ax.lo.x, -ax.lo.y)});
+          *reinterpret_cast<float2*>(sm.rs + 2 * p) = __fadd2_rn(rr.hi, rr.lo);
         }
       }
+      bar_sync_all();
+      if (trace && tid == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveResidual, t - tp); tp = t; }
+      // own rows of this thread (R consecutive, 16-byte aligned in sm.rs)
 #pragma unroll
-      for (int j = 0; j < R; ++j) r[j] = active ? sm.rs[i0 + j] : 0.f;
-      if (trace) {
-        bar_sync_all();
-        if (tid == 0) { const unsigned long long t = global_ns(); atomicAdd(trace + kTrSolveResidual, t - tp); tp = t; }
+      for (int j = 0; j < R; j += 4) {
+        const float4 v = active ? *reinterpret_cast<const float4*>(sm.rs + tid * R + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        r[j] = v.x;
+        r[j + 1] = v.y;
+        r[j + 2] = v.z;
+        r[j + 3] = v.w;
       }
 #pragma unroll
       for (int j = 0; j < NW; ++j) w[j] = 0.f;
@@ -1058,21 +1075,26 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
       cheb_iterate_interior<B, R>(r, e, w, nst, iwin, its, sigma, inv2d, pub_l, spl, pub_r, spr, src_l, str_l, src_r,
                                   str_r, bufb);
       if (trace && tid == 0) atomicAdd(trace + kTrSolveInner, global_ns() - tp);
-      // x += e (double-float), size of the correction and of the iterate
-      float dmax = 0.f, xmax = 0.f;
+      // x += e (double-float) over row pairs, size of the correction and of the iterate.  The
+      // iterations' last barrier orders every read of sm.rs above before these writes.
       if (active) {
 #pragma unroll
-        for (int j = 0; j < R; ++j) sm.rs[i0 + j] = e[j];
+        for (int j = 0; j < R; j += 4)
+          *reinterpret_cast<float4*>(sm.rs + tid * R + j) = make_float4(e[j], e[j + 1], e[j + 2], e[j + 3]);
+      }
+      bar_sync_all();
+      float dmax = 0.f, xmax = 0.f;
 #pragma unroll 1
-        for (int j = 0; j < R; ++j) {
-          const float ej = sm.rs[i0 + j];
-          const float2 xo = cold0 ? make_float2(0.f, 0.f) : x[i0 + j];
-          const dfloat nx = df_add(dfloat{xo.x, xo.y}, dfloat{ej, 0.f});
-          x[i0 + j] = make_float2(nx.hi, nx.lo);
-          dmax = fmaxf(dmax, fabsf(ej));
-          xmax = fmaxf(xmax, fabsf(nx.hi));
-          if (!(fabsf(ej) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
-        }
+      for (int p = tid; p < npairs; p += L.tint) {
+        const int i = L.nl + 2 * p;
+        const float2 ev = *reinterpret_cast<const float2*>(sm.rs + 2 * p);
+        const float4 xo = cold0 ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(x + i);
+        const dfloat n0 = df_add(dfloat{xo.x, xo.y}, dfloat{ev.x, 0.f});
+        const dfloat n1 = df_add(dfloat{xo.z, xo.w}, dfloat{ev.y, 0.f});
+        *reinterpret_cast<float4*>(x + i) = make_float4(n0.hi, n0.lo, n1.hi, n1.lo);
+        dmax = fmaxf(dmax, fmaxf(fabsf(ev.x), fabsf(ev.y)));
+        xmax = fmaxf(xmax, fmaxf(fabsf(n0.hi), fabsf(n1.hi)));
+        if (!(fabsf(ev.x) <= 3.0e38f) || !(fabsf(ev.y) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
       }
       const int stop = cheb_pass_end(dmax, xmax, bound, its, pass, a1.hi, a2.hi, mu_max, crho, kappa, sm.red, trace,
                                      tsub);
@@ -1091,13 +1113,13 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
     for (int s2 = 0; s2 < 2; ++s2) {
       const int slot = lane + 32 * s2;
       if (slot < L.nend) {
-        const int row = slot < k.nlead ? slot : L.e0 + (slot - k.nlead);
+        const int row = slot < L.nl ? slot : L.e0 + (slot - L.nl);
         erow[s2] = row;
         eslot[s2] = slot;
         const float2 om = kc_omega(k, row);
         ea1wd[s2] = df_mul(a1, dfloat{om.x, om.y});
         eiw[s2] = kc_inv_omega(k, row);
-        const int ps = (L.tact == 0 || row < k.nlead) ? reg0 + B + row : reg1 + B + (row - L.e0);
+        const int ps = (L.tact == 0 || row < L.nl) ? reg0 + B + row : reg1 + B + (row - L.e0);
         epub[s2] = hbase + 4u * ps;
         ewin[s2] = hbase + 4u * (ps - B);
         ekb[s2] = kbase + 4u * (slot * W);
@@ -1125,10 +1147,11 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
           er[s2] = df_residual_finish(s, c, ea1wd[s2], a2, x[row], sm.q[row]);
         }
       }
-      if (trace) bar_sync_all();
+      bar_sync_all();   // matches the interior group's barrier after its residual
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2) { ee[s2] = 0.f; ed[s2] = er[s2] * eiw[s2] * c0; }
       cheb_iterate_end<B>(er, ee, ed, erow, epub, ewin, ekb, eiw, its, sigma, inv2d, bufb);
+      bar_sync_all();   // matches the interior group's barrier before its update
       float dmax = 0.f, xmax = 0.f;
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2) {
@@ -1299,14 +1322,16 @@ __device__ inline SolverStore solver_bind(int mode, float* fbase, float* gbase, 
   s.mu_max = mu_max;
   s.F = s.X = nullptr;
   if (mode == 3) {
+    // q and rs are read as 16-byte vectors: both start on 16-byte boundaries (fbase is)
+    const int n4 = (n + 3) & ~3;
     s.ch.q = reinterpret_cast<float2*>(fbase);
-    s.ch.kbd = s.ch.q + n;
+    s.ch.rs = fbase + 2 * n4;
+    s.ch.kbd = reinterpret_cast<float2*>(s.ch.rs + n4);
     s.ch.st = s.ch.kbd + kChebEndMax * 15;
     s.ch.S = cheb_buffer_floats(b, static_cast<int>(blockDim.x) - 32);
     s.ch.halo = reinterpret_cast<float*>(s.ch.st + 16);
     s.ch.kb = s.ch.halo + 2 * s.ch.S;
-    s.ch.rs = s.ch.kb + kChebEndMax * 15;
-    s.ch.red = s.ch.rs + n;
+    s.ch.red = s.ch.kb + kChebEndMax * 15;
   } else if (mode == 0) {
     s.cr = cr_bind(fbase, n, b);
     s.F = s.cr.F;
