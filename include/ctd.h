@@ -110,6 +110,21 @@ ctd_status ctd_set_initial_modes(ctd_handle h, int rank, const double* const* mo
  * Returns the most severe status over the steps when stats != NULL. */
 ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats);
 
+/* Batched time steps: advance `count` independent instances (handles made by ctd_create on
+ * the current device, each with its own configuration, workspace and field) by nsteps time
+ * steps each, in one kernel launch per step with one CTA per instance (the many-instance
+ * workload of uneven resolution; each instance runs the Section 3.3 step of ctd_step).
+ * Work is queued on cuda_stream (a cudaStream_t); the handles' own streams must be idle.
+ * workspace: device buffer of ctd_batch_workspace_size(count) bytes, 256-byte aligned, owned
+ * by the caller, free again when the call returns with stats != NULL (else once the stream
+ * has passed the launches).  stats: NULL, or count * nsteps records, instance-major
+ * (stats[i * nsteps + k]); with stats the call synchronises and returns the most severe
+ * status.  An instance stepped here is stepped in the same way as by ctd_step: its energy,
+ * modes and later ctd_step calls continue from the new state. */
+ctd_status ctd_batch_workspace_size(int count, size_t* bytes);
+ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void* workspace,
+                          size_t workspace_bytes, void* cuda_stream, ctd_step_stats* stats);
+
 /* Discrete energy of the current field, E_h = sum_grid omega F(u) + 1/2 kappa u^T K_grad u
  * (energy functional of Section 2.1 with F of Eq. energyfunction; F integrated with the
  * nodal rule, gradient with the exact stiffness).  FP64.  Synchronises. */

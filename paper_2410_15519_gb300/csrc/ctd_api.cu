@@ -1,5 +1,6 @@
 // C ABI of the CTD solver (declared in include/ctd.h): workspace layout, handle, launches.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -343,6 +344,8 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   h->grid = grid;
   h->plan = make_plan(*cfg, grid);
   carve(*cfg, h->plan, workspace, &h->P, &h->X, h->kc_store, &h->energy_part, &h->energy_gram, &h->stats_dev);
+  h->P.vgrid = grid;   // each CTA sets its own rank in its shared-memory copy
+  h->P.vrank = 0;
 
   StepParams& P = h->P;
   Extra& X = h->X;
@@ -617,6 +620,87 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
     done += batch;
   }
   if (!stats) CTD_CUDA(h, cudaGetLastError());
+  return worst;
+}
+
+ctd_status ctd_batch_workspace_size(int count, size_t* bytes) {
+  if (count < 1 || !bytes) return CTD_ERR_ARG;
+  *bytes = (sizeof(ctd::BatchEntry) * static_cast<size_t>(count) + 255) / 256 * 256 +
+           (sizeof(int) * static_cast<size_t>(count) + 255) / 256 * 256;
+  return CTD_OK;
+}
+
+ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void* workspace,
+                          size_t workspace_bytes, void* cuda_stream, ctd_step_stats* stats) {
+  if (!handles || count < 1 || nsteps < 0) return CTD_ERR_ARG;
+  size_t need = 0;
+  ctd_batch_workspace_size(count, &need);
+  if (!workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) return CTD_ERR_WORKSPACE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CTD_ERR_CUDA;
+  for (int i = 0; i < count; ++i) {
+    ctd_ctx* h = handles[i];
+    if (!h) return CTD_ERR_ARG;
+    if (!h->has_modes) return fail(h, CTD_ERR_STATE, "ctd_set_initial_modes has not been called");
+    if (h->device != dev) return fail(h, CTD_ERR_STATE, "instance on another device");
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  // one entry per instance; the largest instances start first
+  std::vector<ctd::BatchEntry> entries(count);
+  std::vector<int> order(count);
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) {
+    ctd_ctx* h = handles[i];
+    std::memset(&entries[i], 0, sizeof(ctd::BatchEntry));
+    entries[i].tm = h->tm;
+    entries[i].P = h->P;
+    entries[i].P.stats = h->stats_dev;
+    entries[i].P.trace = nullptr;
+    entries[i].X = h->X;
+    smem = std::max(smem, static_cast<size_t>(h->P.smem_bytes));
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return handles[a]->plan.N > handles[b]->plan.N; });
+  auto* dev_entries = static_cast<ctd::BatchEntry*>(workspace);
+  int* dev_order = reinterpret_cast<int*>(static_cast<char*>(workspace) +
+                                          (sizeof(ctd::BatchEntry) * static_cast<size_t>(count) + 255) / 256 * 256);
+  ctd_ctx* h0 = handles[0];
+  CTD_CUDA(h0, cudaMemcpyAsync(dev_entries, entries.data(), sizeof(ctd::BatchEntry) * count, cudaMemcpyHostToDevice,
+                               stream));
+  CTD_CUDA(h0, cudaMemcpyAsync(dev_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, stream));
+  ctd_status worst = CTD_OK;
+  std::vector<StepStatsDev> rec;
+  int done = 0;
+  while (done < nsteps) {
+    const int batch = std::min(nsteps - done, kStatsCap);
+    for (int k = 0; k < batch; ++k) CTD_CUDA(h0, ctd::launch_batch_step(dev_entries, dev_order, count, k, smem, stream));
+    if (stats) {
+      CTD_CUDA(h0, cudaStreamSynchronize(stream));
+      rec.resize(batch);
+      for (int i = 0; i < count; ++i) {
+        ctd_ctx* h = handles[i];
+        CTD_CUDA(h, cudaMemcpy(rec.data(), h->stats_dev, sizeof(StepStatsDev) * batch, cudaMemcpyDeviceToHost));
+        InstState st;
+        CTD_CUDA(h, cudaMemcpy(&st, h->P.st, sizeof(InstState), cudaMemcpyDeviceToHost));
+        const ctd_status es = status_from_bits(st.status);
+        for (int k = 0; k < batch; ++k) {
+          ctd_step_stats& o = stats[static_cast<size_t>(i) * nsteps + done + k];
+          o.modes = rec[k].modes;
+          o.als_sweeps = rec[k].als_sweeps;
+          o.als_sweeps_max = rec[k].als_sweeps_max;
+          o.capped = rec[k].capped;
+          o.not_converged = rec[k].not_converged;
+          o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
+          if (o.status < 0) worst = static_cast<ctd_status>(o.status);
+          else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
+        }
+        if (es != CTD_OK) fail(h, es, "device status set");
+      }
+      if (worst < 0) return worst;
+    }
+    done += batch;
+  }
+  if (!stats) CTD_CUDA(h0, cudaGetLastError());
   return worst;
 }
 

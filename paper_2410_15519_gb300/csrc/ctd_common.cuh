@@ -79,6 +79,9 @@ struct StepParams {
   float2* xsol_g;          // [kMaxN] solution iterate in global memory (solver mode 1)
   int smem_bytes;          // dynamic shared memory of the step kernel
   int n_max;               // largest n over the dimensions
+  int vgrid, vrank;        // CTAs working on this instance and this CTA's rank among them: the
+                           // launch grid for a single instance, 1 and 0 in a batched launch
+                           // (set by each CTA in its shared-memory copy)
 };
 
 // phases accumulated in StepParams::trace (each includes its closing grid barrier)

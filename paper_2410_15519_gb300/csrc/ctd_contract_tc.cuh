@@ -190,8 +190,8 @@ struct TcDir {
 static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir* dirs, __nv_bfloat16* const* kr, int pb,
                                   int Mk) {
   const int Kp = P.Kpad, W = 2 * Kp;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  const long long t0 = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
+  const long long t0 = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x;
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     const long long total = static_cast<long long>(dd.n_pad) * Kp;
@@ -274,7 +274,7 @@ __host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_
 static __device__ __noinline__ bool tc_contract(const StepParams& P, const KCompressed* kc, const TcDir& td,
                                    const CUtensorMap* Pmap, const CUtensorMap* Qmap, int x, int Mk, int stages,
                                    unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump) {
-  const int G = gridDim.x, cta = blockIdx.x;
+  const int G = P.vgrid, cta = P.vrank;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunks = 2 * P.Kpad / kTcChunkElems;
   const int ksteps = (Mk + 15) / 16;

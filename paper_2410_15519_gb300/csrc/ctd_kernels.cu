@@ -64,8 +64,18 @@ __device__ __forceinline__ void stage_to_smem(T* dst, const T& src) {
   for (int i = threadIdx.x; i < static_cast<int>(sizeof(T) / sizeof(int)); i += blockDim.x) d[i] = s[i];
 }
 
+// Shared-memory copy of the parameters with this CTA's place in the virtual grid
+__device__ __forceinline__ void stage_params(StepParams* dst, const StepParams& src, int vgrid, int vrank) {
+  stage_to_smem(dst, src);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dst->vgrid = vgrid;
+    dst->vrank = vrank;
+  }
+}
+
 __device__ __forceinline__ void trace_mark(const StepParams& P, unsigned long long& t, int phase) {
-  if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (P.trace && P.vrank == 0 && threadIdx.x == 0) {
     const unsigned long long now = global_ns();
     atomicAdd(P.trace + phase, now - t);
     t = now;
@@ -73,7 +83,7 @@ __device__ __forceinline__ void trace_mark(const StepParams& P, unsigned long lo
 }
 
 __device__ inline bool sync_all(const StepParams& P, unsigned& epoch, int where) {
-  if (gridDim.x == 1) {
+  if (P.vgrid == 1) {
     __syncthreads();
     return true;
   }
@@ -85,7 +95,7 @@ __device__ __noinline__ void convert_prev_modes(const StepParams& P, const Extra
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
-    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
     for (int m = 0; m < Mk; ++m)
       for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
         X.Af[d][static_cast<size_t>(m) * dd.n + i] = f2_to_double(dd.bank[pb][static_cast<size_t>(m) * dd.n + i]);
@@ -111,7 +121,7 @@ __device__ __noinline__ void init_mode(const StepParams& P, int m, int pb, int M
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
-    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       float2 v;
       if (s_nz[d]) {
@@ -128,7 +138,7 @@ __device__ __noinline__ void init_mode(const StepParams& P, int m, int pb, int M
 // Convergence partials (own slices): per dimension c the six products of old, delta = new -
 // old and new, and max |new|; slot (c * 6 + k) of the gram buffer, maxpart[c * G + cta].
 __device__ __noinline__ void convergence_partials(const StepParams& P, const Extra& X, float2* sh) {
-  const int G = gram_ctas(), cta = blockIdx.x;
+  const int G = gram_ctas(P), cta = P.vrank;
   if (cta >= G) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = 0; c < P.dim; ++c) {
@@ -177,7 +187,7 @@ __device__ __noinline__ void save_old(const StepParams& P) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
-    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) dd.vold[i] = dd.v[i];
   }
 }
@@ -188,7 +198,7 @@ __device__ __noinline__ void commit_mode(const StepParams& P, const Extra& X, in
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
-    slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+    slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
     const dfloat sc = df_of(scale[d]);
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       st_df(dd.bank[cb] + static_cast<size_t>(M) * dd.n + i, df_mul(ld_df(dd.v + i), sc));
@@ -279,10 +289,10 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
       save_old(P);
       for (int x = 0; x < D; ++x) {
         // Phase A: Gram partials of the fixed factors + nonlinear contraction partials
-        unsigned long long tsub = (P.trace && blockIdx.x == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
+        unsigned long long tsub = (P.trace && P.vrank == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
         gram_partials(P, X, x, Mk, M, pb, cb, ar.gram_rows);
         __syncthreads();
-        if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (P.trace && P.vrank == 0 && threadIdx.x == 0) {
           const unsigned long long t = global_ns();
           atomicAdd(P.trace + kTrGram, t - tsub);
           tsub = t;
@@ -297,7 +307,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
                            X.rpart32, nullptr))
             return;
         }
-        if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(P.trace + kTrContract, global_ns() - tsub);
+        if (P.trace && P.vrank == 0 && threadIdx.x == 0) atomicAdd(P.trace + kTrContract, global_ns() - tsub);
         if (!sync_all(P, epoch, 3)) return;
         trace_mark(P, tmark, kTrGramContract);
         // Phase B: coefficients (every CTA, same order) and right-hand-side rows
@@ -306,13 +316,13 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
         if (!sync_all(P, epoch, 4)) return;
         trace_mark(P, tmark, kTrRhs);
         // Phase C: banded solve on CTA 0
-        if (blockIdx.x == 0) solve_direction(P, X, x, sm, ar, it > 1);
+        if (P.vrank == 0) solve_direction(P, X, x, sm, ar, it > 1);
         if (!sync_all(P, epoch, 5)) return;
         trace_mark(P, tmark, kTrSolve);
         const int zflag = *reinterpret_cast<volatile int*>(X.ctrl + 0);
         const int fflag = *reinterpret_cast<volatile int*>(X.ctrl + 1);
         if (fflag) {
-          if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.st->status, kErrNonfinite);
+          if (P.vrank == 0 && threadIdx.x == 0) atomicOr(&P.st->status, kErrNonfinite);
           return;
         }
         if (zflag) { zero_mode = true; break; }
@@ -326,7 +336,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
       {
         __shared__ double s_dots[kMaxDim * 6];
         __shared__ double s_max[kMaxDim];
-        const int Gg = gram_ctas();
+        const int Gg = gram_ctas(P);
         if (threadIdx.x < D * 6) s_dots[threadIdx.x] = df_to_double(reduce_slot(P.gram + static_cast<size_t>(threadIdx.x) * Gg, Gg));
         if (threadIdx.x < D) {
           double mx = 0.0;
@@ -388,7 +398,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
     trace_mark(P, tmark, kTrCommit);
   }
   // ---- epilogue
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (P.vrank == 0 && threadIdx.x == 0) {
     InstState s = st0;
     s.Mk = M;
     s.bank = cb;
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant
   __shared__ uint32_t s_tmem;
   __shared__ __align__(16) StepParams sP;
   __shared__ __align__(16) Extra sX;
-  stage_to_smem(&sP, P);
+  stage_params(&sP, P, gridDim.x, blockIdx.x);
   stage_to_smem(&sX, X);
   const bool tc = P.precision != 0;
   if (tc && (threadIdx.x >> 5) == 1) tmem_alloc(&s_tmem, kTcAccCols);
@@ -421,6 +431,33 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant
   __syncthreads();
   tc_fence_after();
   step_body(sP, sX, tm, smem_raw, tc ? s_tmem : 0u);
+  __syncthreads();
+  if (tc && (threadIdx.x >> 5) == 1) {
+    tc_fence_after();
+    tmem_dealloc(s_tmem, kTcAccCols);
+  }
+}
+
+// Batched time steps: one CTA advances one instance (its own parameters, workspace and
+// tensor maps, read from entries[order[blockIdx.x]]), with CTA-wide barriers in place of
+// grid-wide ones.  kstep selects the instance's step record.  No CTA waits on another, so a
+// plain launch with more instances than SMs is fine.
+__global__ void __launch_bounds__(kThreads, 1) batch_step_kernel(const BatchEntry* entries, const int* order,
+                                                                 int kstep) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(16) StepParams sP;
+  __shared__ __align__(16) Extra sX;
+  const BatchEntry& E = entries[order[blockIdx.x]];
+  stage_params(&sP, E.P, 1, 0);
+  stage_to_smem(&sX, E.X);
+  if (threadIdx.x == 0) sP.stats = E.P.stats + kstep;
+  const bool tc = E.P.precision != 0;
+  if (tc && (threadIdx.x >> 5) == 1) tmem_alloc(&s_tmem, kTcAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  step_body(sP, sX, E.tm, smem_raw, tc ? s_tmem : 0u);
   __syncthreads();
   if (tc && (threadIdx.x >> 5) == 1) {
     tc_fence_after();
@@ -542,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const __gri
   __shared__ uint32_t s_tmem;
   __shared__ __align__(16) StepParams sP;
   __shared__ __align__(16) Extra sX;
-  stage_to_smem(&sP, P);
+  stage_params(&sP, P, gridDim.x, blockIdx.x);
   stage_to_smem(&sX, X);
   const bool tc = P.precision != 0;
   if (tc && (threadIdx.x >> 5) == 1) tmem_alloc(&s_tmem, kTcAccCols);
@@ -563,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, 1) probe_solve_kernel(const __grid_c
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) StepParams P;
   __shared__ __align__(16) Extra X;
-  stage_to_smem(&P, Pp);
+  stage_params(&P, Pp, 1, 0);
   stage_to_smem(&X, Xp);
   __syncthreads();
   SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
@@ -617,6 +654,14 @@ cudaError_t launch_step(const StepParams& P, const Extra& X, const TmapSet& tm, 
   void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), const_cast<TmapSet*>(&tm)};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&step_kernel), dim3(grid), dim3(kThreads),
                                      args, smem, s);
+}
+
+cudaError_t launch_batch_step(const BatchEntry* entries, const int* order, int count, int kstep, size_t smem,
+                              cudaStream_t s) {
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&batch_step_kernel), smem);
+  if (e != cudaSuccess) return e;
+  batch_step_kernel<<<count, kThreads, smem, s>>>(entries, order, kstep);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, int x,

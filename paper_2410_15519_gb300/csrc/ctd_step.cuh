@@ -77,11 +77,11 @@ constexpr int kChunk = 256;
 // after the grid-wide wait: every CTA reads all of them)
 constexpr int kGramCtas = 16;
 
-__device__ __forceinline__ int gram_ctas() { return gridDim.x < kGramCtas ? gridDim.x : kGramCtas; }
+__device__ __forceinline__ int gram_ctas(const StepParams& P) { return P.vgrid < kGramCtas ? P.vgrid : kGramCtas; }
 
 static __device__ __noinline__ void gram_partials(const StepParams& P, const Extra& X, int x, int Mk, int M,
                               int pb, int cb, float2* sh) {
-  const int G = gram_ctas(), cta = blockIdx.x, D = P.dim, spd = slots_per_dim(P.Mcap);
+  const int G = gram_ctas(P), cta = P.vrank, D = P.dim, spd = slots_per_dim(P.Mcap);
   if (cta >= G) return;
   float2* sv = sh;               // v_i
   float2* sdv = sh + kChunk;     // omega_i v_i
@@ -178,7 +178,7 @@ struct Coef {
 
 static __device__ __noinline__ void build_coefficients(const StepParams& P, int x, int Mk, int M, Coef* c,
                                    float2* red /* >= 2*kMaxDim float2 */) {
-  const int G = gram_ctas(), D = P.dim, spd = slots_per_dim(P.Mcap);
+  const int G = gram_ctas(P), D = P.dim, spd = slots_per_dim(P.Mcap);
   const int nO = D - 1;
   // m_d, k_d of the fixed factors
   if (threadIdx.x < 2 * nO) {
@@ -234,7 +234,7 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
                          int cb, const Coef* c) {
   const Dim& dd = P.d[x];
   int lo, hi;
-  slice_of(dd.n, gridDim.x, blockIdx.x, lo, hi);
+  slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
   const int rows = hi - lo;
   if (rows <= 0) return;
   // a group of tpr consecutive lanes per row; its lanes split the mode sums
@@ -250,10 +250,10 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
     const long long T = static_cast<long long>(td.nrb) * td.ntc;
     rb_lo = lo / kTcM;
     const int rb_hi = (hi - 1) / kTcM;
-    cr_lo = tile_owner(T, gridDim.x, static_cast<long long>(rb_lo) * td.ntc + td.ntc - 1) -
-            tile_owner(T, gridDim.x, static_cast<long long>(rb_lo) * td.ntc) + 1;
-    cr_hi = tile_owner(T, gridDim.x, static_cast<long long>(rb_hi) * td.ntc + td.ntc - 1) -
-            tile_owner(T, gridDim.x, static_cast<long long>(rb_hi) * td.ntc) + 1;
+    cr_lo = tile_owner(T, P.vgrid, static_cast<long long>(rb_lo) * td.ntc + td.ntc - 1) -
+            tile_owner(T, P.vgrid, static_cast<long long>(rb_lo) * td.ntc) + 1;
+    cr_hi = tile_owner(T, P.vgrid, static_cast<long long>(rb_hi) * td.ntc + td.ntc - 1) -
+            tile_owner(T, P.vgrid, static_cast<long long>(rb_hi) * td.ntc) + 1;
     if (rb_hi > rb_lo + 1) rb_lo = -1;
   }
   for (int i0 = lo; i0 < hi; i0 += groups) {
@@ -289,8 +289,8 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         int Cr;
         if (rb_lo < 0) {
           const long long T = static_cast<long long>(td.nrb) * td.ntc;
-          Cr = tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
-               tile_owner(T, gridDim.x, static_cast<long long>(rb) * td.ntc) + 1;
+          Cr = tile_owner(T, P.vgrid, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
+               tile_owner(T, P.vgrid, static_cast<long long>(rb) * td.ntc) + 1;
         } else {
           Cr = rb == rb_lo ? cr_lo : cr_hi;
         }
@@ -325,8 +325,8 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
   const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
   const int C = P.rchunks[x];
   const int nc = P.d[x].n;
-  const int warp_g = blockIdx.x * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  const int total_warps = gridDim.x * kWarps;
+  const int warp_g = P.vrank * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int total_warps = P.vgrid * kWarps;
   const double* W = P.W;
   if (x == D - 1) {
     // column sums: R[c] = sum_r W[r * nc + c] wrow(r); units (32-column block, row chunk)
@@ -416,8 +416,8 @@ static __device__ __noinline__ void materialise_w(const StepParams& P, const Ext
   const int D = P.dim;
   const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
   const long long N = static_cast<long long>(n0) * n1 * n2;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < N; p += stride) {
+  const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
+  for (long long p = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x; p < N; p += stride) {
     double u = 0.0;
     if (D == 2) {
       const int i = static_cast<int>(p / n1), j = static_cast<int>(p - static_cast<long long>(i) * n1);

@@ -76,9 +76,12 @@ def load() -> ctypes.CDLL:
     lib.ctd_probe_trace.argtypes = [vp, i, vp, i]
     lib.ctd_probe_reconstruct.argtypes = [vp, i, vp, vp, sz]
     lib.ctd_probe_reconstruct_noalloc.argtypes = [vp, i, vp]
+    lib.ctd_batch_workspace_size.argtypes = [i, ctypes.POINTER(sz)]
+    lib.ctd_step_batch.argtypes = [ctypes.POINTER(vp), i, i, vp, sz, vp, ctypes.POINTER(StepStats)]
     for f in ("ctd_workspace_size", "ctd_create", "ctd_set_initial_modes", "ctd_step", "ctd_energy",
               "ctd_get_modes", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve", "ctd_probe_trace",
-              "ctd_probe_reconstruct", "ctd_probe_reconstruct_noalloc"):
+              "ctd_probe_reconstruct", "ctd_probe_reconstruct_noalloc", "ctd_batch_workspace_size",
+              "ctd_step_batch"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -135,6 +138,36 @@ def probe_cfem(cfg: Config, d: int):
     _check(lib, None, lib.ctd_probe_cfem(ctypes.byref(cfg), d, om.ctypes.data, kb.ctypes.data, ctypes.byref(b)),
            "probe_cfem")
     return om, kb, b.value
+
+
+def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True, stream=None):
+    """Advance independent instances together, one CTA per instance per launch
+    (ctd_step_batch).  Returns per-instance lists of step records when stats is true."""
+    import torch
+    lib = load()
+    count = len(solvers)
+    nb = ctypes.c_size_t(0)
+    _check(lib, None, lib.ctd_batch_workspace_size(count, ctypes.byref(nb)), "ctd_batch_workspace_size")
+    ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    handles = (ctypes.c_void_p * count)(*[s.h for s in solvers])
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    for s in solvers:
+        s.stream.synchronize()
+    rec = (StepStats * (count * nsteps))() if stats else None
+    st = lib.ctd_step_batch(handles, count, nsteps, ctypes.c_void_p(ws.data_ptr()), nb.value,
+                            ctypes.c_void_p(stream.cuda_stream), rec)
+    if st < 0:
+        bad = next((s.h for s in solvers if lib.ctd_last_error(s.h)), None)
+        _check(lib, bad, st, "ctd_step_batch")
+    if not stats:
+        stream.synchronize()
+        return None
+    out = []
+    for i in range(count):
+        out.append([dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
+                         capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status)
+                    for r in rec[i * nsteps:(i + 1) * nsteps]])
+    return out
 
 
 class Solver:
