@@ -347,6 +347,208 @@ def sep_rel_l2(A, B):
     return float(torch.linalg.vector_norm(ua - ub) / torch.linalg.vector_norm(ub))
 
 
+# --------------------------------------------------------------------------- batched leg (c4)
+C4_COUNT, C4_SEED = 256, 4
+
+
+def c4_config(ws):
+    sizes = {}
+    for w in ws:
+        sizes[w.n[0]] = sizes.get(w.n[0], 0) + 1
+    return {"workload": f"c4: {len(ws)} independent 2D instances, n per dimension in "
+                        f"{dict(sorted(sizes.items()))}, s=p=2, eps ~ U(0.01, 0.05), S=2, dt=1e-3, "
+                        f"mode caps U{{8..40}}, rank-4 seeded cosine initial modes",
+            "grid_points": int(sum(w.grid_points for w in ws)), "instances": len(ws),
+            "l2": "no flush: the instances' operands (about 0.3 GB) exceed the 129 MB L2",
+            "step": "one batched time step advances every instance by one time step"}
+
+
+def run_batch(args, rank, world, local_rank):
+    """c4: every timed step is one batched launch advancing all instances by one time step."""
+    import torch
+
+    from paper_2410_15519_gb300 import build, ctd
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    ws = workloads.batch_instances(C4_COUNT, C4_SEED + rank)
+
+    def make(prec, subset=None):
+        out = []
+        for w in (subset if subset is not None else ws):
+            s = ctd.Solver(ctd.config_from_workload(w, precision=ctd.PREC_FP64 if prec == "fp64"
+                                                    else ctd.PREC_SPLIT_BF16))
+            s.set_initial_modes(workloads.initial_modes(w))
+            out.append(s)
+        return out
+
+    def timed(solvers, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            ctd.step_batch(solvers, 1, stats=False)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        if clocks:
+            clocks.start()
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ctd.step_batch(solvers, steps, stats=False, stream=stream, sync=False)
+        ev1.record(stream)
+        ev1.synchronize()
+        clk = clocks.stop() if clocks else None
+        return ev0.elapsed_time(ev1), clk
+
+    out = {"config": c4_config(ws)}
+    sol = make(args.precision)
+    total_ms, clk = timed(sol, args.steps, args.warmup, ClockSampler(local_rank))
+    if world > 1:
+        torch.distributed.barrier()
+    out["total_ms"] = max_over_ranks(total_ms, world)
+    out["clocks"] = clk
+    st = ctd.step_batch(sol, 1)
+    out["sweeps_per_instance_step"] = sum(r[0]["als_sweeps"] for r in st) / len(st)
+    out["modes_per_instance"] = sum(r[0]["modes"] for r in st) / len(st)
+    # end to end: host modes of every instance in, one batched step, host modes out
+    n_e2e = min(args.steps, 3)
+    host = [s.get_modes() for s in sol]
+    bi = bo = 0
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        for s, m in zip(sol, host):
+            s.set_initial_modes(m, first_step=1000 + k)
+            bi += sum(a.nbytes for a in m)
+        ctd.step_batch(sol, 1, stats=False)
+        host = [s.get_modes() for s in sol]
+        bo += sum(a.nbytes for m in host for a in m)
+    out["e2e"] = dict(steps=n_e2e, seconds=time.perf_counter() - t0, h2d=bi / n_e2e, d2h=bo / n_e2e)
+    for s in sol:
+        s.close()
+    # accuracy: the first batched step of the smallest instances against the oracle (cpu leg)
+    small = [w for w in ws if w.n[0] == min(x.n[0] for x in ws)][:2]
+    sm = make(args.precision, small)
+    ctd.step_batch(sm, 1)
+    out["first_step_small"] = [(w, s.get_modes()) for w, s in zip(small, sm)]
+    for s in sm:
+        s.close()
+    # the plain FP64 form side by side: batched, and one instance after another on the whole GPU
+    if args.compare_steps > 0 and rank == 0:
+        f64 = make("fp64")
+        ms64, _ = timed(f64, 1, 1)
+        for s in f64:
+            s.close()
+        seq = 0.0
+        for w in ws:
+            s = make("fp64", [w])[0]
+            s.step(1, stats=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.step(1, stats=False)
+            e1.record(s.stream)
+            e1.synchronize()
+            seq += e0.elapsed_time(e1)
+            s.close()
+        out["compare"] = {"fp64_batched_ms_per_step": ms64, "fp64_one_instance_at_a_time_ms_per_step": seq}
+    return out
+
+
+def c4_oracle_baseline(budget_s: float):
+    """Oracle time of one batched step, estimated from one oracle step of one instance of each
+    size (the batch's step time is the sum over its instances)."""
+    ws = workloads.batch_instances(C4_COUNT, C4_SEED)
+    per_size = {}
+    for w in ws:
+        if w.n[0] not in per_size:
+            per_size[w.n[0]] = w
+    t = {}
+    for nsz, w in sorted(per_size.items()):
+        code = ("import sys, time, json; sys.path.insert(0, %r)\n" % ROOT +
+                "import workloads\nfrom oracle import ctd\n"
+                "w = [x for x in workloads.batch_instances(%d, %d) if x.name == %r][0]\n" % (C4_COUNT, C4_SEED, w.name) +
+                "prob = ctd.Problem(dim=2, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, "
+                "a0=w.a0, alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als, "
+                "tol_enrich=w.tol_enrich, seed=w.seed)\n"
+                "ops = ctd.build_operators(prob); A = workloads.initial_modes(w)\n"
+                "t0 = time.perf_counter(); A, st = ctd.step(prob, ops, A, 0); print(json.dumps(time.perf_counter() - t0))\n")
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], check=True, env=env, capture_output=True, text=True)
+        t[nsz] = float(r.stdout.strip().splitlines()[-1])
+    counts = {}
+    for w in ws:
+        counts[w.n[0]] = counts.get(w.n[0], 0) + 1
+    batch_s = sum(counts[k] * t[k] for k in counts)
+    return 1.0 / batch_s, t
+
+
+def c4_first_step_errors(first):
+    from oracle import ctd as octd
+    errs = []
+    for w, G in first:
+        prob = octd.Problem(dim=2, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
+                            alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+                            tol_enrich=w.tol_enrich, seed=w.seed)
+        ops = octd.build_operators(prob)
+        A, _ = octd.step(prob, ops, workloads.initial_modes(w), 0)
+        errs.append(octd.rel_l2_between(G, A))
+    return errs
+
+
+def main_batch(args, rank, world, local_rank):
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, per = c4_oracle_baseline(args.oracle_budget)
+        ws = workloads.batch_instances(C4_COUNT, C4_SEED)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": 1, "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": c4_config(ws),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"one oracle step of one instance per size {per} s, summed over the "
+                                           f"batch's instances; single-threaded BLAS, {cpu_model()}"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_batch(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    value = replica_units(args.steps, world) / (res["total_ms"] / 1e3)
+    cfg = res["config"]
+    e2e = res["e2e"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3-split/f32-acc; solves, Gram products, energy FP64-accurate" if args.precision == "mixed"
+            else "f64", "data": "synthetic", "config": cfg,
+            "instance_steps_per_s": value * cfg["instances"],
+            "dof_updates_per_s": value * cfg["grid_points"],
+            "sweeps_per_instance_step": res["sweeps_per_instance_step"],
+            "modes_per_instance": res["modes_per_instance"],
+            "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                         "traffic": None, "kernel": "ctd::batch_step_kernel (one CTA per instance)",
+                         "note": "each instance is a latency-bound chain on one SM; see the c1 line for "
+                                 "the contraction roofline"},
+            "clocks": res["clocks"], "gpu_launches": args.steps,
+            "e2e": {"value": world * e2e["steps"] / e2e["seconds"], "unit": UNIT,
+                    "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"])}}
+    if "compare" in res:
+        c = res["compare"]
+        line["compare"] = {"fp64_batched": {"ms_per_step": c["fp64_batched_ms_per_step"],
+                                            "value": 1e3 / c["fp64_batched_ms_per_step"]},
+                           "fp64_one_instance_at_a_time": {"ms_per_step": c["fp64_one_instance_at_a_time_ms_per_step"],
+                                                           "value": 1e3 / c["fp64_one_instance_at_a_time_ms_per_step"]}}
+    if not args.no_cpu_baseline:
+        v, per = c4_oracle_baseline(args.oracle_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one oracle step of one instance per size {per} s, summed over the "
+                                          f"batch's instances; single-threaded BLAS, {cpu_model()}"}
+        line["first_step_err_u_vs_oracle_smallest_instances"] = c4_first_step_errors(res["first_step_small"])
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -365,6 +567,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "c4":
+        main_batch(args, rank, world, local_rank)
+        return
     w = workloads.preset(args.workload)
     config = {"workload": f"{w.name}: {w.dim}D {'x'.join(map(str, w.n))} nodes, s={w.s} p={w.p}, eps={w.eps}, "
                           f"S={w.S}, dt={w.dt}, M_max={w.M_max}, tol_als={w.tol_als}, tol_enrich={w.tol_enrich}",

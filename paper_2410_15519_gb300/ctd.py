@@ -140,9 +140,13 @@ def probe_cfem(cfg: Config, d: int):
     return om, kb, b.value
 
 
-def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True, stream=None):
+_batch_keep: List = []
+
+
+def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True, stream=None, sync: bool = True):
     """Advance independent instances together, one CTA per instance per launch
-    (ctd_step_batch).  Returns per-instance lists of step records when stats is true."""
+    (ctd_step_batch).  Returns per-instance lists of step records when stats is true; without
+    stats and with sync false the launches are left queued on the stream."""
     import torch
     lib = load()
     count = len(solvers)
@@ -160,7 +164,11 @@ def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True,
         bad = next((s.h for s in solvers if lib.ctd_last_error(s.h)), None)
         _check(lib, bad, st, "ctd_step_batch")
     if not stats:
-        stream.synchronize()
+        if sync:
+            stream.synchronize()
+        else:
+            _batch_keep.append(ws)   # the queued launches still read it
+            del _batch_keep[:-4]
         return None
     out = []
     for i in range(count):
