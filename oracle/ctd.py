@@ -68,6 +68,8 @@ class Problem:
     seed: int = 0
     fixed_als_iters: int = 0   # >0: exactly this many sweeps per mode (strict-parity mode)
     fixed_modes: int = 0       # >0: exactly this many modes per step (strict-parity mode)
+    reduced_tol: float = 0.0   # >0: reduced integration domain (Section 3.3), see below
+    reduced_block: int = 128   # nodes per dimension of the element blocks it keeps or drops
 
     @property
     def c_t(self) -> float:
@@ -120,11 +122,31 @@ def grid_weights(ops: Operators) -> np.ndarray:
     return W
 
 
+def reduced_domain_mask(prob: Problem, W: np.ndarray) -> np.ndarray:
+    """Reduced integration domain (Section 3.3: keep only where ``w(u^k)`` is not close to
+    zero).  Reading: the grid is cut into blocks of ``reduced_block`` nodes per dimension
+    (the last block of a dimension may be shorter); a block stays in the domain when the
+    largest ``|w(u^k)|`` at its nodes exceeds ``reduced_tol``, else its nodes drop out of the
+    nonlinear integral.  ``reduced_tol <= 0`` keeps every node."""
+    keep = np.ones(W.shape, dtype=bool)
+    if prob.reduced_tol <= 0.0:
+        return keep
+    B = prob.reduced_block
+    nb = [(n + B - 1) // B for n in W.shape]
+    for blk in np.ndindex(*nb):
+        sl = tuple(slice(b * B, min((b + 1) * B, n)) for b, n in zip(blk, W.shape))
+        if not np.max(np.abs(W[sl])) > prob.reduced_tol:
+            keep[sl] = False
+    return keep
+
+
 def nonlinear_tensor(prob: Problem, ops: Operators, A: Sequence[np.ndarray]) -> np.ndarray:
     """The nonlinear operator of Eq. KxxMxx under the nodal rule, as a D-way array:
-    ``Mxy[i, j(, l)] = L prod_d omega_d w(u^k(x_i, y_j(, z_l)))``."""
+    ``Mxy[i, j(, l)] = L prod_d omega_d w(u^k(x_i, y_j(, z_l)))``, zero outside the reduced
+    domain when one is set."""
     U = reconstruct(A)
-    return prob.L * grid_weights(ops) * w_of_u(U, prob.a0)
+    W = w_of_u(U, prob.a0)
+    return prob.L * grid_weights(ops) * W * reduced_domain_mask(prob, W)
 
 
 def contract_except(T: np.ndarray, vecs: Sequence[np.ndarray], keep: int) -> np.ndarray:

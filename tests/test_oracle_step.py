@@ -210,3 +210,56 @@ def test_mode_cap_sets_capped_flag():
     A = workloads.cosine_modes(prob.n, prob.length, 3, 4, 1)
     B, st = ctd.step(prob, ops, A, 0)
     assert st["modes"] == 1 and st["capped"]
+
+
+# ---------------------------------------------------------------- reduced integration domain
+def _reduced_case(tol, block=8):
+    w = workloads.preset("c0", n=(40, 36), eps=0.05, ic_rank=0, ic_tanh=True)
+    prob = ctd.Problem(dim=2, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
+                        alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+                        tol_enrich=w.tol_enrich, seed=w.seed, reduced_tol=tol, reduced_block=block)
+    return w, prob, ctd.build_operators(prob), workloads.initial_modes(w)
+
+
+def test_reduced_domain_zero_tolerance_is_the_full_integral():
+    w, prob, ops, A = _reduced_case(0.0)
+    full = ctd.nonlinear_tensor(prob, ops, A)
+    prob.reduced_tol = 0.0
+    U = ctd.reconstruct(A)
+    assert np.array_equal(full, prob.L * ctd.grid_weights(ops) * ctd.w_of_u(U, prob.a0))
+
+
+def test_reduced_domain_mask_brute_force_blocks():
+    # every block is kept iff some node in it has |w| > tol (plain loops over the nodes)
+    w, prob, ops, A = _reduced_case(1e-3, block=8)
+    W = ctd.w_of_u(ctd.reconstruct(A), prob.a0)
+    mask = ctd.reduced_domain_mask(prob, W)
+    n0, n1 = W.shape
+    for i in range(n0):
+        for j in range(n1):
+            bi, bj = i // 8, j // 8
+            big = False
+            for ii in range(bi * 8, min(bi * 8 + 8, n0)):
+                for jj in range(bj * 8, min(bj * 8 + 8, n1)):
+                    big = big or abs(W[ii, jj]) > 1e-3
+            assert mask[i, j] == big
+    # the tanh interface sits at x = 1/2: blocks far from it drop out, blocks on it stay
+    assert not mask[0, 0] and not mask[-1, -1] and mask[n0 // 2, 0]
+
+
+def test_reduced_domain_error_bound_and_limits():
+    w, prob, ops, A = _reduced_case(1e-3, block=8)
+    red = ctd.nonlinear_tensor(prob, ops, A)
+    prob.reduced_tol = 0.0
+    full = ctd.nonlinear_tensor(prob, ops, A)
+    v = [np.random.default_rng(2).uniform(0.5, 1.5, size=w.n[d]) for d in range(2)]
+    W = ctd.w_of_u(ctd.reconstruct(A), prob.a0)
+    prob.reduced_tol = 1e-3
+    drop = ~ctd.reduced_domain_mask(prob, W)
+    for x in range(2):
+        diff = np.abs(ctd.contract_except(full - red, v, x))
+        bound = 1e-3 * ctd.contract_except(prob.L * ctd.grid_weights(ops) * drop, v, x)
+        assert np.all(diff <= bound * (1 + 1e-12) + 1e-300)
+    # a tolerance above every |w| removes the whole nonlinear term
+    prob.reduced_tol = 10.0 * float(np.max(np.abs(W)))
+    assert not np.any(ctd.nonlinear_tensor(prob, ops, A))
