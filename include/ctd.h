@@ -73,6 +73,10 @@ typedef struct {
   unsigned long long seed;  /* SplitMix64 seed for modes without a warm start               */
   double wait_limit_s;      /* limit of each grid-wide wait; <= 0 means 1 second            */
   int grid_ctas;            /* persistent CTAs; <= 0 means one per SM                       */
+  double reduced_tol;       /* > 0: reduced integration domain of the nonlinear term
+                               (Section 3.3): a 128 x 128 node block drops out of M_xy for
+                               the step when max |w(u^k)| over its nodes <= reduced_tol;
+                               0: the whole domain.  2D only (CTD_ERR_UNSUPPORTED in 3D)   */
 } ctd_config;
 
 typedef struct {

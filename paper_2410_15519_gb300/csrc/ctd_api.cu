@@ -168,6 +168,7 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   p.xsol_g = cv.take<float2>(ctd::kMaxN);
   p.W = (c.precision == CTD_PREC_FP64) ? cv.take<double>(static_cast<size_t>(pl.N)) : nullptr;
   p.barrier = cv.take<unsigned>(64);
+  p.tile_max = cv.take<unsigned>(static_cast<size_t>(pl.n_pad[0] / ctd::kTcM) * (pl.n_pad[1] / ctd::kTcN));
   p.trace = cv.take<unsigned long long>(ctd::kTrSlots);
   p.st = cv.take<InstState>(1);
   x.maxpart = cv.take<double>(static_cast<size_t>(ctd::kMaxDim) * Gs);
@@ -213,6 +214,8 @@ ctd_status validate(const ctd_config* c) {
   if (c->fixed_als_iters < 0 || c->fixed_modes < 0 || c->fixed_modes > c->M_max) return CTD_ERR_ARG;
   if (c->precision != CTD_PREC_FP64 && c->precision != CTD_PREC_SPLIT_BF16) return CTD_ERR_ARG;
   if (c->grid_ctas > kGridMax) return CTD_ERR_ARG;
+  if (!(c->reduced_tol >= 0.0) || !std::isfinite(c->reduced_tol)) return CTD_ERR_ARG;
+  if (c->reduced_tol > 0.0 && c->dim != 2) return CTD_ERR_UNSUPPORTED;
   return CTD_OK;
 }
 
@@ -368,6 +371,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   }
   P.tol_als = cfg->tol_als;
   P.tol_enrich = cfg->tol_enrich;
+  P.reduced_tol = cfg->reduced_tol;
   P.I_max = cfg->I_max;
   P.M_max = cfg->M_max;
   P.fixed_als = cfg->fixed_als_iters;

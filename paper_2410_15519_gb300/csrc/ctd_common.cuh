@@ -79,6 +79,8 @@ struct StepParams {
   float2* xsol_g;          // [kMaxN] solution iterate in global memory (solver mode 1)
   int smem_bytes;          // dynamic shared memory of the step kernel
   int n_max;               // largest n over the dimensions
+  double reduced_tol;      // > 0: reduced integration domain of the nonlinear term (2D)
+  unsigned* tile_max;      // [nrb_0 * ntc_0] max |u(u^2-1)| per 128 x 128 node block (float bits)
   int vgrid, vrank;        // CTAs working on this instance and this CTA's rank among them: the
                            // launch grid for a single instance, 1 and 0 in a batched launch
                            // (set by each CTA in its shared-memory copy)

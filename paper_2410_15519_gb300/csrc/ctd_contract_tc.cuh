@@ -271,10 +271,22 @@ __host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_
 // rpart32[row * cmax + (cta - first owner of the row block)].  If dump != null the raw
 // reconstructed values are written to dump[row * ncols_pad + col] instead (test probe).
 // Returns false if a wait expired.
+//
+// Reduced integration domain (Section 3.3), 2D: with tile_max != null only the tiles whose
+// stored max |u(u^2 - 1)| times on_scale (4 a0) exceeds on_tol are contracted; the others
+// add nothing (their rows still get their partial sums written).  tile_max is indexed by
+// the tile of direction 0 (row block of dimension 0, column block of dimension 1).
 static __device__ __noinline__ bool tc_contract(const StepParams& P, const KCompressed* kc, const TcDir& td,
                                    const CUtensorMap* Pmap, const CUtensorMap* Qmap, int x, int Mk, int stages,
-                                   unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump) {
+                                   unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump,
+                                   const unsigned* tile_max = nullptr, float on_scale = 0.f, float on_tol = 0.f) {
   const int G = P.vgrid, cta = P.vrank;
+  auto active = [&](int t) -> bool {
+    if (!tile_max) return true;
+    const int rb = t / td.ntc, cb = t - rb * td.ntc;
+    const int idx = x == 0 ? t : cb * td.nrb + rb;
+    return __uint_as_float(tile_max[idx]) * on_scale > on_tol;
+  };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunks = 2 * P.Kpad / kTcChunkElems;
   const int ksteps = (Mk + 15) / 16;
@@ -326,7 +338,8 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     // ---------------- TMA producer
     fence_proxy_async_global();     // operands were written through the generic proxy
     int cur_rb = -1, a_loads = 0;
-    for (int t = t0, it = 0; t < t1 && ok; ++t, ++it) {
+    for (int t = t0, it = 0; t < t1 && ok; ++t) {
+      if (!active(t)) continue;
       const int rb = t / td.ntc, cb = t - rb * td.ntc;
       if (rb != cur_rb) {
         if (a_loads > 0 && !mbar_wait(&sh->a_empty, (a_loads - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
@@ -342,6 +355,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       for (int ch = 0; ch < chunks; ++ch)
         tma_load_2d(Bs + static_cast<size_t>(s) * stage_bytes + ch * kTcChunkBytes, Qmap, &sh->b_full[s],
                     ch * kTcChunkElems, cb * kTcN);
+      ++it;
     }
     if (!ok) sh->abort = 1;
   } else if (warp == 1 && lane == 0) {
@@ -349,8 +363,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     const uint32_t idesc = umma_idesc_bf16();
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
     const int lo_chunk = P.Kpad / kTcChunkElems;
-    int cur_rb = -1, a_uses = 0;
-    for (int t = t0, it = 0; t < t1 && ok; ++t, ++it) {
+    int cur_rb = -1, a_uses = 0, n_it = 0;
+    for (int t = t0, it = 0; t < t1 && ok; ++t) {
+      if (!active(t)) continue;
       const int rb = t / td.ntc;
       if (rb != cur_rb) {
         if (!mbar_wait(&sh->a_full, a_uses & 1, lim, P.st, abort_flag)) { ok = false; break; }
@@ -377,13 +392,16 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       }
       tc_commit(&sh->b_empty[s]);
       tc_commit(&sh->acc_full[ab]);
-      if (t + 1 == t1 || (t + 1) / td.ntc != rb) tc_commit(&sh->a_empty);
+      int tn = t + 1;   // next tile that is contracted
+      while (tn < t1 && !active(tn)) ++tn;
+      if (tn == t1 || tn / td.ntc != rb) tc_commit(&sh->a_empty);
+      ++it;
+      n_it = it;
     }
     if (!ok) {
       sh->abort = 1;
-    } else if (t1 > t0) {
+    } else if (n_it > 0) {
       // quiesce: the last commits have landed before the barriers are re-initialised
-      const int n_it = t1 - t0;
       for (int s = 0; s < stages && s < n_it; ++s) {
         const int last_it = s + ((n_it - 1 - s) / stages) * stages;
         if (!mbar_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, P.st, abort_flag)) { ok = false; break; }
@@ -404,15 +422,17 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         rpart32[static_cast<size_t>(row) * td.cmax + j] = acc;
       }
     };
-    for (int t = t0, it = 0; t < t1; ++t, ++it) {
+    for (int t = t0, it = 0; t < t1; ++t) {
       const int rb = t / td.ntc, cb = t - rb * td.ntc;
       if (rb != cur_rb) {
         if (cur_rb >= 0) flush(cur_rb);
         acc = 0.f;
         cur_rb = rb;
       }
-      const int ab = it & 1;
-      if (!mbar_wait(&sh->acc_full[ab], (it >> 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      if (!active(t)) continue;
+      const int itc = it++;
+      const int ab = itc & 1;
+      if (!mbar_wait(&sh->acc_full[ab], (itc >> 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
       tc_fence_after();
       const int col0 = cb * kTcN;
       const float* wt;

@@ -270,6 +270,16 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
     tc_prepare(P, X.dirs, X.kr, pb, Mk);
     fence_proxy_async_global();
   }
+  if (P.reduced_tol > 0.0 && Mk > 0) {
+    // reduced integration domain (Section 3.3): the nonlinear term is fixed for the step, so
+    // its 128 x 128 node blocks are classified once
+    if (P.precision == 0) {
+      if (!sync_all(P, epoch, 9)) return;
+      reduce_domain_fp64(P);
+    } else {
+      classify_tiles(P, pb, Mk, reinterpret_cast<float*>(arena_base(smem_raw)));
+    }
+  }
   trace_mark(P, tmark, kTrPrologue);
 
   int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0;
@@ -304,7 +314,8 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
           const TcDir& td = X.dirs[x];
           const CUtensorMap* qmap = (D == 2) ? &tm.op[td.last] : &tm.kr[x];
           if (!tc_contract(P, X.kc, td, &tm.op[x], qmap, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base,
-                           X.rpart32, nullptr))
+                           X.rpart32, nullptr, P.reduced_tol > 0.0 ? P.tile_max : nullptr,
+                           static_cast<float>(4.0 * P.a0), static_cast<float>(P.reduced_tol)))
             return;
         }
         if (P.trace && P.vrank == 0 && threadIdx.x == 0) atomicAdd(P.trace + kTrContract, global_ns() - tsub);

@@ -408,6 +408,85 @@ static __device__ __noinline__ void load_weights_fp64(const StepParams& P, const
   __syncthreads();
 }
 
+// Reduced integration domain on the materialised grid (FP64 path, 2D): every 128 x 128 node
+// block whose largest |W| is not above reduced_tol is set to zero.  Blocks are split over
+// the CTAs; each CTA reads its block, reduces the maximum in a fixed order, then zeroes it.
+static __device__ __noinline__ void reduce_domain_fp64(const StepParams& P) {
+  const int n0 = P.d[0].n, n1 = P.d[1].n;
+  const int nb0 = (n0 + kTcM - 1) / kTcM, nb1 = (n1 + kTcN - 1) / kTcN;
+  double* W = P.W;
+  __shared__ double s_red[kWarps];
+  __shared__ int s_keep;
+  for (int blk = P.vrank; blk < nb0 * nb1; blk += P.vgrid) {
+    const int b0 = blk / nb1, b1 = blk - b0 * nb1;
+    const int r0 = b0 * kTcM, r1 = min(n0, r0 + kTcM), c0 = b1 * kTcN, c1 = min(n1, c0 + kTcN);
+    const int w = c1 - c0, cnt = (r1 - r0) * w;
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int r = r0 + e / w, c = c0 + e % w;
+      mx = fmax(mx, fabs(W[static_cast<size_t>(r) * n1 + c]));
+    }
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int k = 0; k < kWarps; ++k) m = fmax(m, s_red[k]);
+      s_keep = m > P.reduced_tol;
+    }
+    __syncthreads();
+    if (!s_keep)
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int r = r0 + e / w, c = c0 + e % w;
+        W[static_cast<size_t>(r) * n1 + c] = 0.0;
+      }
+    __syncthreads();
+  }
+}
+
+// Reduced integration domain, tensor-core path (2D): max |u(u^2 - 1)| of u^k over every
+// 128 x 128 node block, from the FP32 parts of the factors (the arithmetic of the tiles it
+// gates), into P.tile_max (float bits).  Blocks are split over the CTAs; a block's factor
+// rows are staged in shared memory (sh: 2 * 128 * Mk floats).
+static __device__ __noinline__ void classify_tiles(const StepParams& P, int pb, int Mk, float* sh) {
+  const Dim& d0 = P.d[0];
+  const Dim& d1 = P.d[1];
+  const int n0 = d0.n, n1 = d1.n;
+  const int nb0 = (n0 + kTcM - 1) / kTcM, nb1 = (n1 + kTcN - 1) / kTcN;
+  float* sa = sh;              // [Mk][128] rows of the block, dimension 0
+  float* sb = sh + Mk * kTcM;  // [Mk][128] columns of the block, dimension 1
+  __shared__ float s_red[kWarps];
+  for (int blk = P.vrank; blk < nb0 * nb1; blk += P.vgrid) {
+    const int b0 = blk / nb1, b1 = blk - b0 * nb1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < Mk * kTcM; e += blockDim.x) {
+      const int m = e / kTcM, r = e - m * kTcM;
+      const int i = b0 * kTcM + r, j = b1 * kTcN + r;
+      const float2 a = i < n0 ? d0.bank[pb][static_cast<size_t>(m) * n0 + i] : make_float2(0.f, 0.f);
+      const float2 b = j < n1 ? d1.bank[pb][static_cast<size_t>(m) * n1 + j] : make_float2(0.f, 0.f);
+      sa[e] = a.x + a.y;
+      sb[e] = b.x + b.y;
+    }
+    __syncthreads();
+    float mx = 0.f;
+    for (int e = threadIdx.x; e < kTcM * kTcN; e += blockDim.x) {
+      const int r = e / kTcN, c = e - r * kTcN;
+      float u = 0.f;
+      for (int m = 0; m < Mk; ++m) u = __fmaf_rn(sa[m * kTcM + r], sb[m * kTcM + c], u);
+      mx = fmaxf(mx, fabsf(u * __fmaf_rn(u, u, -1.f)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
+      for (int k = 0; k < kWarps; ++k) m = fmaxf(m, s_red[k]);
+      P.tile_max[blk] = __float_as_uint(m);
+    }
+  }
+  __syncthreads();
+}
+
 // w(u) = dF/du = 4 a0 (u^3 - u) (Eq. energyfunction)
 __device__ __forceinline__ double w_of_u(double u, double a0) { return 4.0 * a0 * (u * u * u - u); }
 

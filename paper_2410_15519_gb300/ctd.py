@@ -31,7 +31,8 @@ class Config(ctypes.Structure):
                 ("I_max", ctypes.c_int), ("tol_als", ctypes.c_double), ("tol_enrich", ctypes.c_double),
                 ("precision", ctypes.c_int), ("fixed_als_iters", ctypes.c_int),
                 ("fixed_modes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
-                ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int)]
+                ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int),
+                ("reduced_tol", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):
@@ -89,7 +90,7 @@ def load() -> ctypes.CDLL:
 
 def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
                 precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
-                grid_ctas=0) -> Config:
+                grid_ctas=0, reduced_tol=0.0) -> Config:
     c = Config()
     c.dim = dim
     for k in range(3):
@@ -101,6 +102,7 @@ def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, 
     c.tol_als, c.tol_enrich = float(tol_als), float(tol_enrich)
     c.precision, c.fixed_als_iters, c.fixed_modes = int(precision), int(fixed_als_iters), int(fixed_modes)
     c.seed, c.wait_limit_s, c.grid_ctas = int(seed), float(wait_limit_s), int(grid_ctas)
+    c.reduced_tol = float(reduced_tol)
     return c
 
 
