@@ -217,11 +217,11 @@ def stored_traffic(workload: str, precision: str):
     return e.get("dram_bytes_per_launch")
 
 
-def timed_run(ctd, torch, w, precision, steps, warmup, flush, clocks=None):
+def timed_run(ctd, torch, w, precision, steps, warmup, flush, clocks=None, reduced_tol=0.0):
     """Advance `steps` time steps after `warmup`; one step kernel launch each, bracketed by CUDA
     events on the solver's stream, L2 flushed between steps."""
     prec = ctd.PREC_FP64 if precision == "fp64" else ctd.PREC_SPLIT_BF16
-    solver = ctd.Solver(ctd.config_from_workload(w, precision=prec))
+    solver = ctd.Solver(ctd.config_from_workload(w, precision=prec, reduced_tol=reduced_tol))
     stream = solver.stream
     solver.set_initial_modes(workloads.initial_modes(w))
     for _ in range(warmup):
@@ -260,7 +260,7 @@ def run_gpu(args, rank, world, local_rank):
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank)
     solver, times_ms, stats, rank0, clk = timed_run(ctd, torch, w, args.precision, args.steps, args.warmup, flush,
-                                                     clocks)
+                                                     clocks, args.reduced_tol)
     if world > 1:
         torch.distributed.barrier()
     total_ms = max_over_ranks(sum(times_ms), world)
@@ -294,7 +294,7 @@ def run_gpu(args, rank, world, local_rank):
     solver.close()
     # first-step result from the initial condition (accuracy check against the oracle)
     prec = ctd.PREC_FP64 if args.precision == "fp64" else ctd.PREC_SPLIT_BF16
-    s2 = ctd.Solver(ctd.config_from_workload(w, precision=prec))
+    s2 = ctd.Solver(ctd.config_from_workload(w, precision=prec, reduced_tol=args.reduced_tol))
     s2.set_initial_modes(workloads.initial_modes(w))
     s2.step(1)
     out["first_step_modes"] = s2.get_modes()
@@ -303,12 +303,14 @@ def run_gpu(args, rank, world, local_rank):
     # and both forms advanced K steps from the initial condition (field error, energy law)
     if args.compare_steps > 0 and rank == 0:
         other = "fp64" if args.precision == "mixed" else "mixed"
-        s3, t3, st3, _, _ = timed_run(ctd, torch, w, other, args.compare_steps, args.warmup, flush)
+        s3, t3, st3, _, _ = timed_run(ctd, torch, w, other, args.compare_steps, args.warmup, flush,
+                                      reduced_tol=args.reduced_tol)
         s3.close()
         traj = {}
         for prec_name in (args.precision, other):
             sv = ctd.Solver(ctd.config_from_workload(
-                w, precision=ctd.PREC_FP64 if prec_name == "fp64" else ctd.PREC_SPLIT_BF16))
+                w, precision=ctd.PREC_FP64 if prec_name == "fp64" else ctd.PREC_SPLIT_BF16,
+                reduced_tol=args.reduced_tol))
             sv.set_initial_modes(workloads.initial_modes(w))
             energies = [sv.energy()]
             first = None
@@ -330,6 +332,19 @@ def run_gpu(args, rank, world, local_rank):
                                                            zip(v["energies"], v["energies"][1:]))
                                                     for k, v in traj.items()},
                               energy_first_last={k: [v["energies"][0], v["energies"][-1]] for k, v in traj.items()})
+    if args.reduced_tol > 0 and args.compare_steps > 0 and rank == 0:
+        sf, tf, stf, _, _ = timed_run(ctd, torch, w, args.precision, args.compare_steps, args.warmup, flush)
+        sf.close()
+        trajs = []
+        for tol in (args.reduced_tol, 0.0):
+            sv = ctd.Solver(ctd.config_from_workload(
+                w, precision=ctd.PREC_FP64 if args.precision == "fp64" else ctd.PREC_SPLIT_BF16, reduced_tol=tol))
+            sv.set_initial_modes(workloads.initial_modes(w))
+            sv.step(args.compare_steps, stats=False)
+            trajs.append(sv.get_modes())
+            sv.close()
+        out["full_domain"] = dict(steps=len(tf), ms_per_step=sum(tf) / len(tf),
+                                  u_rel_l2_reduced_vs_full=sep_rel_l2(trajs[0], trajs[1]))
     return w, out
 
 
@@ -560,6 +575,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--compare-steps", type=int, default=10,
                     help="steps of the other arithmetic (FP64 vs mixed) timed for the side-by-side numbers")
+    ap.add_argument("--reduced-tol", type=float, default=0.0,
+                    help="reduced integration domain: drop 128 x 128 node blocks with max |w(u^k)| <= this")
     ap.add_argument("--oracle-budget", type=float, default=25.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -573,7 +590,7 @@ def main():
     w = workloads.preset(args.workload)
     config = {"workload": f"{w.name}: {w.dim}D {'x'.join(map(str, w.n))} nodes, s={w.s} p={w.p}, eps={w.eps}, "
                           f"S={w.S}, dt={w.dt}, M_max={w.M_max}, tol_als={w.tol_als}, tol_enrich={w.tol_enrich}",
-              "grid_points": w.grid_points, "ic": f"rank-{w.ic_rank} seeded cosine modes",
+              "grid_points": w.grid_points, "ic": (f"rank-{w.ic_rank} seeded cosine modes" + (" + tanh interface mode" if w.ic_tanh else "")),
               "precision": args.precision,
               "l2": "256 MB buffer written between timed steps (L2 flush)"}
 
@@ -643,6 +660,13 @@ def main():
             "note": "one half-sweep's tensor-core contraction as timed by CTA 0's global-timer trace "
                     "(until its own tiles are done); roof = max(split MMA at sustained BF16 peak, "
                     "3 FP32 instructions per grid point)"}
+    if args.reduced_tol > 0:
+        line["config"]["reduced_tol"] = args.reduced_tol
+        if "full_domain" in res:
+            fd = res["full_domain"]
+            line["full_domain"] = {"ms_per_step": fd["ms_per_step"], "value": 1e3 / fd["ms_per_step"],
+                                   "u_rel_l2_reduced_vs_full": fd["u_rel_l2_reduced_vs_full"],
+                                   "note": f"same workload without the reduced domain, {fd['steps']} steps"}
     if "compare" in res:
         c = res["compare"]
         line["compare"] = {"precision": c["precision"], "steps": c["steps"], "ms_per_step": c["ms_per_step"],

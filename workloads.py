@@ -129,6 +129,9 @@ def preset(name: str, **overrides) -> Workload:
                    seed=0, ic_rank=4, ic_k=4),
         "c1": dict(dim=2, n=(4096, 4096), s=2, p=2, eps=0.01, dt=1e-3, steps=1000, M_max=50,
                    seed=1, ic_rank=8, ic_k=4),
+        # c1 from a phase-separated state: one straight interface (tanh profile) across x
+        "c1i": dict(dim=2, n=(4096, 4096), s=2, p=2, eps=0.01, dt=1e-3, steps=1000, M_max=50,
+                    seed=1, ic_rank=0, ic_k=4, ic_tanh=True),
         "c2": dict(dim=3, n=(512, 512, 512), s=2, p=2, eps=0.02, dt=5e-3, steps=500,
                    M_max=60, seed=2, ic_rank=6, ic_k=6, ic_tanh=True),
         "c3": dict(dim=3, n=(1024, 1024, 1024), s=3, p=3, eps=0.01, dt=2e-3, steps=200,
