@@ -152,8 +152,14 @@ struct TcPlan {
   int cmax;       // partial slots per row
 };
 
+// The first kLightCtas CTAs also compute the Gram partial sums before their tiles; they take
+// half the tiles of the others so that all finish together.
+constexpr int kLightCtas = 16;
 __host__ __device__ inline int tile_lo(long long T, int G, int c) {
-  return static_cast<int>(T * c / G);
+  const int L = G < kLightCtas ? G : kLightCtas;
+  const long long cum = (c < L ? c : L) + 2LL * (c > L ? c - L : 0);
+  const long long tot = L + 2LL * (G - L);
+  return static_cast<int>(T * cum / tot);
 }
 // CTA that owns tile t under the contiguous split [tile_lo(c), tile_lo(c+1))
 __host__ __device__ inline int tile_owner(long long T, int G, long long t) {

@@ -75,7 +75,7 @@ __device__ inline int pow2_floor(int x) {
 constexpr int kChunk = 256;
 // Gram and convergence partial sums are computed by this many CTAs (fewer partials to reduce
 // after the grid-wide wait: every CTA reads all of them)
-constexpr int kGramCtas = 16;
+constexpr int kGramCtas = kLightCtas;   // the lighter-loaded contraction CTAs
 
 __device__ __forceinline__ int gram_ctas(const StepParams& P) { return P.vgrid < kGramCtas ? P.vgrid : kGramCtas; }
 
