@@ -153,20 +153,29 @@ struct TcPlan {
 };
 
 // The first kLightCtas CTAs also compute the Gram partial sums before their tiles; they take
-// half the tiles of the others so that all finish together.
+// half the tiles of the others so that all finish together.  CTA c owns the contiguous tile
+// range [tile_lo(c), tile_lo(c + 1)) with tile_lo(c) = floor(T cum(c) / tot), cum(c) the
+// number of half-weight units before c (1 per light CTA, 2 per other) and tot = cum(G).
 constexpr int kLightCtas = 16;
-__host__ __device__ inline int tile_lo(long long T, int G, int c) {
+__host__ __device__ inline long long tile_cum(int G, int c) {
   const int L = G < kLightCtas ? G : kLightCtas;
-  const long long cum = (c < L ? c : L) + 2LL * (c > L ? c - L : 0);
-  const long long tot = L + 2LL * (G - L);
-  return static_cast<int>(T * cum / tot);
+  return c <= L ? c : L + 2LL * (c - L);
 }
-// CTA that owns tile t under the contiguous split [tile_lo(c), tile_lo(c+1))
+// floor(a / b) for a, b >= 0; 32-bit division when both fit
+__host__ __device__ inline long long tile_div(long long a, long long b) {
+  if (a < 0xFFFFFFFFLL) return static_cast<long long>(static_cast<unsigned>(a) / static_cast<unsigned>(b));
+  return a / b;
+}
+__host__ __device__ inline int tile_lo(long long T, int G, int c) {
+  return static_cast<int>(tile_div(T * tile_cum(G, c), tile_cum(G, G)));
+}
+// CTA that owns tile t (0 <= t < T): the largest c < G with tile_lo(c) <= t, i.e. with
+// cum(c) <= kmax = floor(((t + 1) tot - 1) / T)
 __host__ __device__ inline int tile_owner(long long T, int G, long long t) {
-  int c = static_cast<int>((t * G) / T);
-  while (c + 1 < G && tile_lo(T, G, c + 1) <= t) ++c;
-  while (c > 0 && tile_lo(T, G, c) > t) --c;
-  return c;
+  const int L = G < kLightCtas ? G : kLightCtas;
+  const long long kmax = tile_div((t + 1) * tile_cum(G, G) - 1, T);
+  const long long c = kmax <= L ? kmax : L + (kmax - L) / 2;
+  return static_cast<int>(c < G - 1 ? c : G - 1);
 }
 
 struct TcShared {           // barriers and TMEM handle (placed at the start of the arena)
@@ -238,12 +247,15 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
   }
 }
 
-// FP32 column weights 4 a0 omega_d v_d of dimension d into shared memory (zero padded).
-__device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, int d, float* w, int npad) {
+// FP32 column weights 4 a0 omega_d v_d of dimension d into shared memory (zero padded),
+// entries [lo, hi) of [0, npad).
+__device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, int d, float* w, int npad,
+                                  int lo = 0, int hi = 1 << 30) {
   const Dim& dd = P.d[d];
   const float s = static_cast<float>(4.0 * P.a0);
+  if (hi > npad) hi = npad;
   constexpr int kGroup = 8;   // loads of eight entries first, so that their latencies overlap
-  for (int i0 = threadIdx.x; i0 < npad; i0 += kGroup * blockDim.x) {
+  for (int i0 = lo + threadIdx.x; i0 < hi; i0 += kGroup * blockDim.x) {
     float2 x[kGroup];
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
@@ -253,7 +265,7 @@ __device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, in
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
       const int i = i0 + g * blockDim.x;
-      if (i < npad) w[i] = i < dd.n ? s * kc_omega(kc, i).x * (x[g].x + x[g].y) : 0.f;
+      if (i < hi) w[i] = i < dd.n ? s * kc_omega(kc, i).x * (x[g].x + x[g].y) : 0.f;
     }
   }
 }
@@ -317,9 +329,21 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     sh->abort = 0;
     fence_barrier_init();
   }
-  // column weights of the fixed factors
-  tc_weights(P, kc[td.last], td.last, wl, wl_n);
-  if (td.mid >= 0) tc_weights(P, kc[td.mid], td.mid, wm, wm_n);
+  // column weights of the fixed factors; in 2D only those of this CTA's column blocks
+  if (td.mid >= 0) {
+    tc_weights(P, kc[td.last], td.last, wl, wl_n);
+    tc_weights(P, kc[td.mid], td.mid, wm, wm_n);
+  } else if (t1 - t0 >= td.ntc) {
+    tc_weights(P, kc[td.last], td.last, wl, wl_n);
+  } else if (t1 > t0) {
+    const int cb_lo = t0 % td.ntc, cb_hi = (t1 - 1) % td.ntc;
+    if (cb_lo <= cb_hi) {
+      tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, (cb_hi + 1) * kTcN);
+    } else {   // the range wraps into the next row block
+      tc_weights(P, kc[td.last], td.last, wl, wl_n, 0, (cb_hi + 1) * kTcN);
+      tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, wl_n);
+    }
+  }
   __syncthreads();
   if (Mk == 0 || ksteps == 0) {
     // u^k = 0: w(0) = 0, every partial is zero

@@ -23,6 +23,7 @@ __host__ __device__ inline size_t arena_phase_a_bytes() {
   return sizeof(double) * kMaxDim * kMaxN > sizeof(float2) * 3 * kChunk ? sizeof(double) * kMaxDim * kMaxN
                                                                          : sizeof(float2) * 3 * kChunk;
 }
+static_assert(kCoefScratchBytes <= sizeof(double) * kMaxDim * kMaxN, "coefficient scratch exceeds the arena");
 __host__ __device__ inline size_t solver_smem_offset(int n_max) { return (sizeof(float2) * n_max + 127) / 128 * 128; }
 
 struct Arena {
@@ -322,7 +323,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
         if (!sync_all(P, epoch, 3)) return;
         trace_mark(P, tmark, kTrGramContract);
         // Phase B: coefficients (every CTA, same order) and right-hand-side rows
-        build_coefficients(P, x, Mk, M, &sm.coef, sm.red2);
+        build_coefficients(P, x, Mk, M, &sm.coef, ar.gram_rows);
         rhs_rows(P, X, x, Mk, M, pb, cb, &sm.coef);
         if (!sync_all(P, epoch, 4)) return;
         trace_mark(P, tmark, kTrRhs);
@@ -347,12 +348,28 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
       {
         __shared__ double s_dots[kMaxDim * 6];
         __shared__ double s_max[kMaxDim];
+        // the D * 6 dot slots and D max slots: 16 lanes per slot, lane g holds CTA g's
+        // partial; all loads issued together, then fixed xor trees
         const int Gg = gram_ctas(P);
-        if (threadIdx.x < D * 6) s_dots[threadIdx.x] = df_to_double(reduce_slot(P.gram + static_cast<size_t>(threadIdx.x) * Gg, Gg));
-        if (threadIdx.x < D) {
-          double mx = 0.0;
-          for (int g = 0; g < Gg; ++g) mx = fmax(mx, X.maxpart[threadIdx.x * Gg + g]);
-          s_max[threadIdx.x] = mx;
+        const int g = threadIdx.x & 15, sub = threadIdx.x >> 4, nd = D * 6, nu = nd + D;
+        float2 pv[2];
+        double pm[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int u = r * (kThreads / 16) + sub;
+          pv[r] = make_float2(0.f, 0.f);
+          pm[r] = 0.0;
+          if (g < Gg && u < nd) pv[r] = P.gram[static_cast<size_t>(u) * Gg + g];
+          else if (g < Gg && u < nu) pm[r] = X.maxpart[(u - nd) * Gg + g];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int u = r * (kThreads / 16) + sub;
+          const dfloat t = group_sum(dfloat{pv[r].x, pv[r].y}, 16);
+          double mx = pm[r];
+          for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          if (g == 0 && u < nd) s_dots[u] = df_to_double(t);
+          else if (g == 0 && u < nu) s_max[u - nd] = mx;
         }
         __syncthreads();
         // ||(x)new - (x)old||^2 = sum_{d,e} prod_c <T_d(c), T_e(c)>, factor of T_d at c:

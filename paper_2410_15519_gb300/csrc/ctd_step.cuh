@@ -154,20 +154,6 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
   }
 }
 
-// Sum the G partials of one slot in a fixed order (four interleaved accumulators).
-__device__ inline dfloat reduce_slot(const float2* part, int G) {
-  dfloat a0 = {0.f, 0.f}, a1 = a0, a2 = a0, a3 = a0;
-  int g = 0;
-  for (; g + 3 < G; g += 4) {
-    a0 = df_add(a0, ld_df(part + g));
-    a1 = df_add(a1, ld_df(part + g + 1));
-    a2 = df_add(a2, ld_df(part + g + 2));
-    a3 = df_add(a3, ld_df(part + g + 3));
-  }
-  for (; g < G; ++g) a0 = df_add(a0, ld_df(part + g));
-  return df_add(df_add(a0, a1), df_add(a2, a3));
-}
-
 // Coefficients of Eq. KxQx for direction x, in shared memory (double-float):
 // coef[0] = alpha1, coef[1] = alpha2, H[m] = prod_{d!=x} h_d,m, GM[m] = prod gM_d,m,
 // GK[m] = sum_{d'} gK_{d',m} prod_{d != x,d'} gM_d,m.
@@ -176,49 +162,70 @@ struct Coef {
   float2 H[kMaxModes], GM[kMaxModes], GK[kMaxModes];
 };
 
+// Used Gram slots of one fixed dimension: m_d, k_d, gM (M), gK (M), h (Mk)
+__host__ __device__ inline int coef_slots(int M, int Mk) { return 2 + 2 * M + Mk; }
+constexpr size_t kCoefScratchBytes = sizeof(float2) * (kMaxDim - 1) * (2 + 3 * kMaxModes);
+
+// Every used slot's G partials are loaded at once (16 lanes per slot, lane g holds CTA g's
+// partial, G <= 16) and summed by a fixed xor tree, so that all CTAs get the same bits.
+// scratch: kCoefScratchBytes of shared memory.
 static __device__ __noinline__ void build_coefficients(const StepParams& P, int x, int Mk, int M, Coef* c,
-                                   float2* red /* >= 2*kMaxDim float2 */) {
+                                   float2* scratch) {
   const int G = gram_ctas(P), D = P.dim, spd = slots_per_dim(P.Mcap);
-  const int nO = D - 1;
-  // m_d, k_d of the fixed factors
-  if (threadIdx.x < 2 * nO) {
-    const int o = threadIdx.x >> 1, s = threadIdx.x & 1;
-    st_df(red + threadIdx.x, reduce_slot(P.gram + static_cast<size_t>(o * spd + s) * G, G));
-  }
-  for (int m = threadIdx.x; m < max(M, Mk); m += blockDim.x) {
-    dfloat gm[kMaxDim - 1], gk[kMaxDim - 1];
-    dfloat H = {1.f, 0.f};
-    for (int o = 0; o < nO; ++o) {
-      const float2* base = P.gram + static_cast<size_t>(o * spd) * G;
-      if (m < M) {
-        gm[o] = reduce_slot(base + static_cast<size_t>(2 + m) * G, G);
-        gk[o] = reduce_slot(base + static_cast<size_t>(2 + P.Mcap + m) * G, G);
+  const int nO = D - 1, per = coef_slots(M, Mk), nsl = nO * per;
+  const int g = threadIdx.x & 15, sub = threadIdx.x >> 4;
+  constexpr int kSub = kThreads / 16;   // slots per round
+  constexpr int kRounds = 4;            // rounds whose loads are issued together
+  for (int u0 = 0; u0 < nsl; u0 += kSub * kRounds) {
+    float2 v[kRounds];
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const int u = u0 + r * kSub + sub;
+      v[r] = make_float2(0.f, 0.f);
+      if (u < nsl && g < G) {
+        const int o = u / per, k = u - o * per;
+        int slot;
+        if (k < 2 + M) slot = k;                                     // m_d, k_d, gM
+        else if (k < 2 + 2 * M) slot = 2 + P.Mcap + (k - 2 - M);     // gK
+        else slot = 2 + 2 * P.Mcap + (k - 2 - 2 * M);                // h
+        v[r] = P.gram[static_cast<size_t>(o * spd + slot) * G + g];
       }
-      if (m < Mk) H = df_mul(H, reduce_slot(base + static_cast<size_t>(2 + 2 * P.Mcap + m) * G, G));
     }
-    if (m < Mk) st_df(c->H + m, H);
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const int u = u0 + r * kSub + sub;
+      const dfloat t = group_sum(dfloat{v[r].x, v[r].y}, 16);
+      if (u < nsl && g == 0) st_df(scratch + u, t);
+    }
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < max(M, Mk); m += blockDim.x) {
+    if (m < Mk) {
+      dfloat H = {1.f, 0.f};
+      for (int o = 0; o < nO; ++o) H = df_mul(H, ld_df(scratch + o * per + 2 + 2 * M + m));
+      st_df(c->H + m, H);
+    }
     if (m < M) {
       dfloat GM = {1.f, 0.f}, GK = {0.f, 0.f};
-      for (int o = 0; o < nO; ++o) GM = df_mul(GM, gm[o]);
+      for (int o = 0; o < nO; ++o) GM = df_mul(GM, ld_df(scratch + o * per + 2 + m));
       for (int o2 = 0; o2 < nO; ++o2) {
-        dfloat t = gk[o2];
+        dfloat t = ld_df(scratch + o2 * per + 2 + M + m);
         for (int o = 0; o < nO; ++o)
-          if (o != o2) t = df_mul(t, gm[o]);
+          if (o != o2) t = df_mul(t, ld_df(scratch + o * per + 2 + m));
         GK = df_add(GK, t);
       }
       st_df(c->GM + m, GM);
       st_df(c->GK + m, GK);
     }
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
     const dfloat ct = ld_df(&P.ct_df), ck = ld_df(&P.ck_df);
     dfloat pm = {1.f, 0.f}, stiff = {0.f, 0.f};
-    for (int o = 0; o < nO; ++o) pm = df_mul(pm, ld_df(red + 2 * o));
+    for (int o = 0; o < nO; ++o) pm = df_mul(pm, ld_df(scratch + o * per));
     for (int o2 = 0; o2 < nO; ++o2) {
-      dfloat t = ld_df(red + 2 * o2 + 1);
+      dfloat t = ld_df(scratch + o2 * per + 1);
       for (int o = 0; o < nO; ++o)
-        if (o != o2) t = df_mul(t, ld_df(red + 2 * o));
+        if (o != o2) t = df_mul(t, ld_df(scratch + o * per));
       stiff = df_add(stiff, t);
     }
     st_df(&c->alpha1, df_add(df_mul(ct, pm), df_mul(ck, stiff)));

@@ -1,7 +1,12 @@
 """Reduced integration domain (Section 3.3) on the GPU against the oracle with the same
 reading (128 x 128 node blocks dropped while max |w(u^k)| <= reduced_tol): a straight
 interface across a 640 x 300 grid leaves one block row of five in the domain.  FP64 path
-within 1e-12, split-BF16 path within 1e-5 (u and energy)."""
+within 1e-12, split-BF16 path within 1e-5 (u and energy).
+
+The energy of a sharp interface is a sum of terms much larger than itself (the stiffness
+products of the nearly constant regions cancel), so its FP64 evaluation, in either program,
+carries a relative error up to cond_E 2^-53 with cond_E = sum |terms| / |E| (about 1.2e4
+here, i.e. 1.4e-12); the energy tolerance adds four times that bound."""
 import numpy as np
 import pytest
 
@@ -19,6 +24,24 @@ def lib():
     from paper_2410_15519_gb300 import build, ctd
     build.build()
     return ctd
+
+
+def energy_condition(prob, ops, A):
+    """sum of |terms| of the discrete energy over |E| (nodal bulk term + stiffness term)."""
+    U = octd.reconstruct(A)
+    Wg = octd.grid_weights(ops)
+    absum = float(np.sum(np.abs(Wg * prob.a0 * (U ** 2 - 1.0) ** 2)))
+    for d in range(prob.dim):
+        T = np.moveaxis(np.abs(U), d, 0)
+        KT = np.moveaxis((abs(ops.K[d]) @ T.reshape(T.shape[0], -1)).reshape(T.shape), 0, d)
+        ow = np.ones_like(U)
+        for e in range(prob.dim):
+            if e != d:
+                sh = [1] * prob.dim
+                sh[e] = -1
+                ow = ow * ops.omega[e].reshape(sh)
+        absum += 0.5 * prob.kappa * float(np.sum(np.abs(U) * KT * ow))
+    return absum / abs(octd.energy(prob, ops, A))
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
@@ -46,7 +69,8 @@ def test_reduced_domain_matches_oracle(lib, prec, tol):
         G = s.get_modes()
         assert octd.rel_l2_between(G, A) < tol, (k, octd.rel_l2_between(G, A))
         eo = octd.energy(prob, ops, A)
-        assert abs(s.energy() - eo) / abs(eo) < tol, k
+        tol_e = tol + 4.0 * energy_condition(prob, ops, A) * 2.0 ** -53
+        assert abs(s.energy() - eo) / abs(eo) < tol_e, (k, abs(s.energy() - eo) / abs(eo), tol_e)
     s.close()
 
 
