@@ -10,7 +10,6 @@
 #include <vector>
 
 #include <cuda.h>
-#include <cudaTypedefs.h>
 
 #include "ctd.h"
 #include "cfem_host.h"
@@ -235,7 +234,6 @@ struct ctd_ctx {
   StepStatsDev* stats_dev;
   unsigned long long* trace_dev;
   double mu_max[3];
-  ctd::TmapSet tm;
   std::vector<double> omega[3], kband[3];
   bool has_modes;
   std::string err;
@@ -503,40 +501,6 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     }
     P.smem_bytes = static_cast<int>(need);
   }
-  if (cfg->precision == CTD_PREC_SPLIT_BF16) {
-    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    CTD_CUDA(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", reinterpret_cast<void**>(&encode), 12000,
-                                                 cudaEnableDefault, &q));
-    if (!encode || q != cudaDriverEntryPointSuccess) {
-      ctd_status s = fail(h, CTD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-      delete h;
-      return s;
-    }
-    auto make_map = [&](CUtensorMap* m, void* ptr, long long rows) -> bool {
-      const cuuint64_t dims[2] = {static_cast<cuuint64_t>(2 * h->plan.Kpad), static_cast<cuuint64_t>(rows)};
-      const cuuint64_t strides[1] = {static_cast<cuuint64_t>(2 * h->plan.Kpad) * sizeof(__nv_bfloat16)};
-      const cuuint32_t box[2] = {static_cast<cuuint32_t>(ctd::kTcChunkElems), static_cast<cuuint32_t>(ctd::kTcM)};
-      const cuuint32_t es[2] = {1, 1};
-      return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-    };
-    std::memset(&h->tm, 0, sizeof(h->tm));
-    for (int d = 0; d < cfg->dim; ++d)
-      if (!make_map(&h->tm.op[d], P.d[d].op, h->plan.n_pad[d])) {
-        ctd_status s = fail(h, CTD_ERR_CUDA, "tensor map encoding failed");
-        delete h;
-        return s;
-      }
-    if (cfg->dim == 3)
-      for (int x = 0; x < 3; ++x)
-        if (!make_map(&h->tm.kr[x], X.kr[x], h->plan.dirs[x].ncols_pad)) {
-          ctd_status s = fail(h, CTD_ERR_CUDA, "tensor map encoding failed");
-          delete h;
-          return s;
-        }
-  }
   InstState st{};
   CTD_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
   CTD_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -594,7 +558,7 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
     for (int k = 0; k < batch; ++k) {
       h->P.stats = h->stats_dev + k;
       CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-      CTD_CUDA(h, ctd::launch_step(h->P, h->X, h->tm, h->grid, h->stream));
+      CTD_CUDA(h, ctd::launch_step(h->P, h->X, h->grid, h->stream));
     }
     if (stats) {
       rec.resize(batch);
@@ -656,7 +620,6 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
   for (int i = 0; i < count; ++i) {
     ctd_ctx* h = handles[i];
     std::memset(&entries[i], 0, sizeof(ctd::BatchEntry));
-    entries[i].tm = h->tm;
     entries[i].P = h->P;
     entries[i].P.stats = h->stats_dev;
     entries[i].P.trace = nullptr;
@@ -793,7 +756,7 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
     CTD_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->tm, h->grid, x, nullptr, h->stream));
+  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, nullptr, h->stream));
   const int n = h->cfg.n[x];
   if (h->cfg.precision == CTD_PREC_FP64) {
     const int C = h->plan.rchunks[x];
@@ -845,7 +808,7 @@ ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch,
   }
   CTD_CUDA(h, cudaMemsetAsync(scratch, 0, need, h->stream));
   CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->tm, h->grid, x, static_cast<float*>(scratch), h->stream));
+  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, static_cast<float*>(scratch), h->stream));
   CTD_CUDA(h, cudaMemcpyAsync(out, scratch, need, cudaMemcpyDeviceToHost, h->stream));
   CTD_CUDA(h, cudaStreamSynchronize(h->stream));
   InstState st;
@@ -880,7 +843,7 @@ ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out) {
   }
   CTD_CUDA(h, cudaMemsetAsync(scratch, 0, need, h->stream));
   CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->tm, h->grid, x, static_cast<float*>(scratch), h->stream));
+  CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, static_cast<float*>(scratch), h->stream));
   CTD_CUDA(h, cudaMemcpyAsync(out, scratch, need, cudaMemcpyDeviceToHost, h->stream));
   CTD_CUDA(h, cudaStreamSynchronize(h->stream));
   InstState st;

@@ -3,8 +3,10 @@
 // For direction x, with P the factors of u^k in dimension x (n_x x M_k) and Q the factors of
 // the other dimension (2D) or their row-wise (Khatri-Rao) products (3D), the grid values
 // of u^k are U = P Q^T.  Each CTA walks a contiguous range of 128 x 128 tiles of U:
-//   * TMA loads P's 128-row block once per row block and Q's 128-row column blocks through a
-//     ring of stages (128-byte swizzled, K-major BF16);
+//   * the operands are stored as tile images: per 128-row block and 16-wide K step a hi and a
+//     lo image of 128 x 16 BF16 in the canonical K-major layout without swizzle, so that one
+//     bulk TMA copy (cp.async.bulk) brings a row block's K steps into shared memory: P's
+//     block once per row block, Q's column blocks through a ring of stages;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in TMEM) for the
 //     split product U = P_hi Q_hi^T + P_hi Q_lo^T + P_lo Q_hi^T (P = P_hi + P_lo in BF16);
 //   * four epilogue warps read the accumulator rows with tcgen05.ld and fuse the cubic
@@ -13,7 +15,6 @@
 //   * two TMEM accumulators alternate so the MMAs of tile t+1 overlap the epilogue of t.
 // Every wait is bounded in time; on expiry the kernel records kErrTimeout and unwinds.
 #pragma once
-#include <cuda.h>
 
 #include "ctd_common.cuh"
 #include "ctd_solve.cuh"
@@ -22,14 +23,23 @@ namespace ctd {
 
 constexpr int kTcN = 128;              // columns per tile (UMMA N)
 constexpr int kTcM = 128;              // rows per tile (UMMA M)
-constexpr int kTcChunkElems = 64;      // BF16 elements per 128-byte swizzle row
-constexpr int kTcChunkBytes = kTcM * 128;   // one 128-row x 128-byte TMA box (16 KB)
+// Shared-memory sizing unit: a row block's image of 2 Kpad K columns (hi and lo) takes
+// (2 Kpad / kTcChunkElems) units of kTcChunkBytes
+constexpr int kTcChunkElems = 64;
+constexpr int kTcChunkBytes = kTcM * 128;   // 16 KB
 constexpr int kTcAccCols = 2 * kTcN;   // TMEM columns allocated (two accumulators)
 
-struct TmapSet {
-  CUtensorMap op[kMaxDim];    // per-dimension operand [n_pad][2*Kpad] BF16 (hi | lo)
-  CUtensorMap kr[kMaxDim];    // 3D: Khatri-Rao operand of the two dimensions other than x
-};
+// Tile-image operand layout.  Rows come in blocks of 128; a block holds KS = Kpad / 16 K steps,
+// each a hi and a lo image of 4 KB: 16 groups of 8 rows (256 bytes apart), each group two core
+// matrices of 8 rows x 8 columns (128 contiguous bytes, the second holding columns 8..15).
+constexpr int kTcImgElems = kTcM * 16;                  // elements of one image
+constexpr uint32_t kTcImgBytes = kTcImgElems * 2;       // 4 KB
+__host__ __device__ inline size_t tc_img_index(long long i, int k, int h, int KS) {
+  const long long rb = i >> 7;
+  const int r = static_cast<int>(i & 127), g = r >> 3, rr = r & 7;
+  const int ks = k >> 4, j = (k >> 3) & 1, e = k & 7;
+  return static_cast<size_t>(((rb * KS + ks) * 2 + h) * kTcImgElems) + g * 128 + j * 64 + rr * 8 + e;
+}
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -78,11 +88,12 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
+// Bulk TMA copy global -> shared (both 16-byte aligned, bytes a multiple of 16), completion
+// counted on the mbarrier's transaction bytes
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -124,15 +135,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor of one tile image: K-major, no swizzle, core matrices
+// adjacent in K 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart (stride
+// byte offset).
+__device__ __forceinline__ uint64_t umma_desc_img(uint32_t saddr) {
   uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);        // start address
-  d |= static_cast<uint64_t>(1) << 16;                       // leading byte offset (unused here)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;               // stride byte offset
-  d |= static_cast<uint64_t>(1) << 46;                       // descriptor version
-  d |= static_cast<uint64_t>(2) << 61;                       // 128-byte swizzle
-  return d;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFF) >> 4);   // start address
+  d |= static_cast<uint64_t>(128 >> 4) << 16;           // leading byte offset
+  d |= static_cast<uint64_t>(256 >> 4) << 32;           // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                  // descriptor version
+  return d;                                             // swizzle mode 0: none
 }
 // Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = kTcN.
 __host__ __device__ constexpr uint32_t umma_idesc_bf16() {
@@ -200,27 +212,53 @@ struct TcDir {
   int cmax;         // partial slots per row in rpart32
 };
 
-// Split u^k's factors into BF16 hi/lo operands [n_pad][2*Kpad] and, in 3D, the Khatri-Rao
-// operands of the two other dimensions for every direction.  Grid-stride over all CTAs.
+// Split u^k's factors into BF16 hi/lo tile-image operands and, in 3D, the Khatri-Rao operands
+// of the two other dimensions for every direction.  Only the K steps that hold modes are
+// written.  One unit = 8 consecutive K columns of one row (one 16-byte core-matrix row of the
+// hi and of the lo image); units in image order, grid-stride over all CTAs.
 static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir* dirs, __nv_bfloat16* const* kr, int pb,
                                   int Mk) {
-  const int Kp = P.Kpad, W = 2 * Kp;
+  const int KS = P.Kpad / 16, ksteps = (Mk + 15) / 16;
   const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
   const long long t0 = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x;
+  // unit u -> (row block, K step, group, core matrix, row in group)
+  auto unit = [&](long long u, long long& i, int& k0) {
+    const int rr = static_cast<int>(u & 7), j = static_cast<int>((u >> 3) & 1), g = static_cast<int>((u >> 4) & 15);
+    const long long q = u >> 8;
+    const int ks = static_cast<int>(q % ksteps);
+    i = (q / ksteps) * 128 + g * 8 + rr;
+    k0 = ks * 16 + j * 8;
+  };
+  auto store = [&](__nv_bfloat16* op, long long i, int k0, const float (&a)[8]) {
+    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      hi[e] = __float2bfloat16_rn(a[e]);
+      lo[e] = __float2bfloat16_rn(a[e] - __bfloat162float(hi[e]));
+    }
+    const size_t o = tc_img_index(i, k0, 0, KS);
+    *reinterpret_cast<uint4*>(op + o) = *reinterpret_cast<const uint4*>(hi);
+    *reinterpret_cast<uint4*>(op + o + kTcImgElems) = *reinterpret_cast<const uint4*>(lo);
+  };
+  if (ksteps == 0) return;
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
-    const long long total = static_cast<long long>(dd.n_pad) * Kp;
-    for (long long t = t0; t < total; t += stride) {
-      const int i = static_cast<int>(t / Kp), k = static_cast<int>(t - static_cast<long long>(i) * Kp);
-      float a = 0.f;
-      if (i < dd.n && k < Mk) {
-        const float2 v = dd.bank[pb][static_cast<size_t>(k) * dd.n + i];
-        a = v.x + v.y;
+    const long long total = static_cast<long long>(dd.n_pad) * ksteps * 2;
+    for (long long u = t0; u < total; u += stride) {
+      long long i;
+      int k0;
+      unit(u, i, k0);
+      float a[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        a[e] = 0.f;
+        if (i < dd.n && k < Mk) {
+          const float2 v = dd.bank[pb][static_cast<size_t>(k) * dd.n + i];
+          a[e] = v.x + v.y;
+        }
       }
-      const __nv_bfloat16 hi = __float2bfloat16_rn(a);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(a - __bfloat162float(hi));
-      dd.op[static_cast<size_t>(i) * W + k] = hi;
-      dd.op[static_cast<size_t>(i) * W + Kp + k] = lo;
+      store(dd.op, i, k0, a);
     }
   }
   if (P.dim != 3) return;
@@ -228,21 +266,24 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
     const TcDir& td = dirs[x];
     const Dim& dm = P.d[td.mid];
     const Dim& dl = P.d[td.last];
-    const long long total = static_cast<long long>(dm.n) * td.n_last_pad * Kp;
-    for (long long t = t0; t < total; t += stride) {
-      const long long row = t / Kp;
-      const int k = static_cast<int>(t - row * Kp);
+    const long long total = static_cast<long long>(td.ncols_pad) * ksteps * 2;
+    for (long long u = t0; u < total; u += stride) {
+      long long row;
+      int k0;
+      unit(u, row, k0);
       const int j = static_cast<int>(row / td.n_last_pad), l = static_cast<int>(row - static_cast<long long>(j) * td.n_last_pad);
-      float a = 0.f;
-      if (l < dl.n && k < Mk) {
-        const float2 vm = dm.bank[pb][static_cast<size_t>(k) * dm.n + j];
-        const float2 vl = dl.bank[pb][static_cast<size_t>(k) * dl.n + l];
-        a = (vm.x + vm.y) * (vl.x + vl.y);
+      float a[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        a[e] = 0.f;
+        if (j < dm.n && l < dl.n && k < Mk) {
+          const float2 vm = dm.bank[pb][static_cast<size_t>(k) * dm.n + j];
+          const float2 vl = dl.bank[pb][static_cast<size_t>(k) * dl.n + l];
+          a[e] = (vm.x + vm.y) * (vl.x + vl.y);
+        }
       }
-      const __nv_bfloat16 hi = __float2bfloat16_rn(a);
-      const __nv_bfloat16 lo = __float2bfloat16_rn(a - __bfloat162float(hi));
-      kr[x][static_cast<size_t>(row) * W + k] = hi;
-      kr[x][static_cast<size_t>(row) * W + Kp + k] = lo;
+      store(kr[x], row, k0, a);
     }
   }
 }
@@ -295,7 +336,7 @@ __host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_
 // add nothing (their rows still get their partial sums written).  tile_max is indexed by
 // the tile of direction 0 (row block of dimension 0, column block of dimension 1).
 static __device__ __noinline__ bool tc_contract(const StepParams& P, const KCompressed* kc, const TcDir& td,
-                                   const CUtensorMap* Pmap, const CUtensorMap* Qmap, int x, int Mk, int stages,
+                                   const __nv_bfloat16* Pop, const __nv_bfloat16* Qop, int x, int Mk, int stages,
                                    unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump,
                                    const unsigned* tile_max = nullptr, float on_scale = 0.f, float on_tol = 0.f) {
   const int G = P.vgrid, cta = P.vrank;
@@ -308,6 +349,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunks = 2 * P.Kpad / kTcChunkElems;
   const int ksteps = (Mk + 15) / 16;
+  // a block's images of the K steps that hold modes: one contiguous bulk copy
+  const uint32_t load_bytes = 2u * ksteps * kTcImgBytes;
+  const size_t block_elems = static_cast<size_t>(P.Kpad / 16) * 2 * kTcImgElems;
   const int wl_n = td.mid < 0 ? td.ncols_pad : td.n_last_pad;
   const int wm_n = td.mid < 0 ? 0 : P.d[td.mid].n;
   const TcLayout Ly = tc_layout(chunks, stages, wl_n, wm_n);
@@ -373,18 +417,16 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       const int rb = t / td.ntc, cb = t - rb * td.ntc;
       if (rb != cur_rb) {
         if (a_loads > 0 && !mbar_wait(&sh->a_empty, (a_loads - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
-        mbar_expect_tx(&sh->a_full, stage_bytes);
-        for (int ch = 0; ch < chunks; ++ch)
-          tma_load_2d(As + ch * kTcChunkBytes, Pmap, &sh->a_full, ch * kTcChunkElems, rb * kTcM);
+        mbar_expect_tx(&sh->a_full, load_bytes);
+        bulk_load(As, Pop + static_cast<size_t>(rb) * block_elems, load_bytes, &sh->a_full);
         ++a_loads;
         cur_rb = rb;
       }
       const int s = it % stages, round = it / stages;
       if (it >= stages && !mbar_wait(&sh->b_empty[s], (round - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
-      mbar_expect_tx(&sh->b_full[s], stage_bytes);
-      for (int ch = 0; ch < chunks; ++ch)
-        tma_load_2d(Bs + static_cast<size_t>(s) * stage_bytes + ch * kTcChunkBytes, Qmap, &sh->b_full[s],
-                    ch * kTcChunkElems, cb * kTcN);
+      mbar_expect_tx(&sh->b_full[s], load_bytes);
+      bulk_load(Bs + static_cast<size_t>(s) * stage_bytes, Qop + static_cast<size_t>(cb) * block_elems, load_bytes,
+                &sh->b_full[s]);
       ++it;
     }
     if (!ok) sh->abort = 1;
@@ -392,7 +434,6 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     // ---------------- MMA issuer
     const uint32_t idesc = umma_idesc_bf16();
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-    const int lo_chunk = P.Kpad / kTcChunkElems;
     int cur_rb = -1, a_uses = 0, n_it = 0;
     for (int t = t0, it = 0; t < t1 && ok; ++t) {
       if (!active(t)) continue;
@@ -410,12 +451,11 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       const uint32_t d = tmem_base + static_cast<uint32_t>(ab * kTcN);
       const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes;
       for (int k = 0; k < ksteps; ++k) {
-        const uint32_t off = static_cast<uint32_t>((k & 3) * 32);
-        const uint32_t chh = static_cast<uint32_t>(k >> 2), chl = chh + lo_chunk;
-        const uint64_t ah = umma_desc_sw128(a_base + chh * kTcChunkBytes + off);
-        const uint64_t al = umma_desc_sw128(a_base + chl * kTcChunkBytes + off);
-        const uint64_t bh = umma_desc_sw128(bs + chh * kTcChunkBytes + off);
-        const uint64_t bl = umma_desc_sw128(bs + chl * kTcChunkBytes + off);
+        const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
+        const uint64_t ah = umma_desc_img(a_base + hi_off);
+        const uint64_t al = umma_desc_img(a_base + lo_off);
+        const uint64_t bh = umma_desc_img(bs + hi_off);
+        const uint64_t bl = umma_desc_img(bs + lo_off);
         tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
         tc_mma(d, ah, bl, idesc, 1u);
         tc_mma(d, al, bh, idesc, 1u);

@@ -252,7 +252,7 @@ __device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X
 }
 
 // ---------------------------------------------------------------------------------------
-__device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm, unsigned char* smem_raw,
+__device__ void step_body(const StepParams& P, const Extra& X, unsigned char* smem_raw,
                           uint32_t tmem_base) {
   SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
   const Arena ar = arena_of(smem_raw, P);
@@ -313,8 +313,8 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
           contract_fp64(P, x, ar.wv);
         } else {
           const TcDir& td = X.dirs[x];
-          const CUtensorMap* qmap = (D == 2) ? &tm.op[td.last] : &tm.kr[x];
-          if (!tc_contract(P, X.kc, td, &tm.op[x], qmap, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base,
+          const __nv_bfloat16* qop = (D == 2) ? P.d[td.last].op : X.kr[x];
+          if (!tc_contract(P, X.kc, td, P.d[x].op, qop, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base,
                            X.rpart32, nullptr, P.reduced_tol > 0.0 ? P.tile_max : nullptr,
                            static_cast<float>(4.0 * P.a0), static_cast<float>(P.reduced_tol)))
             return;
@@ -445,8 +445,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, const TmapSet& tm
 }
 
 __global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant__ StepParams P,
-                                                           const __grid_constant__ Extra X,
-                                                           const __grid_constant__ TmapSet tm) {
+                                                           const __grid_constant__ Extra X) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(16) StepParams sP;
@@ -458,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  step_body(sP, sX, tm, smem_raw, tc ? s_tmem : 0u);
+  step_body(sP, sX, smem_raw, tc ? s_tmem : 0u);
   __syncthreads();
   if (tc && (threadIdx.x >> 5) == 1) {
     tc_fence_after();
@@ -466,8 +465,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant
   }
 }
 
-// Batched time steps: one CTA advances one instance (its own parameters, workspace and
-// tensor maps, read from entries[order[blockIdx.x]]), with CTA-wide barriers in place of
+// Batched time steps: one CTA advances one instance (its own parameters and workspace,
+// read from entries[order[blockIdx.x]]), with CTA-wide barriers in place of
 // grid-wide ones.  kstep selects the instance's step record.  No CTA waits on another, so a
 // plain launch with more instances than SMs is fine.
 __global__ void __launch_bounds__(kThreads, 1) batch_step_kernel(const BatchEntry* entries, const int* order,
@@ -485,7 +484,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_step_kernel(const BatchEntr
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  step_body(sP, sX, E.tm, smem_raw, tc ? s_tmem : 0u);
+  step_body(sP, sX, smem_raw, tc ? s_tmem : 0u);
   __syncthreads();
   if (tc && (threadIdx.x >> 5) == 1) {
     tc_fence_after();
@@ -576,7 +575,7 @@ __global__ void energy_gram_kernel(const StepParams P, const Extra X, int Mk, do
 
 // ---------------------------------------------------------------------------------------
 // Probe kernels
-__device__ void probe_contract_body(const StepParams& P, const Extra& X, const TmapSet& tm, int x, float* dump,
+__device__ void probe_contract_body(const StepParams& P, const Extra& X, int x, float* dump,
                                     unsigned char* smem_raw, uint32_t tmem_base) {
   const Arena ar = arena_of(smem_raw, P);
   unsigned epoch = 0;
@@ -593,15 +592,15 @@ __device__ void probe_contract_body(const StepParams& P, const Extra& X, const T
     fence_proxy_async_global();
     if (!sync_all(P, epoch, 11)) return;
     const TcDir& td = X.dirs[x];
-    const CUtensorMap* qmap = (P.dim == 2) ? &tm.op[td.last] : &tm.kr[x];
-    tc_contract(P, X.kc, td, &tm.op[x], qmap, x, st0.Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart32,
+    const __nv_bfloat16* qop = (P.dim == 2) ? P.d[td.last].op : X.kr[x];
+    tc_contract(P, X.kc, td, P.d[x].op, qop, x, st0.Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart32,
                 dump);
   }
 }
 
 __global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const __grid_constant__ StepParams P,
                                                                      const __grid_constant__ Extra X,
-                                                                     const __grid_constant__ TmapSet tm, int x,
+                                                                     int x,
                                                                      float* dump) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_tmem;
@@ -614,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) probe_contract_kernel(const __gri
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  probe_contract_body(sP, sX, tm, x, dump, smem_raw, tc ? s_tmem : 0u);
+  probe_contract_body(sP, sX, x, dump, smem_raw, tc ? s_tmem : 0u);
   __syncthreads();
   if (tc && (threadIdx.x >> 5) == 1) {
     tc_fence_after();
@@ -675,11 +674,11 @@ static cudaError_t set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
 }
 
-cudaError_t launch_step(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, cudaStream_t s) {
+cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s) {
   const size_t smem = P.smem_bytes;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&step_kernel), smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), const_cast<TmapSet*>(&tm)};
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X)};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&step_kernel), dim3(grid), dim3(kThreads),
                                      args, smem, s);
 }
@@ -692,12 +691,12 @@ cudaError_t launch_batch_step(const BatchEntry* entries, const int* order, int c
   return cudaGetLastError();
 }
 
-cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, int x,
+cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x,
                                   float* dump, cudaStream_t s) {
   const size_t smem = P.smem_bytes;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&probe_contract_kernel), smem);
   if (e != cudaSuccess) return e;
-  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), const_cast<TmapSet*>(&tm), &x, &dump};
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X), &x, &dump};
   return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&probe_contract_kernel), dim3(grid),
                                      dim3(kThreads), args, smem, s);
 }

@@ -3,18 +3,17 @@
 #include "ctd_step.cuh"
 
 namespace ctd {
-// One instance of a batched launch (global memory; the tensor maps need 64-byte alignment).
+// One instance of a batched launch (global memory).
 struct __align__(128) BatchEntry {
-  TmapSet tm;
   StepParams P;
   Extra X;
 };
 size_t step_smem_fixed_bytes();
 size_t step_arena_bytes(int n_max, size_t solver_floats, int mode);
-cudaError_t launch_step(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, cudaStream_t s);
+cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s);
 cudaError_t launch_batch_step(const BatchEntry* entries, const int* order, int count, int kstep, size_t smem,
                               cudaStream_t s);
-cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, const TmapSet& tm, int grid, int x,
+cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x,
                                   float* dump, cudaStream_t s);
 cudaError_t launch_probe_solve(const StepParams& P, const Extra& X, int x, double a1, double a2,
                                cudaStream_t s);

@@ -29,7 +29,10 @@ def pad128(n):
     return (n + 127) // 128 * 128
 
 
-@pytest.mark.parametrize("n,rank", [((128, 128), 4), ((200, 77), 5), ((256, 384), 20), ((64, 64), 50)])
+# ranks cover every K box width of the tiles: 16 (rank <= 16), 32 (17..32), 64 (33..64) and
+# two 64-wide boxes per half (65..128)
+@pytest.mark.parametrize("n,rank", [((128, 128), 4), ((200, 77), 5), ((256, 384), 20), ((130, 90), 33),
+                                    ((64, 64), 50), ((200, 150), 70)])
 def test_tensor_core_reconstruction_2d(lib, n, rank):
     w = workloads.preset("c0", n=n, M_max=max(rank, 8))
     cfg = lib.config_from_workload(w, precision=lib.PREC_SPLIT_BF16)
@@ -48,12 +51,13 @@ def test_tensor_core_reconstruction_2d(lib, n, rank):
     s.close()
 
 
-@pytest.mark.parametrize("dim,n", [(2, (64, 64)), (2, (300, 130)), (3, (20, 33, 17))])
-def test_tensor_core_contraction(lib, dim, n):
-    w = workloads.preset("c0", dim=dim, n=n, length=(1.0,) * dim)
+@pytest.mark.parametrize("dim,n,rank", [(2, (64, 64), 5), (2, (300, 130), 5), (2, (300, 130), 24),
+                                        (2, (160, 140), 40), (3, (20, 33, 17), 5), (3, (20, 33, 17), 20)])
+def test_tensor_core_contraction(lib, dim, n, rank):
+    w = workloads.preset("c0", dim=dim, n=n, length=(1.0,) * dim, M_max=max(rank, 20))
     cfg = lib.config_from_workload(w, precision=lib.PREC_SPLIT_BF16)
     s = lib.Solver(cfg)
-    A = workloads.cosine_modes(n, (1.0,) * dim, 5, 4, 3, amp=0.7)
+    A = workloads.cosine_modes(n, (1.0,) * dim, rank, 4, 3, amp=0.7)
     s.set_initial_modes(A)
     prob = octd.Problem(dim=dim, n=n, length=(1.0,) * dim, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
                         alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
