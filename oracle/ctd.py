@@ -14,6 +14,8 @@ What is computed (paper passages):
     ``Q_x`` from Eq. KxQx / Eq. KyQy), sweeping x -> y (-> z) until the mode stops
     changing; stop adding modes once a mode's size is negligible.
   * Eq. KxxMxx: ``M_xy = int N~_x^T N~_y L w(u^k) dx dy``, the nonlinear term.
+  * Eq. MxySep (Section 3.3): the same term from a separated form ``w = sum_q prod_d w_d^(q)``
+    of the nonlinearity, integrated as products of 1D integrals.
 
 Readings of silent or ambiguous points (each also listed in the design notes):
   * Quadrature (the paper only mentions "Gauss points" for the reduced domain): all
@@ -33,6 +35,12 @@ Readings of silent or ambiguous points (each also listed in the design notes):
     ``M_max`` committed modes ends the step with the "capped" flag.
   * If a solve returns an all-zero factor the mode is zero: its sweep stops at once and the
     enrichment test discards it.
+  * Separated nonlinearity (the paper names SVD or HOPGD for the decomposition of w(u^k)):
+    for the cubic w and a separated u^k the decomposition is exact and needs neither --
+    ``u^3`` expands into one separated term per multiset {m1, m2, m3} of mode indices
+    (weight = its number of orderings) and ``-u`` into one per mode, so
+    Q = C(M_k + 2, 3) + M_k terms reproduce w(u^k) on the grid up to rounding.  It is used
+    for steps with M_k <= ``separated_max_modes`` and the full integral otherwise.
 """
 from __future__ import annotations
 
@@ -70,6 +78,8 @@ class Problem:
     fixed_modes: int = 0       # >0: exactly this many modes per step (strict-parity mode)
     reduced_tol: float = 0.0   # >0: reduced integration domain (Section 3.3), see below
     reduced_block: int = 128   # nodes per dimension of the element blocks it keeps or drops
+    nonlinear_form: str = "grid"   # "grid" (Eq. KxxMxx) or "separated" (Eq. MxySep)
+    separated_max_modes: int = 16  # separated form only for steps with M_k up to this
 
     @property
     def c_t(self) -> float:
@@ -149,6 +159,56 @@ def nonlinear_tensor(prob: Problem, ops: Operators, A: Sequence[np.ndarray]) -> 
     return prob.L * grid_weights(ops) * W * reduced_domain_mask(prob, W)
 
 
+def separated_nonlinear_terms(prob: Problem, A: Sequence[np.ndarray]):
+    """Exact separated form of ``w(u^k) = 4 a0 (u^3 - u)`` for ``u^k = sum_m prod_d A[d][:, m]``
+    (Eq. energyfunction for w; used by Eq. MxySep): a list of ``(c_q, [f_q,d for d])`` with
+    ``w = sum_q c_q prod_d f_q,d``.  The cubic gives one term per multiset m1 <= m2 <= m3
+    (``f = A[:, m1] A[:, m2] A[:, m3]``, ``c = 4 a0`` times the multiset's orderings); the
+    linear part gives ``c = -4 a0``, ``f = A[:, m]``."""
+    D = prob.dim
+    Mk = A[0].shape[1]
+    terms = []
+    for m1 in range(Mk):
+        for m2 in range(m1, Mk):
+            for m3 in range(m2, Mk):
+                orderings = 6 if (m1 != m2 and m2 != m3) else (1 if m1 == m3 else 3)
+                f = [A[d][:, m1] * A[d][:, m2] * A[d][:, m3] for d in range(D)]
+                terms.append((4.0 * prob.a0 * orderings, f))
+    for m in range(Mk):
+        terms.append((-4.0 * prob.a0, [A[d][:, m].copy() for d in range(D)]))
+    return terms
+
+
+def separated_contraction(prob: Problem, ops: Operators, terms, v: Sequence[np.ndarray], x: int) -> np.ndarray:
+    """``M_xy`` of Eq. MxySep applied to the fixed factors: ``sum_q L c_q (omega_x f_q,x)
+    prod_{d != x} (f_q,d . omega_d v_d)`` (nodal rule for every 1D integral)."""
+    out = np.zeros(prob.n[x])
+    for c, f in terms:
+        s = prob.L * c
+        for d in range(prob.dim):
+            if d != x:
+                s = s * float(f[d] @ (ops.omega[d] * v[d]))
+        out = out + s * (ops.omega[x] * f[x])
+    return out
+
+
+def nonlinear_projection(prob: Problem, ops: Operators, nl, v: Sequence[np.ndarray], x: int) -> np.ndarray:
+    """``M_xy u_y`` (and its D-way analogue): ``nl`` is ``("grid", Mxy)`` or
+    ``("separated", terms)``."""
+    kind, data = nl
+    if kind == "grid":
+        return contract_except(data, v, x)
+    return separated_contraction(prob, ops, data, v, x)
+
+
+def nonlinear_operator(prob: Problem, ops: Operators, A: Sequence[np.ndarray]):
+    """The nonlinear term of a step in the form the problem asks for (see the readings)."""
+    Mk = A[0].shape[1]
+    if prob.nonlinear_form == "separated" and 0 < Mk <= prob.separated_max_modes:
+        return ("separated", separated_nonlinear_terms(prob, A))
+    return ("grid", nonlinear_tensor(prob, ops, A))
+
+
 def contract_except(T: np.ndarray, vecs: Sequence[np.ndarray], keep: int) -> np.ndarray:
     """Contract the D-way array ``T`` with ``vecs[d]`` on every axis except ``keep``."""
     out = T
@@ -209,7 +269,7 @@ def rel_change(new: Sequence[np.ndarray], old: Sequence[np.ndarray]) -> float:
 
 
 def half_sweep(prob: Problem, ops: Operators, x: int, v: List[np.ndarray],
-               A: Sequence[np.ndarray], B: Sequence[np.ndarray], Mxy: np.ndarray):
+               A: Sequence[np.ndarray], B: Sequence[np.ndarray], Mxy):
     """Fix every factor but ``v[x]`` and solve Eq. ux for it (Eq. KxQx, generalised to D).
 
     Returns the new ``v[x]`` (not normalised) and ``(alpha1, alpha2)``.
@@ -252,7 +312,9 @@ def half_sweep(prob: Problem, ops: Operators, x: int, v: List[np.ndarray],
     # right-hand side, in the term order of Eq. KxQx
     Q = c_t * (Mx @ (A[x] @ H))                 # + sum_m c_t M_xx u_x^(m,k) (...)
     Q = Q - c_t * (Mx @ (B[x] @ GM))            # - sum_m c_t M_xx u_x^(m) (...)
-    Q = Q - contract_except(Mxy, v, x)          # - M_xy u_y
+    if not isinstance(Mxy, tuple):
+        Mxy = ("grid", Mxy)
+    Q = Q - nonlinear_projection(prob, ops, Mxy, v, x)   # - M_xy u_y
     Q = Q - c_k * (Kx @ (B[x] @ GM))            # - sum_m L kappa K_xx u_x^(m) (...)
     Q = Q - c_k * (Mx @ (B[x] @ GK))            # - sum_m L kappa M_xx u_x^(m) (u^T K u^(m))
 
@@ -280,7 +342,7 @@ def step(prob: Problem, ops: Operators, A: Sequence[np.ndarray], step_index: int
     """
     D = prob.dim
     A = [np.asarray(a, dtype=np.float64) for a in A]
-    Mxy = nonlinear_tensor(prob, ops, A)
+    Mxy = nonlinear_operator(prob, ops, A)
     B = [np.zeros((prob.n[d], 0)) for d in range(D)]
     stats = {"modes": 0, "als_iters": [], "als_delta": [], "amplitude": [],
              "capped": False, "als_not_converged": False}

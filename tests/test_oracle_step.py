@@ -263,3 +263,68 @@ def test_reduced_domain_error_bound_and_limits():
     # a tolerance above every |w| removes the whole nonlinear term
     prob.reduced_tol = 10.0 * float(np.max(np.abs(W)))
     assert not np.any(ctd.nonlinear_tensor(prob, ops, A))
+
+
+# ---- separated nonlinearity (Eq. MxySep)
+
+def _separated_case(dim, rank, seed=3):
+    n = (11, 9) if dim == 2 else (7, 6, 5)
+    prob = ctd.Problem(dim=dim, n=n, length=(1.0,) * dim, s=1, p=1, a=12.0, L=1.3, kappa=1e-3, a0=0.25,
+                       alpha=2.0, dt=0.01, M_max=20, I_max=50, tol_als=1e-8, tol_enrich=1e-4, seed=0)
+    ops = ctd.build_operators(prob)
+    rng = np.random.default_rng(seed)
+    A = [rng.uniform(-1.0, 1.0, size=(n[d], rank)) for d in range(dim)]
+    return prob, ops, A
+
+
+@pytest.mark.parametrize("dim,rank", [(2, 1), (2, 4), (3, 3)])
+def test_separated_terms_reproduce_w_on_the_grid(dim, rank):
+    # sum_q c_q prod_d f_q,d evaluated node by node against w(u) of the reconstructed field
+    prob, ops, A = _separated_case(dim, rank)
+    terms = ctd.separated_nonlinear_terms(prob, A)
+    assert len(terms) == math.comb(rank + 2, 3) + rank
+    W = ctd.w_of_u(ctd.reconstruct(A), prob.a0)
+    S = np.zeros_like(W)
+    for idx in np.ndindex(*W.shape):
+        S[idx] = sum(c * np.prod([f[d][idx[d]] for d in range(dim)]) for c, f in terms)
+    assert np.max(np.abs(S - W)) <= 1e-13 * max(1.0, np.max(np.abs(W)))
+
+
+@pytest.mark.parametrize("dim,rank", [(2, 4), (3, 3)])
+def test_separated_contraction_equals_full_integral(dim, rank):
+    # Eq. MxySep against Eq. KxxMxx (the full nodal integral over the grid)
+    prob, ops, A = _separated_case(dim, rank)
+    terms = ctd.separated_nonlinear_terms(prob, A)
+    Mxy = ctd.nonlinear_tensor(prob, ops, A)
+    v = [np.random.default_rng(9).uniform(-1.0, 1.0, size=prob.n[d]) for d in range(dim)]
+    for x in range(dim):
+        ref = ctd.contract_except(Mxy, v, x)
+        got = ctd.separated_contraction(prob, ops, terms, v, x)
+        assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref), x
+
+
+def test_separated_step_equals_grid_step():
+    # same step with either form of the nonlinear term: same decisions, same field
+    w = workloads.preset("c0", n=(20, 17), M_max=8)
+    kw = dict(dim=2, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
+              alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+              tol_enrich=w.tol_enrich, seed=w.seed)
+    pg = ctd.Problem(**kw)
+    ps = ctd.Problem(**kw, nonlinear_form="separated")
+    ops = ctd.build_operators(pg)
+    Ag = As = workloads.initial_modes(w)
+    for k in range(3):
+        Ag, sg = ctd.step(pg, ops, Ag, k)
+        As, ss = ctd.step(ps, ops, As, k)
+        assert sg["modes"] == ss["modes"] and sg["als_iters"] == ss["als_iters"], (k, sg, ss)
+        assert ctd.rel_l2_between(As, Ag) < 1e-12, k
+
+
+def test_separated_form_falls_back_above_the_mode_limit():
+    prob, ops, A = _separated_case(2, 4)
+    prob.nonlinear_form = "separated"
+    prob.separated_max_modes = 3
+    assert ctd.nonlinear_operator(prob, ops, A)[0] == "grid"
+    prob.separated_max_modes = 4
+    assert ctd.nonlinear_operator(prob, ops, A)[0] == "separated"
+    assert ctd.nonlinear_operator(prob, ops, [a[:, :0] for a in A])[0] == "grid"   # u^k = 0
