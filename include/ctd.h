@@ -77,7 +77,17 @@ typedef struct {
                                (Section 3.3): a 128 x 128 node block drops out of M_xy for
                                the step when max |w(u^k)| over its nodes <= reduced_tol;
                                0: the whole domain.  2D only (CTD_ERR_UNSUPPORTED in 3D)   */
+  int nonlinear_form;       /* CTD_NONLINEAR_GRID: M_xy as the full nodal integral over the
+                               grid (Eq. KxxMxx), tile by tile.  CTD_NONLINEAR_SEPARATED: the
+                               separated form of Eq. MxySep, with the exact decomposition of
+                               w(u^k) = 4 a0 (u^3 - u) into C(M_k + 2, 3) + M_k separated
+                               terms (one per multiset of mode indices, one per mode): every
+                               integral becomes a 1D sum, no grid pass.  Requires
+                               M_max <= 16 and reduced_tol == 0 (CTD_ERR_ARG otherwise);
+                               ctd_step_batch refuses it (CTD_ERR_UNSUPPORTED).            */
 } ctd_config;
+
+enum { CTD_NONLINEAR_GRID = 0, CTD_NONLINEAR_SEPARATED = 1 };
 
 typedef struct {
   int modes;                /* M of u^{k+1}                                                  */

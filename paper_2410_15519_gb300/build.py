@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctd.so")
 
-SOURCES = ["cfem_host.cpp", "ctd_kernels.cu", "ctd_api.cu"]
+SOURCES = ["cfem_host.cpp", "ctd_kernels.cu", "ctd_kernels_sep.cu", "ctd_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -42,7 +42,7 @@ struct Carver {
 };
 
 struct Plan {
-  int D, n[3], b[3], n_pad[3], Mcap, Kpad, grid, rchunks[3];
+  int D, n[3], b[3], n_pad[3], Mcap, Kpad, sep_q, grid, rchunks[3];
   long long N;
   size_t rpart_len, rpart32_len;
   ctd::TcDir dirs[3];
@@ -106,6 +106,7 @@ Plan make_plan(const ctd_config& c, int grid) {
   }
   p.Mcap = c.M_max;
   p.Kpad = (c.M_max + 63) / 64 * 64;
+  p.sep_q = c.nonlinear_form == CTD_NONLINEAR_SEPARATED ? ctd::sep_terms(c.M_max) : 0;
   p.grid = grid;
   p.rpart_len = 0;
   p.rpart32_len = 0;
@@ -149,7 +150,7 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   }
   int nmax = 0;
   for (int d = 0; d < D; ++d) nmax = std::max(nmax, pl.n[d]);
-  const int spd = ctd::slots_per_dim(pl.Mcap);
+  const int spd = ctd::slots_per_dim(pl.Mcap, pl.sep_q);
   const int nslots = std::max((D - 1) * spd, D * 6);
   p.gram = cv.take<float2>(static_cast<size_t>(nslots) * Gs);
   p.rpart = cv.take<double>(pl.rpart_len);
@@ -215,6 +216,9 @@ ctd_status validate(const ctd_config* c) {
   if (c->grid_ctas > kGridMax) return CTD_ERR_ARG;
   if (!(c->reduced_tol >= 0.0) || !std::isfinite(c->reduced_tol)) return CTD_ERR_ARG;
   if (c->reduced_tol > 0.0 && c->dim != 2) return CTD_ERR_UNSUPPORTED;
+  if (c->nonlinear_form != CTD_NONLINEAR_GRID && c->nonlinear_form != CTD_NONLINEAR_SEPARATED) return CTD_ERR_ARG;
+  if (c->nonlinear_form == CTD_NONLINEAR_SEPARATED && (c->reduced_tol > 0.0 || c->M_max > ctd::kMaxSepModes))
+    return CTD_ERR_ARG;
   return CTD_OK;
 }
 
@@ -370,6 +374,8 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   P.tol_als = cfg->tol_als;
   P.tol_enrich = cfg->tol_enrich;
   P.reduced_tol = cfg->reduced_tol;
+  P.nl_form = cfg->nonlinear_form;
+  P.sep_q = h->plan.sep_q;
   P.I_max = cfg->I_max;
   P.M_max = cfg->M_max;
   P.fixed_als = cfg->fixed_als_iters;
@@ -558,7 +564,8 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
     for (int k = 0; k < batch; ++k) {
       h->P.stats = h->stats_dev + k;
       CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
-      CTD_CUDA(h, ctd::launch_step(h->P, h->X, h->grid, h->stream));
+      CTD_CUDA(h, h->P.nl_form == CTD_NONLINEAR_SEPARATED ? ctd::launch_step_sep(h->P, h->X, h->grid, h->stream)
+                                                         : ctd::launch_step(h->P, h->X, h->grid, h->stream));
     }
     if (stats) {
       rec.resize(batch);
@@ -611,6 +618,8 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
     if (!h) return CTD_ERR_ARG;
     if (!h->has_modes) return fail(h, CTD_ERR_STATE, "ctd_set_initial_modes has not been called");
     if (h->device != dev) return fail(h, CTD_ERR_STATE, "instance on another device");
+    if (h->P.nl_form != CTD_NONLINEAR_GRID)
+      return fail(h, CTD_ERR_UNSUPPORTED, "batched steps integrate the nonlinear term over the grid only");
   }
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   // one entry per instance; the largest instances start first

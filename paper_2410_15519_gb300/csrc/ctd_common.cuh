@@ -12,6 +12,11 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxDim = 3;
 constexpr int kMaxN = 4096;            // nodes per dimension
 constexpr int kMaxModes = 128;         // M_max limit
+// Separated nonlinearity: u^3 of a rank-M_k field has one separated term per multiset
+// {m1 <= m2 <= m3} of mode indices; used for M_k up to kMaxSepModes (kMaxSep multisets)
+constexpr int kMaxSepModes = 16;
+constexpr int kMaxSep = kMaxSepModes * (kMaxSepModes + 1) * (kMaxSepModes + 2) / 6;
+__host__ __device__ constexpr int sep_terms(int Mk) { return Mk * (Mk + 1) * (Mk + 2) / 6; }
 constexpr int kTileRows = 128;         // tensor-core tile rows (operand rows padded to this)
 
 // status bits written by the kernels (host maps them to ctd_status)
@@ -81,6 +86,9 @@ struct StepParams {
   int n_max;               // largest n over the dimensions
   double reduced_tol;      // > 0: reduced integration domain of the nonlinear term (2D)
   unsigned* tile_max;      // [nrb_0 * ntc_0] max |u(u^2-1)| per 128 x 128 node block (float bits)
+  int nl_form;             // 0: nonlinear term as the full nodal integral (Eq. KxxMxx); 1: the
+                           // separated form (Eq. MxySep) for steps with M_k <= kMaxSepModes
+  int sep_q;               // Gram slots per dimension reserved for the separated form (0 if off)
   int vgrid, vrank;        // CTAs working on this instance and this CTA's rank among them: the
                            // launch grid for a single instance, 1 and 0 in a batched launch
                            // (set by each CTA in its shared-memory copy)

@@ -66,7 +66,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait on an mbarrier phase; false (and kErrTimeout recorded) on expiry.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns,
-                                          InstState* st, const volatile int* abort_flag) {
+                                          InstState* st, const volatile int* abort_flag, int where) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
@@ -74,9 +74,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
     if (*abort_flag) return false;
     if (global_ns() - t0 > limit_ns) {
       atomicOr(&st->status, kErrTimeout);
+      atomicExch(&st->err_info, where);
       return false;
     }
   }
+}
+// The same wait by every lane of a warp; the warp leaves it converged and agreeing on the result
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns, InstState* st,
+                                          const volatile int* abort_flag, int where) {
+  const bool r = mbar_wait(bar, parity, limit_ns, st, abort_flag, where);
+  return __all_sync(0xffffffffu, r);
 }
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -388,6 +395,10 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, wl_n);
     }
   }
+  // The arena held generic-proxy data of earlier phases (Gram staging, solver vectors) where
+  // the bulk copies and the MMAs now write and read through the async proxy: every thread
+  // orders its earlier shared-memory accesses before them.
+  fence_proxy_async();
   __syncthreads();
   if (Mk == 0 || ksteps == 0) {
     // u^k = 0: w(0) = 0, every partial is zero
@@ -408,29 +419,37 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   volatile int* abort_flag = &sh->abort;
   bool ok = true;
 
-  if (warp == 0 && lane == 0) {
+  // The producer and MMA warps walk their loops with all lanes (waits by the whole warp, so
+  // that it stays converged); lane 0 issues the copies, the MMAs and the commits.
+  if (warp == 0) {
     // ---------------- TMA producer
-    fence_proxy_async_global();     // operands were written through the generic proxy
+    if (lane == 0) fence_proxy_async_global();     // operands were written through the generic proxy
     int cur_rb = -1, a_loads = 0;
     for (int t = t0, it = 0; t < t1 && ok; ++t) {
       if (!active(t)) continue;
       const int rb = t / td.ntc, cb = t - rb * td.ntc;
       if (rb != cur_rb) {
-        if (a_loads > 0 && !mbar_wait(&sh->a_empty, (a_loads - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
-        mbar_expect_tx(&sh->a_full, load_bytes);
-        bulk_load(As, Pop + static_cast<size_t>(rb) * block_elems, load_bytes, &sh->a_full);
+        if (a_loads > 0 && !warp_wait(&sh->a_empty, (a_loads - 1) & 1, lim, P.st, abort_flag, 21)) { ok = false; break; }
+        if (lane == 0) {
+          mbar_expect_tx(&sh->a_full, load_bytes);
+          bulk_load(As, Pop + static_cast<size_t>(rb) * block_elems, load_bytes, &sh->a_full);
+        }
+        __syncwarp();
         ++a_loads;
         cur_rb = rb;
       }
       const int s = it % stages, round = it / stages;
-      if (it >= stages && !mbar_wait(&sh->b_empty[s], (round - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
-      mbar_expect_tx(&sh->b_full[s], load_bytes);
-      bulk_load(Bs + static_cast<size_t>(s) * stage_bytes, Qop + static_cast<size_t>(cb) * block_elems, load_bytes,
-                &sh->b_full[s]);
+      if (it >= stages && !warp_wait(&sh->b_empty[s], (round - 1) & 1, lim, P.st, abort_flag, 22)) { ok = false; break; }
+      if (lane == 0) {
+        mbar_expect_tx(&sh->b_full[s], load_bytes);
+        bulk_load(Bs + static_cast<size_t>(s) * stage_bytes, Qop + static_cast<size_t>(cb) * block_elems, load_bytes,
+                  &sh->b_full[s]);
+      }
+      __syncwarp();
       ++it;
     }
-    if (!ok) sh->abort = 1;
-  } else if (warp == 1 && lane == 0) {
+    if (!ok && lane == 0) sh->abort = 1;
+  } else if (warp == 1) {
     // ---------------- MMA issuer
     const uint32_t idesc = umma_idesc_bf16();
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
@@ -439,45 +458,48 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       if (!active(t)) continue;
       const int rb = t / td.ntc;
       if (rb != cur_rb) {
-        if (!mbar_wait(&sh->a_full, a_uses & 1, lim, P.st, abort_flag)) { ok = false; break; }
+        if (!warp_wait(&sh->a_full, a_uses & 1, lim, P.st, abort_flag, 23)) { ok = false; break; }
         ++a_uses;
         cur_rb = rb;
       }
       const int s = it % stages;
-      if (!mbar_wait(&sh->b_full[s], (it / stages) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      if (!warp_wait(&sh->b_full[s], (it / stages) & 1, lim, P.st, abort_flag, 24)) { ok = false; break; }
       const int ab = it & 1;
-      if (it >= 2 && !mbar_wait(&sh->acc_empty[ab], ((it >> 1) - 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      if (it >= 2 && !warp_wait(&sh->acc_empty[ab], ((it >> 1) - 1) & 1, lim, P.st, abort_flag, 25)) { ok = false; break; }
       tc_fence_after();
       const uint32_t d = tmem_base + static_cast<uint32_t>(ab * kTcN);
       const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes;
-      for (int k = 0; k < ksteps; ++k) {
-        const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
-        const uint64_t ah = umma_desc_img(a_base + hi_off);
-        const uint64_t al = umma_desc_img(a_base + lo_off);
-        const uint64_t bh = umma_desc_img(bs + hi_off);
-        const uint64_t bl = umma_desc_img(bs + lo_off);
-        tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
-        tc_mma(d, ah, bl, idesc, 1u);
-        tc_mma(d, al, bh, idesc, 1u);
-      }
-      tc_commit(&sh->b_empty[s]);
-      tc_commit(&sh->acc_full[ab]);
       int tn = t + 1;   // next tile that is contracted
       while (tn < t1 && !active(tn)) ++tn;
-      if (tn == t1 || tn / td.ntc != rb) tc_commit(&sh->a_empty);
+      if (lane == 0) {
+        for (int k = 0; k < ksteps; ++k) {
+          const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
+          const uint64_t ah = umma_desc_img(a_base + hi_off);
+          const uint64_t al = umma_desc_img(a_base + lo_off);
+          const uint64_t bh = umma_desc_img(bs + hi_off);
+          const uint64_t bl = umma_desc_img(bs + lo_off);
+          tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
+          tc_mma(d, ah, bl, idesc, 1u);
+          tc_mma(d, al, bh, idesc, 1u);
+        }
+        tc_commit(&sh->b_empty[s]);
+        tc_commit(&sh->acc_full[ab]);
+        if (tn == t1 || tn / td.ntc != rb) tc_commit(&sh->a_empty);
+      }
+      __syncwarp();
       ++it;
       n_it = it;
     }
     if (!ok) {
-      sh->abort = 1;
+      if (lane == 0) sh->abort = 1;
     } else if (n_it > 0) {
       // quiesce: the last commits have landed before the barriers are re-initialised
       for (int s = 0; s < stages && s < n_it; ++s) {
         const int last_it = s + ((n_it - 1 - s) / stages) * stages;
-        if (!mbar_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+        if (!warp_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, P.st, abort_flag, 26)) { ok = false; break; }
       }
-      if (ok && !mbar_wait(&sh->a_empty, (a_uses - 1) & 1, lim, P.st, abort_flag)) ok = false;
-      if (!ok) sh->abort = 1;
+      if (ok && !warp_wait(&sh->a_empty, (a_uses - 1) & 1, lim, P.st, abort_flag, 27)) ok = false;
+      if (!ok && lane == 0) sh->abort = 1;
     }
   } else if (warp >= 4) {
     // ---------------- epilogue: one TMEM lane (tile row) per thread
@@ -502,7 +524,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       if (!active(t)) continue;
       const int itc = it++;
       const int ab = itc & 1;
-      if (!mbar_wait(&sh->acc_full[ab], (itc >> 1) & 1, lim, P.st, abort_flag)) { ok = false; break; }
+      // each lane leaves its wait on its own; the TMEM loads below are warp-collective
+      // (.sync.aligned), so the warp reconverges (and agrees on the outcome) first
+      if (!warp_wait(&sh->acc_full[ab], (itc >> 1) & 1, lim, P.st, abort_flag, 28)) { ok = false; break; }
       tc_fence_after();
       const int col0 = cb * kTcN;
       const float* wt;

@@ -6,6 +6,13 @@
 #include "ctd_kernels.h"
 #include "ctd_step.cuh"
 
+// Functions the separated-form translation unit compiles again get internal linkage there
+#ifdef CTD_SEPARATED_TU
+#define CTD_LOCAL static
+#else
+#define CTD_LOCAL
+#endif
+
 namespace ctd {
 
 // ---------------------------------------------------------------------------------------
@@ -92,7 +99,7 @@ __device__ inline bool sync_all(const StepParams& P, unsigned& epoch, int where)
 }
 
 // Convert u^k factors of this CTA's slices to FP64 copies (FP64-path materialisation).
-__device__ __noinline__ void convert_prev_modes(const StepParams& P, const Extra& X, int pb, int Mk) {
+CTD_LOCAL __device__ __noinline__ void convert_prev_modes(const StepParams& P, const Extra& X, int pb, int Mk) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
@@ -105,7 +112,7 @@ __device__ __noinline__ void convert_prev_modes(const StepParams& P, const Extra
 
 // Mode start vectors (own slices): warm start from u^k's mode m if present and not zero,
 // otherwise SplitMix64 entries in [0.5, 1.5).
-__device__ __noinline__ void init_mode(const StepParams& P, int m, int pb, int Mk, long long step) {
+CTD_LOCAL __device__ __noinline__ void init_mode(const StepParams& P, int m, int pb, int Mk, long long step) {
   __shared__ int s_nz[kMaxDim];
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
@@ -138,7 +145,7 @@ __device__ __noinline__ void init_mode(const StepParams& P, int m, int pb, int M
 
 // Convergence partials (own slices): per dimension c the six products of old, delta = new -
 // old and new, and max |new|; slot (c * 6 + k) of the gram buffer, maxpart[c * G + cta].
-__device__ __noinline__ void convergence_partials(const StepParams& P, const Extra& X, float2* sh) {
+CTD_LOCAL __device__ __noinline__ void convergence_partials(const StepParams& P, const Extra& X, float2* sh) {
   const int G = gram_ctas(P), cta = P.vrank;
   if (cta >= G) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,7 +191,7 @@ __device__ __noinline__ void convergence_partials(const StepParams& P, const Ext
 }
 
 // Save the current trial factors (own slices) at the start of a sweep.
-__device__ __noinline__ void save_old(const StepParams& P) {
+CTD_LOCAL __device__ __noinline__ void save_old(const StepParams& P) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
     int lo, hi;
@@ -194,7 +201,7 @@ __device__ __noinline__ void save_old(const StepParams& P) {
 }
 
 // Commit the converged mode (own slices): b = v * scale_d, K b.
-__device__ __noinline__ void commit_mode(const StepParams& P, const Extra& X, int M, int cb,
+CTD_LOCAL __device__ __noinline__ void commit_mode(const StepParams& P, const Extra& X, int M, int cb,
                             const double* scale) {
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
@@ -210,7 +217,7 @@ __device__ __noinline__ void commit_mode(const StepParams& P, const Extra& X, in
 
 // The solver CTA: solve Eq. ux for direction x, normalise unless x is the last dimension,
 // publish v_x (double-float) and flags in ctrl: [0] zero factor, [1] failure.
-__device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
+CTD_LOCAL __device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
                                 const Arena& ar, bool warm) {
   const Dim& dd = P.d[x];
   const SolverStore store = solver_bind(P.solver_mode == 2 ? 0 : P.solver_mode, ar.solver, P.solver, dd.n, dd.b, dd.mu_max);
@@ -252,7 +259,7 @@ __device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X
 }
 
 // ---------------------------------------------------------------------------------------
-__device__ void step_body(const StepParams& P, const Extra& X, unsigned char* smem_raw,
+CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigned char* smem_raw,
                           uint32_t tmem_base) {
   SmemStep& sm = *reinterpret_cast<SmemStep*>(smem_raw);
   const Arena ar = arena_of(smem_raw, P);
@@ -262,8 +269,10 @@ __device__ void step_body(const StepParams& P, const Extra& X, unsigned char* sm
   if (st0.status != 0) return;
   const int D = P.dim, pb = st0.bank, cb = 1 - pb, Mk = st0.Mk;
 
-  // ---- prologue: the nonlinear term's data for this step
-  if (P.precision == 0) {
+  // ---- prologue: the nonlinear term's data for this step (none for the separated form,
+  // whose 1D sums are Gram slots)
+  if constexpr (kSepTU) {
+  } else if (P.precision == 0) {
     convert_prev_modes(P, X, pb, Mk);
     if (!sync_all(P, epoch, 1)) return;
     materialise_w(P, X, Mk);
@@ -271,7 +280,7 @@ __device__ void step_body(const StepParams& P, const Extra& X, unsigned char* sm
     tc_prepare(P, X.dirs, X.kr, pb, Mk);
     fence_proxy_async_global();
   }
-  if (P.reduced_tol > 0.0 && Mk > 0) {
+  if (!kSepTU && P.reduced_tol > 0.0 && Mk > 0) {
     // reduced integration domain (Section 3.3): the nonlinear term is fixed for the step, so
     // its 128 x 128 node blocks are classified once
     if (P.precision == 0) {
@@ -308,7 +317,8 @@ __device__ void step_body(const StepParams& P, const Extra& X, unsigned char* sm
           atomicAdd(P.trace + kTrGram, t - tsub);
           tsub = t;
         }
-        if (P.precision == 0) {
+        if constexpr (kSepTU) {
+        } else if (P.precision == 0) {
           load_weights_fp64(P, X, x, ar.wv);
           contract_fp64(P, x, ar.wv);
         } else {
@@ -444,6 +454,32 @@ __device__ void step_body(const StepParams& P, const Extra& X, unsigned char* sm
   }
 }
 
+static cudaError_t set_smem(const void* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+}
+
+#ifdef CTD_SEPARATED_TU
+// Time step with the separated nonlinear term (Eq. MxySep): no tensor-core or grid pass.
+__global__ void __launch_bounds__(kThreads, 1) step_kernel_sep(const __grid_constant__ StepParams P,
+                                                               const __grid_constant__ Extra X) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) StepParams sP;
+  __shared__ __align__(16) Extra sX;
+  stage_params(&sP, P, gridDim.x, blockIdx.x);
+  stage_to_smem(&sX, X);
+  __syncthreads();
+  step_body(sP, sX, smem_raw, 0u);
+}
+
+cudaError_t launch_step_sep(const StepParams& P, const Extra& X, int grid, cudaStream_t s) {
+  const size_t smem = P.smem_bytes;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&step_kernel_sep), smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {const_cast<StepParams*>(&P), const_cast<Extra*>(&X)};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&step_kernel_sep), dim3(grid), dim3(kThreads),
+                                     args, smem, s);
+}
+#else
 __global__ void __launch_bounds__(kThreads, 1) step_kernel(const __grid_constant__ StepParams P,
                                                            const __grid_constant__ Extra X) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -670,9 +706,6 @@ __global__ void df_to_f64_kernel(double* dst, const float2* src, long long count
     dst[t] = f2_to_double(src[t]);
 }
 
-static cudaError_t set_smem(const void* fn, size_t bytes) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-}
 
 cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s) {
   const size_t smem = P.smem_bytes;
@@ -739,4 +772,5 @@ cudaError_t launch_modes_to_fp64(double* dst, const float2* src, long long count
   return cudaGetLastError();
 }
 
+#endif  // CTD_SEPARATED_TU
 }  // namespace ctd

@@ -11,6 +11,7 @@ struct __align__(128) BatchEntry {
 size_t step_smem_fixed_bytes();
 size_t step_arena_bytes(int n_max, size_t solver_floats, int mode);
 cudaError_t launch_step(const StepParams& P, const Extra& X, int grid, cudaStream_t s);
+cudaError_t launch_step_sep(const StepParams& P, const Extra& X, int grid, cudaStream_t s);
 cudaError_t launch_batch_step(const BatchEntry* entries, const int* order, int count, int kstep, size_t smem,
                               cudaStream_t s);
 cudaError_t launch_probe_contract(const StepParams& P, const Extra& X, int grid, int x,

@@ -11,7 +11,38 @@ namespace ctd {
 // per other-dimension slot block of the Gram partials:
 // [0] m = v^T M v, [1] k = v^T K v, [2, 2+Mcap) gM_j = v^T M b_j, [2+Mcap, 2+2Mcap) gK_j =
 // v^T K b_j, [2+2Mcap, 2+3Mcap) h_j = v^T M a_j   (a_j: factors of u^k, b_j: of u^{k+1})
-__host__ __device__ inline int slots_per_dim(int Mcap) { return 2 + 3 * Mcap; }
+__host__ __device__ inline int slots_per_dim(int Mcap, int sep_q = 0) { return 2 + 3 * Mcap + sep_q; }
+
+// Multisets {m1 <= m2 <= m3} in colex order (by m3, then m2, then m1), so that those with all
+// indices below M_k are the first sep_terms(M_k); packed m1 | m2 << 8 | m3 << 16 | orderings << 24
+// (orderings: 1, 3 or 6 ordered triples per multiset).
+struct SepTable {
+  unsigned e[kMaxSep];
+};
+constexpr SepTable make_sep_table() {
+  SepTable t{};
+  int q = 0;
+  for (int m3 = 0; m3 < kMaxSepModes; ++m3)
+    for (int m2 = 0; m2 <= m3; ++m2)
+      for (int m1 = 0; m1 <= m2; ++m1) {
+        const unsigned ord = (m1 == m3) ? 1u : ((m1 == m2 || m2 == m3) ? 3u : 6u);
+        t.e[q++] = static_cast<unsigned>(m1) | (static_cast<unsigned>(m2) << 8) | (static_cast<unsigned>(m3) << 16) |
+                   (ord << 24);
+      }
+  return t;
+}
+__constant__ SepTable kSepTable = make_sep_table();
+
+// The separated form (Eq. MxySep) has its own translation unit and step kernel
+// (ctd_kernels_sep.cu compiles ctd_kernels.cu with CTD_SEPARATED_TU); the grid form's kernel
+// holds none of its code.  The separated form requires M_max <= kMaxSepModes, so every M_k is
+// within the multiset table.
+#ifdef CTD_SEPARATED_TU
+constexpr bool kSepTU = true;
+#else
+constexpr bool kSepTU = false;
+#endif
+__device__ __forceinline__ bool sep_active(const StepParams&, int Mk) { return kSepTU && Mk > 0; }
 
 struct Extra {            // per-launch workspace pieces not in StepParams
   KCompressed kc[kMaxDim];
@@ -81,8 +112,9 @@ __device__ __forceinline__ int gram_ctas(const StepParams& P) { return P.vgrid <
 
 static __device__ __noinline__ void gram_partials(const StepParams& P, const Extra& X, int x, int Mk, int M,
                               int pb, int cb, float2* sh) {
-  const int G = gram_ctas(P), cta = P.vrank, D = P.dim, spd = slots_per_dim(P.Mcap);
+  const int G = gram_ctas(P), cta = P.vrank, D = P.dim, spd = slots_per_dim(P.Mcap, P.sep_q);
   if (cta >= G) return;
+  const int nsep = sep_active(P, Mk) ? sep_terms(Mk) : 0;
   float2* sv = sh;               // v_i
   float2* sdv = sh + kChunk;     // omega_i v_i
   float2* skv = sh + 2 * kChunk; // (K v)_i
@@ -92,7 +124,8 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
     const Dim& dd = P.d[d];
     int lo, hi;
     slice_of(dd.n, G, cta, lo, hi);
-    const int nslots = 2 + 2 * M + Mk;
+    const int nbase = 2 + 2 * M + Mk;
+    const int nslots = nbase + nsep;   // separated form: one slot per multiset
     // thread group per slot
     const int tp = min(32, pow2_floor(max(1, kThreads / max(1, nslots))));
     const int groups = kThreads / tp;
@@ -116,6 +149,20 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
         const int s = g + k * groups;
         if (s >= nslots) break;
         dfloat a = acc[k];
+        if (s >= nbase) {
+          // separated form: sum_i (omega v)_i f_m1,i f_m2,i f_m3,i over factors of u^k
+          const unsigned e = kSepTable.e[s - nbase];
+          const float2* f1 = dd.bank[pb] + static_cast<size_t>(e & 0xFF) * dd.n + c0;
+          const float2* f2 = dd.bank[pb] + static_cast<size_t>((e >> 8) & 0xFF) * dd.n + c0;
+          const float2* f3 = dd.bank[pb] + static_cast<size_t>((e >> 16) & 0xFF) * dd.n + c0;
+          for (int i = lane; i < c1 - c0; i += tp) {
+            const float2 x1 = f1[i], x2 = f2[i], x3 = f3[i], w = sdv[i];
+            const dfloat f = df_mul(df_mul(dfloat{x1.x, x1.y}, dfloat{x2.x, x2.y}), dfloat{x3.x, x3.y});
+            a = df_fma(a, f, dfloat{w.x, w.y});
+          }
+          acc[k] = a;
+          continue;
+        }
         // the slot's two vectors: shared-memory staging (v, omega v, K v) or a factor column
         const float2 *lhs, *rhs;
         if (s == 0) { lhs = sv; rhs = sdv; }
@@ -146,7 +193,8 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
         if (s < 2) slot = s;
         else if (s < 2 + M) slot = s;                               // gM
         else if (s < 2 + 2 * M) slot = 2 + P.Mcap + (s - 2 - M);    // gK
-        else slot = 2 + 2 * P.Mcap + (s - 2 - 2 * M);               // h
+        else if (s < nbase) slot = 2 + 2 * P.Mcap + (s - 2 - 2 * M);  // h
+        else slot = 2 + 3 * P.Mcap + (s - nbase);                   // separated multisets
         st_df(P.gram + static_cast<size_t>(o * spd + slot) * G + cta, r);
       }
     }
@@ -156,23 +204,27 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
 
 // Coefficients of Eq. KxQx for direction x, in shared memory (double-float):
 // coef[0] = alpha1, coef[1] = alpha2, H[m] = prod_{d!=x} h_d,m, GM[m] = prod gM_d,m,
-// GK[m] = sum_{d'} gK_{d',m} prod_{d != x,d'} gM_d,m.
+// GK[m] = sum_{d'} gK_{d',m} prod_{d != x,d'} gM_d,m; separated form (Eq. MxySep):
+// T[q] = orderings(q) prod_{d!=x} sum_i (omega v)_d,i f_m1 f_m2 f_m3 for multiset q.
 struct Coef {
   float2 alpha1, alpha2;
   float2 H[kMaxModes], GM[kMaxModes], GK[kMaxModes];
+  float2* T;   // [kMaxSep] in the phase's shared scratch, after the Gram sums
 };
 
-// Used Gram slots of one fixed dimension: m_d, k_d, gM (M), gK (M), h (Mk)
-__host__ __device__ inline int coef_slots(int M, int Mk) { return 2 + 2 * M + Mk; }
-constexpr size_t kCoefScratchBytes = sizeof(float2) * (kMaxDim - 1) * (2 + 3 * kMaxModes);
+// Used Gram slots of one fixed dimension: m_d, k_d, gM (M), gK (M), h (Mk), separated (nsep)
+__host__ __device__ inline int coef_slots(int M, int Mk, int nsep) { return 2 + 2 * M + Mk + nsep; }
+constexpr size_t kCoefScratchSums = (kMaxDim - 1) * (2 + 3 * kMaxModes + kMaxSep);   // float2
+constexpr size_t kCoefScratchBytes = sizeof(float2) * (kCoefScratchSums + kMaxSep);
 
 // Every used slot's G partials are loaded at once (16 lanes per slot, lane g holds CTA g's
 // partial, G <= 16) and summed by a fixed xor tree, so that all CTAs get the same bits.
 // scratch: kCoefScratchBytes of shared memory.
 static __device__ __noinline__ void build_coefficients(const StepParams& P, int x, int Mk, int M, Coef* c,
                                    float2* scratch) {
-  const int G = gram_ctas(P), D = P.dim, spd = slots_per_dim(P.Mcap);
-  const int nO = D - 1, per = coef_slots(M, Mk), nsl = nO * per;
+  const int G = gram_ctas(P), D = P.dim, spd = slots_per_dim(P.Mcap, P.sep_q);
+  const int nsep = sep_active(P, Mk) ? sep_terms(Mk) : 0;
+  const int nO = D - 1, per = coef_slots(M, Mk, nsep), nsl = nO * per;
   const int g = threadIdx.x & 15, sub = threadIdx.x >> 4;
   constexpr int kSub = kThreads / 16;   // slots per round
   constexpr int kRounds = 4;            // rounds whose loads are issued together
@@ -187,7 +239,8 @@ static __device__ __noinline__ void build_coefficients(const StepParams& P, int 
         int slot;
         if (k < 2 + M) slot = k;                                     // m_d, k_d, gM
         else if (k < 2 + 2 * M) slot = 2 + P.Mcap + (k - 2 - M);     // gK
-        else slot = 2 + 2 * P.Mcap + (k - 2 - 2 * M);                // h
+        else if (k < 2 + 2 * M + Mk) slot = 2 + 2 * P.Mcap + (k - 2 - 2 * M);   // h
+        else slot = 2 + 3 * P.Mcap + (k - 2 - 2 * M - Mk);           // separated multisets
         v[r] = P.gram[static_cast<size_t>(o * spd + slot) * G + g];
       }
     }
@@ -217,6 +270,12 @@ static __device__ __noinline__ void build_coefficients(const StepParams& P, int 
       st_df(c->GM + m, GM);
       st_df(c->GK + m, GK);
     }
+  }
+  if (threadIdx.x == 0) c->T = scratch + kCoefScratchSums;
+  for (int q = threadIdx.x; q < nsep; q += blockDim.x) {
+    dfloat t = {static_cast<float>(kSepTable.e[q] >> 24), 0.f};
+    for (int o = 0; o < nO; ++o) t = df_mul(t, ld_df(scratch + o * per + 2 + 2 * M + Mk + q));
+    st_df(scratch + kCoefScratchSums + q, t);
   }
   if (threadIdx.x == 0) {
     const dfloat ct = ld_df(&P.ct_df), ck = ld_df(&P.ck_df);
@@ -249,10 +308,12 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
   const int groups = kThreads / tpr, g = threadIdx.x / tpr, lane = threadIdx.x % tpr;
   const dfloat ct = ld_df(&P.ct_df), ck = ld_df(&P.ck_df), L = ld_df(&P.L_df);
   const int C = P.rchunks[x];
+  const bool sep = sep_active(P, Mk);
+  const int nsep = sep ? sep_terms(Mk) : 0;
   // contraction partials per row block (tensor-core path): a slice of rows shorter than a
   // block spans at most two row blocks; computed once (rb_lo < 0: per row)
   int rb_lo = 0, cr_lo = 0, cr_hi = 0;
-  if (P.precision != 0) {
+  if (P.precision != 0 && !sep) {
     const TcDir& td = X.dirs[x];
     const long long T = static_cast<long long>(td.nrb) * td.ntc;
     rb_lo = lo / kTcM;
@@ -266,10 +327,21 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
   for (int i0 = lo; i0 < hi; i0 += groups) {
     const int i = i0 + g;
     const bool live = i < hi;
-    dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f};
+    dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f}, s4 = {0.f, 0.f};
     if (live) {
-      for (int m = lane; m < Mk; m += tpr)
-        s1 = df_fma(s1, ld_df(dd.bank[pb] + static_cast<size_t>(m) * dd.n + i), ld_df(c->H + m));
+      for (int m = lane; m < Mk; m += tpr) {
+        const dfloat ami = ld_df(dd.bank[pb] + static_cast<size_t>(m) * dd.n + i), h = ld_df(c->H + m);
+        s1 = df_fma(s1, ami, h);
+        if (sep) s4 = df_add(s4, df_neg(df_mul(ami, h)));   // -u part of w (Eq. MxySep)
+      }
+      // u^3 part of w: sum over multisets of a_m1 a_m2 a_m3 (row i of u^k's factors) T_q
+      for (int q = lane; q < nsep; q += tpr) {
+        const unsigned e = kSepTable.e[q];
+        const dfloat a1 = ld_df(dd.bank[pb] + static_cast<size_t>(e & 0xFF) * dd.n + i);
+        const dfloat a2 = ld_df(dd.bank[pb] + static_cast<size_t>((e >> 8) & 0xFF) * dd.n + i);
+        const dfloat a3 = ld_df(dd.bank[pb] + static_cast<size_t>((e >> 16) & 0xFF) * dd.n + i);
+        s4 = df_fma(s4, df_mul(df_mul(a1, a2), a3), ld_df(c->T + q));
+      }
       for (int m = lane; m < M; m += tpr) {
         const dfloat bmi = ld_df(dd.bank[cb] + static_cast<size_t>(m) * dd.n + i);
         const dfloat gm = ld_df(c->GM + m);
@@ -281,9 +353,12 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
     s1 = group_sum(s1, tpr);
     s2 = group_sum(s2, tpr);
     s3 = group_sum(s3, tpr);
+    if (sep) s4 = group_sum(s4, tpr);
     if (live && lane == 0) {
       dfloat R;
-      if (P.precision == 0) {
+      if (sep) {
+        R = df_mul(df_of(4.0 * P.a0), s4);
+      } else if (P.precision == 0) {
         const double* rp = P.rpart + static_cast<size_t>(i) * C;
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
         int k = 0;

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(HERE, "libctd.so")
 
 PREC_FP64 = 0
 PREC_SPLIT_BF16 = 1
+NONLINEAR_GRID = 0         # nonlinear term as the full nodal integral (Eq. KxxMxx)
+NONLINEAR_SEPARATED = 1    # separated form (Eq. MxySep) for steps with M_k <= 16
 
 STATUS = {0: "CTD_OK", 1: "CTD_STATUS_CAPPED", 2: "CTD_STATUS_ALS_NOT_CONVERGED", -1: "CTD_ERR_ARG",
           -2: "CTD_ERR_WORKSPACE", -3: "CTD_ERR_CUDA", -4: "CTD_ERR_NONFINITE", -5: "CTD_ERR_TIMEOUT",
@@ -32,7 +34,7 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("fixed_als_iters", ctypes.c_int),
                 ("fixed_modes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int),
-                ("reduced_tol", ctypes.c_double)]
+                ("reduced_tol", ctypes.c_double), ("nonlinear_form", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -90,7 +92,7 @@ def load() -> ctypes.CDLL:
 
 def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
                 precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
-                grid_ctas=0, reduced_tol=0.0) -> Config:
+                grid_ctas=0, reduced_tol=0.0, nonlinear_form=0) -> Config:
     c = Config()
     c.dim = dim
     for k in range(3):
@@ -103,6 +105,7 @@ def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, 
     c.precision, c.fixed_als_iters, c.fixed_modes = int(precision), int(fixed_als_iters), int(fixed_modes)
     c.seed, c.wait_limit_s, c.grid_ctas = int(seed), float(wait_limit_s), int(grid_ctas)
     c.reduced_tol = float(reduced_tol)
+    c.nonlinear_form = int(nonlinear_form)
     return c
 
 
