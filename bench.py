@@ -217,11 +217,20 @@ def stored_traffic(workload: str, precision: str):
     return e.get("dram_bytes_per_launch")
 
 
-def timed_run(ctd, torch, w, precision, steps, warmup, flush, clocks=None, reduced_tol=0.0):
+def form_over(args, w):
+    """Config overrides of the nonlinear term's form: reduced integration domain, or the
+    separated form (Eq. MxySep, which takes M_max <= 16)."""
+    over = dict(reduced_tol=args.reduced_tol)
+    if args.nonlinear == "separated":
+        over.update(nonlinear_form=1, M_max=min(w.M_max, 16))
+    return over
+
+
+def timed_run(ctd, torch, w, precision, steps, warmup, flush, clocks=None, over=None):
     """Advance `steps` time steps after `warmup`; one step kernel launch each, bracketed by CUDA
     events on the solver's stream, L2 flushed between steps."""
     prec = ctd.PREC_FP64 if precision == "fp64" else ctd.PREC_SPLIT_BF16
-    solver = ctd.Solver(ctd.config_from_workload(w, precision=prec, reduced_tol=reduced_tol))
+    solver = ctd.Solver(ctd.config_from_workload(w, precision=prec, **(over or {})))
     stream = solver.stream
     solver.set_initial_modes(workloads.initial_modes(w))
     for _ in range(warmup):
@@ -259,8 +268,9 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local_rank)
+    over = form_over(args, w)
     solver, times_ms, stats, rank0, clk = timed_run(ctd, torch, w, args.precision, args.steps, args.warmup, flush,
-                                                     clocks, args.reduced_tol)
+                                                     clocks, over)
     if world > 1:
         torch.distributed.barrier()
     total_ms = max_over_ranks(sum(times_ms), world)
@@ -294,7 +304,7 @@ def run_gpu(args, rank, world, local_rank):
     solver.close()
     # first-step result from the initial condition (accuracy check against the oracle)
     prec = ctd.PREC_FP64 if args.precision == "fp64" else ctd.PREC_SPLIT_BF16
-    s2 = ctd.Solver(ctd.config_from_workload(w, precision=prec, reduced_tol=args.reduced_tol))
+    s2 = ctd.Solver(ctd.config_from_workload(w, precision=prec, **over))
     s2.set_initial_modes(workloads.initial_modes(w))
     s2.step(1)
     out["first_step_modes"] = s2.get_modes()
@@ -303,14 +313,12 @@ def run_gpu(args, rank, world, local_rank):
     # and both forms advanced K steps from the initial condition (field error, energy law)
     if args.compare_steps > 0 and rank == 0:
         other = "fp64" if args.precision == "mixed" else "mixed"
-        s3, t3, st3, _, _ = timed_run(ctd, torch, w, other, args.compare_steps, args.warmup, flush,
-                                      reduced_tol=args.reduced_tol)
+        s3, t3, st3, _, _ = timed_run(ctd, torch, w, other, args.compare_steps, args.warmup, flush, over=over)
         s3.close()
         traj = {}
         for prec_name in (args.precision, other):
             sv = ctd.Solver(ctd.config_from_workload(
-                w, precision=ctd.PREC_FP64 if prec_name == "fp64" else ctd.PREC_SPLIT_BF16,
-                reduced_tol=args.reduced_tol))
+                w, precision=ctd.PREC_FP64 if prec_name == "fp64" else ctd.PREC_SPLIT_BF16, **over))
             sv.set_initial_modes(workloads.initial_modes(w))
             energies = [sv.energy()]
             first = None
@@ -345,6 +353,20 @@ def run_gpu(args, rank, world, local_rank):
             sv.close()
         out["full_domain"] = dict(steps=len(tf), ms_per_step=sum(tf) / len(tf),
                                   u_rel_l2_reduced_vs_full=sep_rel_l2(trajs[0], trajs[1]))
+    if args.nonlinear == "separated" and args.compare_steps > 0 and rank == 0:
+        # the grid form (full nodal integral on the tensor cores / in FP64) side by side
+        sg, tg, stg, _, _ = timed_run(ctd, torch, w, args.precision, args.compare_steps, args.warmup, flush)
+        sg.close()
+        trajs = []
+        for o in (over, {}):
+            sv = ctd.Solver(ctd.config_from_workload(
+                w, precision=ctd.PREC_FP64 if args.precision == "fp64" else ctd.PREC_SPLIT_BF16, **o))
+            sv.set_initial_modes(workloads.initial_modes(w))
+            sv.step(args.compare_steps, stats=False)
+            trajs.append(sv.get_modes())
+            sv.close()
+        out["grid_form"] = dict(steps=len(tg), ms_per_step=sum(tg) / len(tg),
+                                u_rel_l2_separated_vs_grid=sep_rel_l2(trajs[0], trajs[1]))
     return w, out
 
 
@@ -577,6 +599,8 @@ def main():
                     help="steps of the other arithmetic (FP64 vs mixed) timed for the side-by-side numbers")
     ap.add_argument("--reduced-tol", type=float, default=0.0,
                     help="reduced integration domain: drop 128 x 128 node blocks with max |w(u^k)| <= this")
+    ap.add_argument("--nonlinear", default="grid", choices=["grid", "separated"],
+                    help="nonlinear term: full nodal integral (Eq. KxxMxx) or separated form (Eq. MxySep)")
     ap.add_argument("--oracle-budget", type=float, default=25.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -660,6 +684,18 @@ def main():
             "note": "one half-sweep's tensor-core contraction as timed by CTA 0's global-timer trace "
                     "(until its own tiles are done); roof = max(split MMA at sustained BF16 peak, "
                     "3 FP32 instructions per grid point)"}
+    if args.nonlinear == "separated":
+        line["config"]["nonlinear"] = "separated (Eq. MxySep), M_max 16"
+        line["roofline"] = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,
+                            "traffic": None, "kernel": "ctd::step_kernel_sep (whole persistent time step)",
+                            "note": "separated form: no grid pass and no dense phase; the step is set by its "
+                                    "barriers and 1D sums (phase_us_per_half_sweep)"}
+        line.pop("contraction_roofline", None)
+        if "grid_form" in res:
+            g = res["grid_form"]
+            line["grid_form"] = {"ms_per_step": g["ms_per_step"], "value": 1e3 / g["ms_per_step"],
+                                 "u_rel_l2_separated_vs_grid": g["u_rel_l2_separated_vs_grid"],
+                                 "note": f"same workload with the full nodal integral, {g['steps']} steps"}
     if args.reduced_tol > 0:
         line["config"]["reduced_tol"] = args.reduced_tol
         if "full_domain" in res:
