@@ -224,7 +224,8 @@ CTD_LOCAL __device__ __noinline__ void solve_direction(const StepParams& P, cons
   const dfloat a1 = ld_df(&sm.coef.alpha1), a2 = ld_df(&sm.coef.alpha2);
   float2* xs = ar.xsol;
   float2* prev = X.xprev + static_cast<size_t>(x) * kMaxN;
-  bool ok = banded_solve(store, X.kc[x], a1, a2, P.Q, xs, sm.redf, P.trace, warm ? prev : nullptr);
+  bool ok = banded_solve(store, X.kc[x], a1, a2, P.Q, xs, sm.redf, P.trace, warm ? prev : nullptr,
+                         P.precision != 0 ? kSolveTolMixed : kSolveTolFp64);
   for (int i = threadIdx.x; i < dd.n; i += blockDim.x) prev[i] = xs[i];
   // zero test and squared norm (double-float, fixed reduction order)
   int nz = 0;

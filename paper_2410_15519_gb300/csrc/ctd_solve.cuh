@@ -776,14 +776,20 @@ __device__ __forceinline__ float cheb_pass_bound(float rho, int its, float kappa
   return 4.f * fmaxf(cheb, kappa * 5.960464477539063e-08f);
 }
 
+// Relative accuracy a solve stops at: 2^-46 of the iterate (the double-float limit) for the
+// FP64 path; 2^-34 for the tensor-core path, whose contraction carries FP32 rounding into
+// every right-hand side (2^-34 is 5.8e-11, far below that).
+constexpr float kSolveTolFp64 = 1.4210854715202004e-14f;
+constexpr float kSolveTolMixed = 5.820766091346741e-11f;
+
 // End of a refinement pass, executed by every thread: CTA max of the correction and of the
 // iterate, trace, and the decision: 0 next pass (with `its` iterations), 1 converged, -1
 // non-finite values.  The error left after the pass is at most bound * dmax; the pass stops
-// the solve once that is below 2^-46 of the iterate, else the next pass gets just enough
+// the solve once that is below tol of the iterate, else the next pass gets just enough
 // iterations to get there (never fewer than the FP32 rounding floor allows).
 __device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& bound, int& its, int pass, float a1,
                                              float a2, float mu_max, float rho, float kappa, float* red,
-                                             unsigned long long* trace, unsigned long long& tsub) {
+                                             unsigned long long* trace, unsigned long long& tsub, float tol) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -803,7 +809,7 @@ __device__ __forceinline__ int cheb_pass_end(float dmax, float xmax, float& boun
     tsub = t;
   }
   if (!(dmax <= 3.0e38f) || !(xmax <= 3.0e38f)) return -1;
-  const float lim = 1.4210854715202004e-14f * xmax;   // 2^-46 of the iterate
+  const float lim = tol * xmax;
   if (dmax <= lim || bound * dmax <= lim) return 1;
   const float need = lim / (2.f * bound * dmax);      // reduction the next pass must reach
   const float floor32 = 4.f * kappa * 5.960464477539063e-08f;
@@ -906,7 +912,7 @@ __device__ __forceinline__ void cheb_iterate_end(float (&er)[2], float (&ee)[2],
 template <int B, int R>
 __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, dfloat a1, dfloat a2, float mu_max,
                              const float2* qg, float2* x, const float2* x0, const ChebSmem& smref,
-                             unsigned long long* trace) {
+                             unsigned long long* trace, float tol) {
   constexpr int W = 2 * B + 1;
   constexpr int NW = R + 2 * B + 2;   // window: halo rows at [1, B + 1) and [R + B + 1, R + 2B + 1)
   constexpr int OWN = B + 1;          // own row j at w[OWN + j] (even index: rows pair up)
@@ -1097,7 +1103,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
         if (!(fabsf(ev.x) <= 3.0e38f) || !(fabsf(ev.y) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
       }
       const int stop = cheb_pass_end(dmax, xmax, bound, its, pass, a1.hi, a2.hi, mu_max, crho, kappa, sm.red, trace,
-                                     tsub);
+                                     tsub, tol);
       if (stop) { fail = stop < 0; break; }
     }
   } else {
@@ -1165,7 +1171,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
         if (!(fabsf(ee[s2]) <= 3.0e38f)) dmax = __int_as_float(0x7f800000);
       }
       const int stop = cheb_pass_end(dmax, xmax, bound, its, pass, a1.hi, a2.hi, mu_max, crho, kappa, sm.red, trace,
-                                     tsub);
+                                     tsub, tol);
       if (stop) { fail = stop < 0; break; }
     }
   }
@@ -1175,20 +1181,20 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
 
 static __device__ __noinline__ bool cheb_banded_solve(const KCompressed& k, dfloat a1, dfloat a2, float mu_max,
                                                       const float2* q, float2* x, const float2* x0,
-                                                      const ChebSmem& sm, unsigned long long* trace) {
+                                                      const ChebSmem& sm, unsigned long long* trace, float tol) {
   ChebLayout L;
   if (!cheb_layout(k.n, k.nlead, k.ntail, k.b, static_cast<int>(blockDim.x) - 32, L)) return false;
   switch (k.b * 100 + L.R) {
-    case 304: return cheb_solve_t<3, 4>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 308: return cheb_solve_t<3, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 312: return cheb_solve_t<3, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 320: return cheb_solve_t<3, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 508: return cheb_solve_t<5, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 512: return cheb_solve_t<5, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 520: return cheb_solve_t<5, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 708: return cheb_solve_t<7, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 712: return cheb_solve_t<7, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
-    case 720: return cheb_solve_t<7, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace);
+    case 304: return cheb_solve_t<3, 4>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 308: return cheb_solve_t<3, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 312: return cheb_solve_t<3, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 320: return cheb_solve_t<3, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 508: return cheb_solve_t<5, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 512: return cheb_solve_t<5, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 520: return cheb_solve_t<5, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 708: return cheb_solve_t<7, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 712: return cheb_solve_t<7, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 720: return cheb_solve_t<7, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
     default: return false;
   }
 }
@@ -1251,8 +1257,8 @@ struct SolverStore {
 // [n].  a1, a2 as double-float.  Returns false on a failed pivot or a non-finite result.
 static __device__ __noinline__ bool banded_solve(const SolverStore& s, const KCompressed& k, dfloat a1, dfloat a2,
                                     const float2* q, float2* x, float* red, unsigned long long* trace = nullptr,
-                                    const float2* x0 = nullptr) {
-  if (s.mode == 3) return cheb_banded_solve(k, a1, a2, s.mu_max, q, x, x0, s.ch, trace);
+                                    const float2* x0 = nullptr, float tol = kSolveTolFp64) {
+  if (s.mode == 3) return cheb_banded_solve(k, a1, a2, s.mu_max, q, x, x0, s.ch, trace, tol);
   const int n = k.n, b = k.b;
   const int npad = (s.mode == 0 ? s.cr.nb : s.l0.nb) * b;
   unsigned long long t0 = trace ? global_ns() : 0ull;
