@@ -218,14 +218,14 @@ CTD_LOCAL __device__ __noinline__ void commit_mode(const StepParams& P, const Ex
 // The solver CTA: solve Eq. ux for direction x, normalise unless x is the last dimension,
 // publish v_x (double-float) and flags in ctrl: [0] zero factor, [1] failure.
 CTD_LOCAL __device__ __noinline__ void solve_direction(const StepParams& P, const Extra& X, int x, SmemStep& sm,
-                                const Arena& ar, bool warm) {
+                                const Arena& ar, bool warm, float tau0) {
   const Dim& dd = P.d[x];
   const SolverStore store = solver_bind(P.solver_mode == 2 ? 0 : P.solver_mode, ar.solver, P.solver, dd.n, dd.b, dd.mu_max);
   const dfloat a1 = ld_df(&sm.coef.alpha1), a2 = ld_df(&sm.coef.alpha2);
   float2* xs = ar.xsol;
   float2* prev = X.xprev + static_cast<size_t>(x) * kMaxN;
   bool ok = banded_solve(store, X.kc[x], a1, a2, P.Q, xs, sm.redf, P.trace, warm ? prev : nullptr,
-                         P.precision != 0 ? kSolveTolMixed : kSolveTolFp64);
+                         P.precision != 0 ? kSolveTolMixed : kSolveTolFp64, tau0);
   for (int i = threadIdx.x; i < dd.n; i += blockDim.x) prev[i] = xs[i];
   // zero test and squared norm (double-float, fixed reduction order)
   int nz = 0;
@@ -339,7 +339,13 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
         if (!sync_all(P, epoch, 4)) return;
         trace_mark(P, tmark, kTrRhs);
         // Phase C: banded solve on CTA 0
-        if (P.vrank == 0) solve_direction(P, X, x, sm, ar, it > 1);
+        // tensor-core path: a warm start from the previous sweep is off by about the mode's last
+        // relative change, so the first pass only needs tol / (4 delta) of error reduction
+        float tau0 = kFirstPassTau;
+        if (P.precision != 0 && it > 1 && delta < 1e299)
+          tau0 = fminf(fmaxf(static_cast<float>(kSolveTolMixed / (4.0 * fmax(delta, 1e-30))), kFirstPassTau),
+                       3.90625e-3f);
+        if (P.vrank == 0) solve_direction(P, X, x, sm, ar, it > 1, tau0);
         if (!sync_all(P, epoch, 5)) return;
         trace_mark(P, tmark, kTrSolve);
         const int zflag = *reinterpret_cast<volatile int*>(X.ctrl + 0);

@@ -781,6 +781,9 @@ __device__ __forceinline__ float cheb_pass_bound(float rho, int its, float kappa
 // every right-hand side (2^-34 is 5.8e-11, far below that).
 constexpr float kSolveTolFp64 = 1.4210854715202004e-14f;
 constexpr float kSolveTolMixed = 5.820766091346741e-11f;
+// Error reduction of a first refinement pass: 2^-22, unless the caller knows its warm start
+// to be closer (then tol over the expected relative change, at most 2^-8)
+constexpr float kFirstPassTau = 2.384185791015625e-07f;
 
 // End of a refinement pass, executed by every thread: CTA max of the correction and of the
 // iterate, trace, and the decision: 0 next pass (with `its` iterations), 1 converged, -1
@@ -912,7 +915,7 @@ __device__ __forceinline__ void cheb_iterate_end(float (&er)[2], float (&ee)[2],
 template <int B, int R>
 __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, dfloat a1, dfloat a2, float mu_max,
                              const float2* qg, float2* x, const float2* x0, const ChebSmem& smref,
-                             unsigned long long* trace, float tol) {
+                             unsigned long long* trace, float tol, float tau0) {
   constexpr int W = 2 * B + 1;
   constexpr int NW = R + 2 * B + 2;   // window: halo rows at [1, B + 1) and [R + B + 1, R + 2B + 1)
   constexpr int OWN = B + 1;          // own row j at w[OWN + j] (even index: rows pair up)
@@ -930,7 +933,7 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
   const float sigma = theta / delta, inv2d = 2.f / delta, c0 = 1.f / theta;
   const float kappa = lmax / lmin;
   const float sk = sqrtf(kappa), crho = (sk - 1.f) / (sk + 1.f);
-  int its = cheb_iterations(a1.hi, a2.hi, mu_max, 2.384185791015625e-07f);   // 2^-22 for a first pass
+  int its = cheb_iterations(a1.hi, a2.hi, mu_max, tau0);   // first pass: error reduction tau0
   const bool ok = (lmin > 0.f) && its < 100000;
   if (its > 4096) its = 4096;
   float bound = cheb_pass_bound(crho, its, kappa);
@@ -1181,20 +1184,21 @@ __device__ bool cheb_solve_t(const KCompressed& kref, const ChebLayout& Lref, df
 
 static __device__ __noinline__ bool cheb_banded_solve(const KCompressed& k, dfloat a1, dfloat a2, float mu_max,
                                                       const float2* q, float2* x, const float2* x0,
-                                                      const ChebSmem& sm, unsigned long long* trace, float tol) {
+                                                      const ChebSmem& sm, unsigned long long* trace, float tol,
+                                                      float tau0) {
   ChebLayout L;
   if (!cheb_layout(k.n, k.nlead, k.ntail, k.b, static_cast<int>(blockDim.x) - 32, L)) return false;
   switch (k.b * 100 + L.R) {
-    case 304: return cheb_solve_t<3, 4>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 308: return cheb_solve_t<3, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 312: return cheb_solve_t<3, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 320: return cheb_solve_t<3, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 508: return cheb_solve_t<5, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 512: return cheb_solve_t<5, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 520: return cheb_solve_t<5, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 708: return cheb_solve_t<7, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 712: return cheb_solve_t<7, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
-    case 720: return cheb_solve_t<7, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol);
+    case 304: return cheb_solve_t<3, 4>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 308: return cheb_solve_t<3, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 312: return cheb_solve_t<3, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 320: return cheb_solve_t<3, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 508: return cheb_solve_t<5, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 512: return cheb_solve_t<5, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 520: return cheb_solve_t<5, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 708: return cheb_solve_t<7, 8>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 712: return cheb_solve_t<7, 12>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
+    case 720: return cheb_solve_t<7, 20>(k, L, a1, a2, mu_max, q, x, x0, sm, trace, tol, tau0);
     default: return false;
   }
 }
@@ -1257,8 +1261,9 @@ struct SolverStore {
 // [n].  a1, a2 as double-float.  Returns false on a failed pivot or a non-finite result.
 static __device__ __noinline__ bool banded_solve(const SolverStore& s, const KCompressed& k, dfloat a1, dfloat a2,
                                     const float2* q, float2* x, float* red, unsigned long long* trace = nullptr,
-                                    const float2* x0 = nullptr, float tol = kSolveTolFp64) {
-  if (s.mode == 3) return cheb_banded_solve(k, a1, a2, s.mu_max, q, x, x0, s.ch, trace, tol);
+                                    const float2* x0 = nullptr, float tol = kSolveTolFp64,
+                                    float tau0 = kFirstPassTau) {
+  if (s.mode == 3) return cheb_banded_solve(k, a1, a2, s.mu_max, q, x, x0, s.ch, trace, tol, tau0);
   const int n = k.n, b = k.b;
   const int npad = (s.mode == 0 ? s.cr.nb : s.l0.nb) * b;
   unsigned long long t0 = trace ? global_ns() : 0ull;
