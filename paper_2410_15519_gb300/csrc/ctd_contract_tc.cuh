@@ -172,13 +172,14 @@ struct TcPlan {
 };
 
 // The first kLightCtas CTAs also compute the Gram partial sums before their tiles; they take
-// half the tiles of the others so that all finish together.  CTA c owns the contiguous tile
-// range [tile_lo(c), tile_lo(c + 1)) with tile_lo(c) = floor(T cum(c) / tot), cum(c) the
-// number of half-weight units before c (1 per light CTA, 2 per other) and tot = cum(G).
+// a quarter of the tiles of the others so that all finish together.  CTA c owns the contiguous
+// tile range [tile_lo(c), tile_lo(c + 1)) with tile_lo(c) = floor(T cum(c) / tot), cum(c) the
+// weight units before c (1 per light CTA, kHeavyWeight per other) and tot = cum(G).
 constexpr int kLightCtas = 16;
+constexpr int kHeavyWeight = 4;
 __host__ __device__ inline long long tile_cum(int G, int c) {
   const int L = G < kLightCtas ? G : kLightCtas;
-  return c <= L ? c : L + 2LL * (c - L);
+  return c <= L ? c : L + static_cast<long long>(kHeavyWeight) * (c - L);
 }
 // floor(a / b) for a, b >= 0; 32-bit division when both fit
 __host__ __device__ inline long long tile_div(long long a, long long b) {
@@ -193,7 +194,7 @@ __host__ __device__ inline int tile_lo(long long T, int G, int c) {
 __host__ __device__ inline int tile_owner(long long T, int G, long long t) {
   const int L = G < kLightCtas ? G : kLightCtas;
   const long long kmax = tile_div((t + 1) * tile_cum(G, G) - 1, T);
-  const long long c = kmax <= L ? kmax : L + (kmax - L) / 2;
+  const long long c = kmax <= L ? kmax : L + (kmax - L) / kHeavyWeight;
   return static_cast<int>(c < G - 1 ? c : G - 1);
 }
 
