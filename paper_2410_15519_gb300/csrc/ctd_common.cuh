@@ -121,19 +121,26 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned& epoch,
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
     unsigned v;
     int ok = 1;
-    const unsigned long long t0 = global_ns();
-    while (true) {
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
-      if (static_cast<int>(v - target) >= 0) break;
-      if (global_ns() - t0 > wait_ns) {
-        ok = 0;
-        atomicOr(&st->status, kErrTimeout);
-        atomicExch(&st->err_info, where);
-        break;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+    if (static_cast<int>(v - target) < 0) {
+      // waiting: also watch the instance status, so that a CTA that timed out elsewhere makes
+      // the others fail fast (checked only while waiting: no extra load on the fast path)
+      const unsigned long long t0 = global_ns();
+      while (true) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+        if (static_cast<int>(v - target) >= 0) break;
+        if (*reinterpret_cast<volatile int*>(&st->status) & kErrTimeout) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > wait_ns) {
+          ok = 0;
+          atomicOr(&st->status, kErrTimeout);
+          atomicExch(&st->err_info, where);
+          break;
+        }
       }
     }
-    // a CTA that timed out makes every later barrier fail fast for the others too
-    if (ok && (*reinterpret_cast<volatile int*>(&st->status) & kErrTimeout)) ok = 0;
     s_ok = ok;
   } else {
     epoch += 1;
