@@ -179,17 +179,31 @@ def algorithmic_flops(w, precision: str, Mk: int, half_sweeps: int) -> float:
     return half_sweeps * 2.0 * 3 * Mk * N
 
 
+def last_cta_tile_share(w, G: int = 152) -> float:
+    """Fraction of direction 0's 128 x 128 tiles that the last of G CTAs contracts (the
+    library's split: the first 16 CTAs, which also form the Gram partial sums, weigh 1, the
+    others 4; CTA c starts at floor(T cum(c) / cum(G)))."""
+    T = 1
+    for d in range(w.dim):
+        T *= -(-w.n[d] // 128)
+    L = min(G, 16)
+    cum = lambda c: c if c <= L else L + 4 * (c - L)
+    lo = T * cum(G - 1) // cum(G)
+    return (T - lo) / T
+
+
 def contraction_roof_us(w, Mk: float, pk: dict) -> dict:
-    """Roofline time of one half-sweep's tensor-core contraction: the larger of the split
-    reconstruction on the tensor cores (2 * 3Mk * N flops at the sustained BF16 peak) and the
-    fused epilogue on the FP32 pipes (3 instructions per grid point: u*u, fma for u^3 - u, fma
-    into the weighted row sum; 152 SMs x 128 lanes x the SM clock)."""
-    N = float(w.grid_points)
-    t_tensor = 2.0 * 3 * Mk * N / (pk["bf16_tflops_sustained"] * 1e12)
-    lanes_per_s = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
-    t_alu = 3.0 * N / lanes_per_s
+    """Roofline time of the last CTA's share of one half-sweep's tensor-core contraction (the
+    phase is timed on that CTA): the larger of the split reconstruction on the tensor cores
+    (2 * 3Mk flops per grid point at one SM's share of the sustained BF16 peak) and the fused
+    epilogue on the FP32 pipes (3 instructions per grid point: u*u, fma for u^3 - u, fma into
+    the weighted row sum; 128 lanes x the SM clock)."""
+    n_cta = float(w.grid_points) * last_cta_tile_share(w)
+    t_tensor = 2.0 * 3 * Mk * n_cta / (pk["bf16_tflops_sustained"] * 1e12 / 152)
+    t_alu = 3.0 * n_cta / (128 * pk.get("sm_max_mhz", 2070.0) * 1e6)
     bound = "tensor" if t_tensor >= t_alu else "alu"
-    return {"roof_us": 1e6 * max(t_tensor, t_alu), "bound": bound, "tensor_us": 1e6 * t_tensor, "alu_us": 1e6 * t_alu}
+    return {"roof_us": 1e6 * max(t_tensor, t_alu), "bound": bound, "tensor_us": 1e6 * t_tensor, "alu_us": 1e6 * t_alu,
+            "grid_points": n_cta}
 
 
 def source_hash() -> str:
@@ -681,9 +695,10 @@ def main():
         line["contraction_roofline"] = {
             "phase_us": ph["contract"], "roof_us": cr["roof_us"], "bound": cr["bound"],
             "frac": cr["roof_us"] / ph["contract"], "tensor_us": cr["tensor_us"], "alu_us": cr["alu_us"],
-            "note": "one half-sweep's tensor-core contraction as timed by CTA 0's global-timer trace "
-                    "(until its own tiles are done); roof = max(split MMA at sustained BF16 peak, "
-                    "3 FP32 instructions per grid point)"}
+            "grid_points_of_cta": cr["grid_points"],
+            "note": "the last CTA's share of one half-sweep's tensor-core contraction (phase entry to its "
+                    "last tile), global-timer trace; roof = max(split MMA at one SM's share of the "
+                    "sustained BF16 peak, 3 FP32 instructions per grid point on 128 lanes)"}
     if args.nonlinear == "separated":
         line["config"]["nonlinear"] = "separated (Eq. MxySep), M_max 16"
         line["roofline"] = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None,

@@ -210,7 +210,8 @@ ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out);
  * 2 Gram products + nonlinear contraction, 3 right-hand sides, 4 banded solve,
  * 5 convergence test, 6 mode commit; inside the banded solve: 8 set-up, 9 first pass,
  * 10 refinement, 11 refinement passes (a count, in units of 1e-9), 14 double-float
- * residuals, 15 inner FP32 solves; 12 Gram products, 13 contraction.  Also counts
+ * residuals, 15 inner FP32 solves; 12 Gram products, 13 contraction (timed on the last CTA,
+ * whose tile share is a full one; every other slot on CTA 0).  Also counts
  * ctd_probe_solve.  Synchronises. */
 ctd_status ctd_probe_trace(ctd_handle h, int enable, double* seconds, int nslots);
 

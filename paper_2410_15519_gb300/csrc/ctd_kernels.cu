@@ -316,8 +316,10 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
         if (P.trace && P.vrank == 0 && threadIdx.x == 0) {
           const unsigned long long t = global_ns();
           atomicAdd(P.trace + kTrGram, t - tsub);
-          tsub = t;
         }
+        // the contraction is timed on the last CTA, which has a full tile share
+        const bool tr_last = P.trace && P.vrank == P.vgrid - 1 && threadIdx.x == 0;
+        const unsigned long long tcon = tr_last ? global_ns() : 0ull;
         if constexpr (kSepTU) {
         } else if (P.precision == 0) {
           load_weights_fp64(P, X, x, ar.wv);
@@ -330,7 +332,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
                            static_cast<float>(4.0 * P.a0), static_cast<float>(P.reduced_tol)))
             return;
         }
-        if (P.trace && P.vrank == 0 && threadIdx.x == 0) atomicAdd(P.trace + kTrContract, global_ns() - tsub);
+        if (tr_last) atomicAdd(P.trace + kTrContract, global_ns() - tcon);
         if (!sync_all(P, epoch, 3)) return;
         trace_mark(P, tmark, kTrGramContract);
         // Phase B: coefficients (every CTA, same order) and right-hand-side rows
