@@ -410,6 +410,63 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
   const int warp_g = P.vrank * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   const int total_warps = P.vgrid * kWarps;
   const double* W = P.W;
+  if (D == 2 && (nc & 1) == 0 && (n0 & 1) == 0 && (n1 & 1) == 0) {
+    // 2D with even extents: two adjacent grid values per 16-byte load, weights read from
+    // shared memory (one broadcast read per row or column pair), two accumulator phases.
+    // The FP64 pipe, not the issue slots, then bounds the pass.
+    const double2* W2 = reinterpret_cast<const double2*>(W);
+    if (x == 1) {
+      // column sums R[c] = sum_r W[r, c] wv0[r]; units (64-column block, row chunk)
+      const int ncp = nc / 2;   // column pairs per row
+      const int cblocks = (ncp + 31) / 32;
+      const int units = cblocks * C;
+      for (int u = warp_g; u < units; u += total_warps) {
+        const int cb = u / C, k = u - cb * C;
+        const int cp = cb * 32 + lane;
+        int r0, r1;
+        slice_of(n0, C, k, r0, r1);
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+        if (cp < ncp) {
+          int r = r0;
+          for (; r + 1 < r1; r += 2) {
+            const double2 w0 = W2[static_cast<size_t>(r) * ncp + cp];
+            const double2 w1 = W2[static_cast<size_t>(r + 1) * ncp + cp];
+            const double f0 = wv[r], f1 = wv[r + 1];
+            a0 = fma(w0.x, f0, a0);
+            a1 = fma(w0.y, f0, a1);
+            b0 = fma(w1.x, f1, b0);
+            b1 = fma(w1.y, f1, b1);
+          }
+          if (r < r1) {
+            const double2 w0 = W2[static_cast<size_t>(r) * ncp + cp];
+            a0 = fma(w0.x, wv[r], a0);
+            a1 = fma(w0.y, wv[r], a1);
+          }
+          P.rpart[static_cast<size_t>(2 * cp) * C + k] = a0 + b0;
+          P.rpart[static_cast<size_t>(2 * cp + 1) * C + k] = a1 + b1;
+        }
+      }
+    } else {
+      // row dots R[r] = sum_q W[r, q] wv1[q]; units (row, column chunk)
+      const double2* wl2 = reinterpret_cast<const double2*>(wv + kMaxN);
+      const int units = nc * C;
+      for (int u = warp_g; u < units; u += total_warps) {
+        const int c = u / C, k = u - c * C;
+        int q0, q1;
+        slice_of(n1 / 2, C, k, q0, q1);   // column pairs
+        const double2* row = W2 + static_cast<size_t>(c) * (n1 / 2);
+        double a0 = 0.0, a1 = 0.0;
+        for (int q = q0 + lane; q < q1; q += 32) {
+          const double2 w = row[q], f = wl2[q];
+          a0 = fma(w.x, f.x, a0);
+          a1 = fma(w.y, f.y, a1);
+        }
+        const double acc = warp_sum(a0 + a1);
+        if (lane == 0) P.rpart[static_cast<size_t>(c) * C + k] = acc;
+      }
+    }
+    return;
+  }
   if (x == D - 1) {
     // column sums: R[c] = sum_r W[r * nc + c] wrow(r); units (32-column block, row chunk)
     const int rows = static_cast<int>(static_cast<long long>(n0) * n1 * n2 / nc);
