@@ -413,7 +413,9 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
   if (D == 2 && (nc & 1) == 0 && (n0 & 1) == 0 && (n1 & 1) == 0) {
     // 2D with even extents: two adjacent grid values per 16-byte load, weights read from
     // shared memory (one broadcast read per row or column pair), two accumulator phases.
-    // The FP64 pipe, not the issue slots, then bounds the pass.
+    // The FP64 pipe, not the issue slots, then bounds the pass.  The grid is read with the
+    // streaming hint (evict first): it is larger than L2 and must not push out the small
+    // working set of the other phases.
     const double2* W2 = reinterpret_cast<const double2*>(W);
     if (x == 1) {
       // column sums R[c] = sum_r W[r, c] wv0[r]; units (64-column block, row chunk)
@@ -429,8 +431,8 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
         if (cp < ncp) {
           int r = r0;
           for (; r + 1 < r1; r += 2) {
-            const double2 w0 = W2[static_cast<size_t>(r) * ncp + cp];
-            const double2 w1 = W2[static_cast<size_t>(r + 1) * ncp + cp];
+            const double2 w0 = __ldcs(W2 + static_cast<size_t>(r) * ncp + cp);
+            const double2 w1 = __ldcs(W2 + static_cast<size_t>(r + 1) * ncp + cp);
             const double f0 = wv[r], f1 = wv[r + 1];
             a0 = fma(w0.x, f0, a0);
             a1 = fma(w0.y, f0, a1);
@@ -438,7 +440,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
             b1 = fma(w1.y, f1, b1);
           }
           if (r < r1) {
-            const double2 w0 = W2[static_cast<size_t>(r) * ncp + cp];
+            const double2 w0 = __ldcs(W2 + static_cast<size_t>(r) * ncp + cp);
             a0 = fma(w0.x, wv[r], a0);
             a1 = fma(w0.y, wv[r], a1);
           }
@@ -457,7 +459,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
         const double2* row = W2 + static_cast<size_t>(c) * (n1 / 2);
         double a0 = 0.0, a1 = 0.0;
         for (int q = q0 + lane; q < q1; q += 32) {
-          const double2 w = row[q], f = wl2[q];
+          const double2 w = __ldcs(row + q), f = wl2[q];
           a0 = fma(w.x, f.x, a0);
           a1 = fma(w.y, f.y, a1);
         }
@@ -638,7 +640,9 @@ static __device__ __noinline__ void materialise_w(const StepParams& P, const Ext
   for (long long p = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x; p < N; p += stride) {
     double u = 0.0;
     if (D == 2) {
-      const int i = static_cast<int>(p / n1), j = static_cast<int>(p - static_cast<long long>(i) * n1);
+      // 32-bit index arithmetic (N < 2^31 for every 2D grid of up to kMaxN^2 nodes)
+      const unsigned pu = static_cast<unsigned>(p);
+      const int i = static_cast<int>(pu / static_cast<unsigned>(n1)), j = static_cast<int>(pu - static_cast<unsigned>(i) * n1);
       for (int m = 0; m < Mk; ++m)
         u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i], X.Af[1][static_cast<size_t>(m) * n1 + j], u);
     } else {
@@ -649,7 +653,7 @@ static __device__ __noinline__ void materialise_w(const StepParams& P, const Ext
         u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i] * X.Af[1][static_cast<size_t>(m) * n1 + j],
                 X.Af[2][static_cast<size_t>(m) * n2 + l], u);
     }
-    P.W[p] = w_of_u(u, P.a0);
+    __stcs(P.W + p, w_of_u(u, P.a0));   // streaming store: the grid exceeds L2
   }
 }
 
