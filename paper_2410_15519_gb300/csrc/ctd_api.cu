@@ -505,6 +505,9 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
       if (stages < 1) { ctd_status s = fail(h, CTD_ERR_UNSUPPORTED, "tensor-core tiles exceed shared memory"); delete h; return s; }
       X.tc_stages = stages;
     }
+    // the tensor-core path allocates all 512 TMEM columns of the SM: more than half the shared
+    // memory keeps it at one CTA per SM, so no CTA waits for another's columns
+    if (cfg->precision == CTD_PREC_SPLIT_BF16) need = std::max(need, static_cast<size_t>(optin) / 2 + 1024);
     P.smem_bytes = static_cast<int>(need);
   }
   InstState st{};

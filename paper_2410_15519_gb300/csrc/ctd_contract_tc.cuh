@@ -12,7 +12,7 @@
 //   * four epilogue warps read the accumulator rows with tcgen05.ld and fuse the cubic
 //     w(u)/(4 a0) = u (u^2 - 1) with the weighted row sum over the tile's columns (weights
 //     4 a0 omega v of the fixed factors), accumulating per row in FP32;
-//   * two TMEM accumulators alternate so the MMAs of tile t+1 overlap the epilogue of t.
+//   * four TMEM accumulators rotate so the MMAs of the next tiles overlap the epilogue of t.
 // Every wait is bounded in time; on expiry the kernel records kErrTimeout and unwinds.
 #pragma once
 
@@ -27,7 +27,8 @@ constexpr int kTcM = 128;              // rows per tile (UMMA M)
 // (2 Kpad / kTcChunkElems) units of kTcChunkBytes
 constexpr int kTcChunkElems = 64;
 constexpr int kTcChunkBytes = kTcM * 128;   // 16 KB
-constexpr int kTcAccCols = 2 * kTcN;   // TMEM columns allocated (two accumulators)
+constexpr int kTcAcc = 4;              // TMEM accumulators in flight (MMAs run ahead of the epilogue)
+constexpr int kTcAccCols = kTcAcc * kTcN;   // TMEM columns allocated: all 512 of the SM
 
 // Tile-image operand layout.  Rows come in blocks of 128; a block holds KS = Kpad / 16 K steps,
 // each a hi and a lo image of 4 KB: 16 groups of 8 rows (256 bytes apart), each group two core
@@ -201,7 +202,7 @@ __host__ __device__ inline int tile_owner(long long T, int G, long long t) {
 struct TcShared {           // barriers and TMEM handle (placed at the start of the arena)
   uint64_t a_full, a_empty;
   uint64_t b_full[8], b_empty[8];
-  uint64_t acc_full[2], acc_empty[2];
+  uint64_t acc_full[kTcAcc], acc_empty[kTcAcc];
   uint32_t tmem_base;
   int abort;
 };
@@ -377,7 +378,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     mbar_init(&sh->a_full, 1);
     mbar_init(&sh->a_empty, 1);
     for (int s = 0; s < stages; ++s) { mbar_init(&sh->b_full[s], 1); mbar_init(&sh->b_empty[s], 1); }
-    for (int a = 0; a < 2; ++a) { mbar_init(&sh->acc_full[a], 1); mbar_init(&sh->acc_empty[a], 128); }
+    for (int a = 0; a < kTcAcc; ++a) { mbar_init(&sh->acc_full[a], 1); mbar_init(&sh->acc_empty[a], 128); }
     sh->abort = 0;
     fence_barrier_init();
   }
@@ -465,8 +466,11 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       }
       const int s = it % stages;
       if (!warp_wait(&sh->b_full[s], (it / stages) & 1, lim, P.st, abort_flag, 24)) { ok = false; break; }
-      const int ab = it & 1;
-      if (it >= 2 && !warp_wait(&sh->acc_empty[ab], ((it >> 1) - 1) & 1, lim, P.st, abort_flag, 25)) { ok = false; break; }
+      const int ab = it % kTcAcc;
+      if (it >= kTcAcc && !warp_wait(&sh->acc_empty[ab], ((it / kTcAcc) - 1) & 1, lim, P.st, abort_flag, 25)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       const uint32_t d = tmem_base + static_cast<uint32_t>(ab * kTcN);
       const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes;
@@ -524,10 +528,10 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       }
       if (!active(t)) continue;
       const int itc = it++;
-      const int ab = itc & 1;
+      const int ab = itc % kTcAcc;
       // each lane leaves its wait on its own; the TMEM loads below are warp-collective
       // (.sync.aligned), so the warp reconverges (and agrees on the outcome) first
-      if (!warp_wait(&sh->acc_full[ab], (itc >> 1) & 1, lim, P.st, abort_flag, 28)) { ok = false; break; }
+      if (!warp_wait(&sh->acc_full[ab], (itc / kTcAcc) & 1, lim, P.st, abort_flag, 28)) { ok = false; break; }
       tc_fence_after();
       const int col0 = cb * kTcN;
       const float* wt;
