@@ -349,10 +349,15 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
                                    unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump,
                                    const unsigned* tile_max = nullptr, float on_scale = 0.f, float on_tol = 0.f) {
   const int G = P.vgrid, cta = P.vrank;
-  auto active = [&](int t) -> bool {
+  // Parameters the role loops use, in registers: P and td live in shared memory, and every
+  // asm statement below (waits, MMAs, commits) is a memory clobber that would reload them.
+  const int ntc = td.ntc, nrb = td.nrb, tmid = td.mid, cmax = td.cmax, n_last_pad = td.n_last_pad;
+  const int ncols_pad = td.ncols_pad, nx = P.d[x].n;
+  InstState* const st = P.st;
+  auto active = [=](int t) -> bool {
     if (!tile_max) return true;
-    const int rb = t / td.ntc, cb = t - rb * td.ntc;
-    const int idx = x == 0 ? t : cb * td.nrb + rb;
+    const int rb = t / ntc, cb = t - rb * ntc;
+    const int idx = x == 0 ? t : cb * nrb + rb;
     return __uint_as_float(tile_max[idx]) * on_scale > on_tol;
   };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -361,15 +366,15 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   // a block's images of the K steps that hold modes: one contiguous bulk copy
   const uint32_t load_bytes = 2u * ksteps * kTcImgBytes;
   const size_t block_elems = static_cast<size_t>(P.Kpad / 16) * 2 * kTcImgElems;
-  const int wl_n = td.mid < 0 ? td.ncols_pad : td.n_last_pad;
-  const int wm_n = td.mid < 0 ? 0 : P.d[td.mid].n;
+  const int wl_n = tmid < 0 ? ncols_pad : n_last_pad;
+  const int wm_n = tmid < 0 ? 0 : P.d[tmid].n;
   const TcLayout Ly = tc_layout(chunks, stages, wl_n, wm_n);
   TcShared* sh = reinterpret_cast<TcShared*>(base + Ly.shared_off);
   unsigned char* As = base + Ly.a_off;
   unsigned char* Bs = base + Ly.b_off;
   float* wl = reinterpret_cast<float*>(base + Ly.wl_off);
   float* wm = reinterpret_cast<float*>(base + Ly.wm_off);
-  const long long T = static_cast<long long>(td.nrb) * td.ntc;
+  const long long T = static_cast<long long>(nrb) * ntc;
   const int t0 = tile_lo(T, G, cta), t1 = tile_lo(T, G, cta + 1);
   const unsigned long long lim = P.wait_ns;
   const uint32_t stage_bytes = static_cast<uint32_t>(chunks) * kTcChunkBytes;
@@ -383,13 +388,13 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     fence_barrier_init();
   }
   // column weights of the fixed factors; in 2D only those of this CTA's column blocks
-  if (td.mid >= 0) {
+  if (tmid >= 0) {
     tc_weights(P, kc[td.last], td.last, wl, wl_n);
-    tc_weights(P, kc[td.mid], td.mid, wm, wm_n);
-  } else if (t1 - t0 >= td.ntc) {
+    tc_weights(P, kc[tmid], tmid, wm, wm_n);
+  } else if (t1 - t0 >= ntc) {
     tc_weights(P, kc[td.last], td.last, wl, wl_n);
   } else if (t1 > t0) {
-    const int cb_lo = t0 % td.ntc, cb_hi = (t1 - 1) % td.ntc;
+    const int cb_lo = t0 % ntc, cb_hi = (t1 - 1) % ntc;
     if (cb_lo <= cb_hi) {
       tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, (cb_hi + 1) * kTcN);
     } else {   // the range wraps into the next row block
@@ -406,12 +411,12 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     // u^k = 0: w(0) = 0, every partial is zero
     if (!dump) {
       for (long long t = t0; t < t1; ++t) {
-        const int rb = static_cast<int>(t / td.ntc);
-        if (t != t0 && t / td.ntc == (t - 1) / td.ntc) continue;
-        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * td.ntc);
+        const int rb = static_cast<int>(t / ntc);
+        if (t != t0 && t / ntc == (t - 1) / ntc) continue;
+        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * ntc);
         for (int r = threadIdx.x; r < kTcM; r += blockDim.x) {
           const int row = rb * kTcM + r;
-          if (row < P.d[x].n) rpart32[static_cast<size_t>(row) * td.cmax + j] = 0.f;
+          if (row < nx) rpart32[static_cast<size_t>(row) * cmax + j] = 0.f;
         }
       }
     }
@@ -427,11 +432,12 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     // ---------------- TMA producer
     if (lane == 0) fence_proxy_async_global();     // operands were written through the generic proxy
     int cur_rb = -1, a_loads = 0;
-    for (int t = t0, it = 0; t < t1 && ok; ++t) {
+    int rb = t0 / ntc, cb = t0 - rb * ntc;   // row and column block of tile t, kept incrementally
+    int s = 0, round = 0;                    // ring stage of the next load and its round
+    for (int t = t0, it = 0; t < t1 && ok; ++t, cb = (cb + 1 == ntc) ? 0 : cb + 1, rb += (cb == 0)) {
       if (!active(t)) continue;
-      const int rb = t / td.ntc, cb = t - rb * td.ntc;
       if (rb != cur_rb) {
-        if (a_loads > 0 && !warp_wait(&sh->a_empty, (a_loads - 1) & 1, lim, P.st, abort_flag, 21)) { ok = false; break; }
+        if (a_loads > 0 && !warp_wait(&sh->a_empty, (a_loads - 1) & 1, lim, st, abort_flag, 21)) { ok = false; break; }
         if (lane == 0) {
           mbar_expect_tx(&sh->a_full, load_bytes);
           bulk_load(As, Pop + static_cast<size_t>(rb) * block_elems, load_bytes, &sh->a_full);
@@ -440,8 +446,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         ++a_loads;
         cur_rb = rb;
       }
-      const int s = it % stages, round = it / stages;
-      if (it >= stages && !warp_wait(&sh->b_empty[s], (round - 1) & 1, lim, P.st, abort_flag, 22)) { ok = false; break; }
+      if (it >= stages && !warp_wait(&sh->b_empty[s], (round - 1) & 1, lim, st, abort_flag, 22)) { ok = false; break; }
       if (lane == 0) {
         mbar_expect_tx(&sh->b_full[s], load_bytes);
         bulk_load(Bs + static_cast<size_t>(s) * stage_bytes, Qop + static_cast<size_t>(cb) * block_elems, load_bytes,
@@ -449,6 +454,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       }
       __syncwarp();
       ++it;
+      if (++s == stages) { s = 0; ++round; }
     }
     if (!ok && lane == 0) sh->abort = 1;
   } else if (warp == 1) {
@@ -456,26 +462,33 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     const uint32_t idesc = umma_idesc_bf16();
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
     int cur_rb = -1, a_uses = 0, n_it = 0;
-    for (int t = t0, it = 0; t < t1 && ok; ++t) {
+    int rb = t0 / ntc, cb = t0 - rb * ntc;
+    int s = 0, round = 0;
+    for (int t = t0, it = 0; t < t1 && ok; ++t, cb = (cb + 1 == ntc) ? 0 : cb + 1, rb += (cb == 0)) {
       if (!active(t)) continue;
-      const int rb = t / td.ntc;
       if (rb != cur_rb) {
-        if (!warp_wait(&sh->a_full, a_uses & 1, lim, P.st, abort_flag, 23)) { ok = false; break; }
+        if (!warp_wait(&sh->a_full, a_uses & 1, lim, st, abort_flag, 23)) { ok = false; break; }
         ++a_uses;
         cur_rb = rb;
       }
-      const int s = it % stages;
-      if (!warp_wait(&sh->b_full[s], (it / stages) & 1, lim, P.st, abort_flag, 24)) { ok = false; break; }
+      if (!warp_wait(&sh->b_full[s], round & 1, lim, st, abort_flag, 24)) { ok = false; break; }
       const int ab = it % kTcAcc;
-      if (it >= kTcAcc && !warp_wait(&sh->acc_empty[ab], ((it / kTcAcc) - 1) & 1, lim, P.st, abort_flag, 25)) {
+      if (it >= kTcAcc && !warp_wait(&sh->acc_empty[ab], ((it / kTcAcc) - 1) & 1, lim, st, abort_flag, 25)) {
         ok = false;
         break;
       }
       tc_fence_after();
       const uint32_t d = tmem_base + static_cast<uint32_t>(ab * kTcN);
       const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes;
-      int tn = t + 1;   // next tile that is contracted
-      while (tn < t1 && !active(tn)) ++tn;
+      // is this the row block's last contracted tile (then its A block is released)?
+      bool last_in_rb;
+      if (!tile_max) {
+        last_in_rb = t + 1 == t1 || cb + 1 == ntc;
+      } else {
+        int tn = t + 1;   // next tile that is contracted
+        while (tn < t1 && !active(tn)) ++tn;
+        last_in_rb = tn == t1 || tn / ntc != rb;
+      }
       if (lane == 0) {
         for (int k = 0; k < ksteps; ++k) {
           const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
@@ -489,11 +502,12 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         }
         tc_commit(&sh->b_empty[s]);
         tc_commit(&sh->acc_full[ab]);
-        if (tn == t1 || tn / td.ntc != rb) tc_commit(&sh->a_empty);
+        if (last_in_rb) tc_commit(&sh->a_empty);
       }
       __syncwarp();
       ++it;
       n_it = it;
+      if (++s == stages) { s = 0; ++round; }
     }
     if (!ok) {
       if (lane == 0) sh->abort = 1;
@@ -501,9 +515,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       // quiesce: the last commits have landed before the barriers are re-initialised
       for (int s = 0; s < stages && s < n_it; ++s) {
         const int last_it = s + ((n_it - 1 - s) / stages) * stages;
-        if (!warp_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, P.st, abort_flag, 26)) { ok = false; break; }
+        if (!warp_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, st, abort_flag, 26)) { ok = false; break; }
       }
-      if (ok && !warp_wait(&sh->a_empty, (a_uses - 1) & 1, lim, P.st, abort_flag, 27)) ok = false;
+      if (ok && !warp_wait(&sh->a_empty, (a_uses - 1) & 1, lim, st, abort_flag, 27)) ok = false;
       if (!ok && lane == 0) sh->abort = 1;
     }
   } else if (warp >= 4) {
@@ -514,13 +528,13 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     int cur_rb = -1;
     auto flush = [&](int rb) {
       const int row = rb * kTcM + r;
-      if (!dump && row < P.d[x].n) {
-        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * td.ntc);
-        rpart32[static_cast<size_t>(row) * td.cmax + j] = acc;
+      if (!dump && row < nx) {
+        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * ntc);
+        rpart32[static_cast<size_t>(row) * cmax + j] = acc;
       }
     };
-    for (int t = t0, it = 0; t < t1; ++t) {
-      const int rb = t / td.ntc, cb = t - rb * td.ntc;
+    int rb = t0 / ntc, cb = t0 - rb * ntc;
+    for (int t = t0, it = 0; t < t1; ++t, cb = (cb + 1 == ntc) ? 0 : cb + 1, rb += (cb == 0)) {
       if (rb != cur_rb) {
         if (cur_rb >= 0) flush(cur_rb);
         acc = 0.f;
@@ -531,16 +545,16 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       const int ab = itc % kTcAcc;
       // each lane leaves its wait on its own; the TMEM loads below are warp-collective
       // (.sync.aligned), so the warp reconverges (and agrees on the outcome) first
-      if (!warp_wait(&sh->acc_full[ab], (itc / kTcAcc) & 1, lim, P.st, abort_flag, 28)) { ok = false; break; }
+      if (!warp_wait(&sh->acc_full[ab], (itc / kTcAcc) & 1, lim, st, abort_flag, 28)) { ok = false; break; }
       tc_fence_after();
       const int col0 = cb * kTcN;
       const float* wt;
       float wscale = 1.f;
-      if (td.mid < 0) {
+      if (tmid < 0) {
         wt = wl + col0;
       } else {
-        const int jm = col0 / td.n_last_pad;
-        wt = wl + (col0 - jm * td.n_last_pad);
+        const int jm = col0 / n_last_pad;
+        wt = wl + (col0 - jm * n_last_pad);
         wscale = wm[jm];
       }
       // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
@@ -553,7 +567,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         tmem_ld32(lane_base + static_cast<uint32_t>(ab * kTcN + q * 32), v);
         if (dump) {
           const int row = rb * kTcM + r;
-          for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * td.ncols_pad + col0 + q * 32 + c] = v[c];
+          for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = v[c];
         }
         const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
 #pragma unroll
