@@ -182,12 +182,12 @@ def algorithmic_flops(w, precision: str, Mk: int, half_sweeps: int) -> float:
 def last_cta_tile_share(w, G: int = 152) -> float:
     """Fraction of direction 0's 128 x 128 tiles that the last of G CTAs contracts (the
     library's split: the first 16 CTAs, which also form the Gram partial sums, weigh 1, the
-    others 4; CTA c starts at floor(T cum(c) / cum(G)))."""
+    others 8; CTA c starts at floor(T cum(c) / cum(G)))."""
     T = 1
     for d in range(w.dim):
         T *= -(-w.n[d] // 128)
     L = min(G, 16)
-    cum = lambda c: c if c <= L else L + 4 * (c - L)
+    cum = lambda c: c if c <= L else L + 8 * (c - L)
     lo = T * cum(G - 1) // cum(G)
     return (T - lo) / T
 

@@ -173,11 +173,11 @@ struct TcPlan {
 };
 
 // The first kLightCtas CTAs also compute the Gram partial sums before their tiles; they take
-// a quarter of the tiles of the others so that all finish together.  CTA c owns the contiguous
+// an eighth of the tiles of the others so that all finish together.  CTA c owns the contiguous
 // tile range [tile_lo(c), tile_lo(c + 1)) with tile_lo(c) = floor(T cum(c) / tot), cum(c) the
 // weight units before c (1 per light CTA, kHeavyWeight per other) and tot = cum(G).
 constexpr int kLightCtas = 16;
-constexpr int kHeavyWeight = 4;
+constexpr int kHeavyWeight = 8;
 __host__ __device__ inline long long tile_cum(int G, int c) {
   const int L = G < kLightCtas ? G : kLightCtas;
   return c <= L ? c : L + static_cast<long long>(kHeavyWeight) * (c - L);
