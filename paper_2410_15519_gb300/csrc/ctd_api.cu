@@ -768,6 +768,8 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
     CTD_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
+  // partial slots of CTAs without a tile in a row block are not written: start from zero
+  CTD_CUDA(h, cudaMemsetAsync(h->X.rpart32, 0, sizeof(float) * std::max<size_t>(1, h->plan.rpart32_len), h->stream));
   CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, nullptr, h->stream));
   const int n = h->cfg.n[x];
   if (h->cfg.precision == CTD_PREC_FP64) {

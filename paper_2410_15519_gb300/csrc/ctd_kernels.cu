@@ -280,6 +280,15 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
   } else {
     tc_prepare(P, X.dirs, X.kr, pb, Mk);
     fence_proxy_async_global();
+    // contraction partial slots start the step at zero (see rhs_rows)
+    size_t nslot = 0;
+    for (int d = 0; d < D; ++d) {
+      const size_t v = static_cast<size_t>(P.d[d].n) * X.dirs[d].cmax;
+      nslot = v > nslot ? v : nslot;
+    }
+    for (size_t i = static_cast<size_t>(P.vrank) * blockDim.x + threadIdx.x; i < nslot;
+         i += static_cast<size_t>(P.vgrid) * blockDim.x)
+      X.rpart32[i] = 0.f;
   }
   if (!kSepTU && P.reduced_tol > 0.0 && Mk > 0) {
     // reduced integration domain (Section 3.3): the nonlinear term is fixed for the step, so

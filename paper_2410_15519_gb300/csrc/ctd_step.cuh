@@ -376,7 +376,10 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         } else {
           Cr = rb == rb_lo ? cr_lo : cr_hi;
         }
-        const float* rp = X.rpart32 + static_cast<size_t>(i) * td.cmax;
+        // Slots of CTAs inside the row block's owner range that hold no tile of it are never
+        // written: the buffer is zero between half-sweeps (cleared in the step prologue, and
+        // every slot read here is cleared again for the next direction)
+        float* rp = X.rpart32 + static_cast<size_t>(i) * td.cmax;
         float part[8];   // loads first, so that their latencies overlap
 #pragma unroll
         for (int k = 0; k < 8; ++k) part[k] = k < Cr ? rp[k] : 0.f;
@@ -385,6 +388,7 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         for (int k = 0; k < 8; ++k)
           if (k < Cr) R = df_add(R, dfloat{part[k], 0.f});
         for (int k = 8; k < Cr; ++k) R = df_add(R, dfloat{rp[k], 0.f});
+        for (int k = 0; k < Cr; ++k) rp[k] = 0.f;
       }
       const float2 om2 = kc_omega(X.kc[x], i);
       const dfloat om = {om2.x, om2.y};
