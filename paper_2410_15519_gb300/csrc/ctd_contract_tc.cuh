@@ -426,6 +426,13 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   volatile int* abort_flag = &sh->abort;
   bool ok = true;
 
+  // Tiles go through the pipeline in groups: two consecutive column blocks of one row block
+  // when no tile is skipped and a stage holds both tiles' images, else one tile.  A group
+  // takes one ring stage (its tiles' images side by side) and one of two accumulator pairs
+  // (TMEM columns [256 p, 256 p + 256)), so each barrier wait and commit covers a group.
+  const bool pairs = !tile_max && 2 * load_bytes <= stage_bytes;
+  auto group_size = [=](int t, int cb) -> int { return (pairs && t + 1 < t1 && cb + 1 < ntc) ? 2 : 1; };
+
   // The producer and MMA warps walk their loops with all lanes (waits by the whole warp, so
   // that it stays converged); lane 0 issues the copies, the MMAs and the commits.
   if (warp == 0) {
@@ -433,9 +440,11 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     if (lane == 0) fence_proxy_async_global();     // operands were written through the generic proxy
     int cur_rb = -1, a_loads = 0;
     int rb = t0 / ntc, cb = t0 - rb * ntc;   // row and column block of tile t, kept incrementally
-    int s = 0, round = 0;                    // ring stage of the next load and its round
-    for (int t = t0, it = 0; t < t1 && ok; ++t, cb = (cb + 1 == ntc) ? 0 : cb + 1, rb += (cb == 0)) {
+    int s = 0, round = 0, gi = 0;            // ring stage of the next group, its round, group count
+    for (int t = t0, g = 1; t < t1 && ok; t += g, cb += g, rb += (cb >= ntc), cb -= (cb >= ntc) ? ntc : 0) {
+      g = 1;
       if (!active(t)) continue;
+      g = group_size(t, cb);
       if (rb != cur_rb) {
         if (a_loads > 0 && !warp_wait(&sh->a_empty, (a_loads - 1) & 1, lim, st, abort_flag, 21)) { ok = false; break; }
         if (lane == 0) {
@@ -446,14 +455,15 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         ++a_loads;
         cur_rb = rb;
       }
-      if (it >= stages && !warp_wait(&sh->b_empty[s], (round - 1) & 1, lim, st, abort_flag, 22)) { ok = false; break; }
+      if (gi >= stages && !warp_wait(&sh->b_empty[s], (round - 1) & 1, lim, st, abort_flag, 22)) { ok = false; break; }
       if (lane == 0) {
-        mbar_expect_tx(&sh->b_full[s], load_bytes);
-        bulk_load(Bs + static_cast<size_t>(s) * stage_bytes, Qop + static_cast<size_t>(cb) * block_elems, load_bytes,
-                  &sh->b_full[s]);
+        mbar_expect_tx(&sh->b_full[s], g * load_bytes);
+        for (int j = 0; j < g; ++j)
+          bulk_load(Bs + static_cast<size_t>(s) * stage_bytes + j * load_bytes,
+                    Qop + static_cast<size_t>(cb + j) * block_elems, load_bytes, &sh->b_full[s]);
       }
       __syncwarp();
-      ++it;
+      ++gi;
       if (++s == stages) { s = 0; ++round; }
     }
     if (!ok && lane == 0) sh->abort = 1;
@@ -461,61 +471,65 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     // ---------------- MMA issuer
     const uint32_t idesc = umma_idesc_bf16();
     const uint32_t a_base = smem_u32(As), b_base = smem_u32(Bs);
-    int cur_rb = -1, a_uses = 0, n_it = 0;
+    int cur_rb = -1, a_uses = 0, n_g = 0;
     int rb = t0 / ntc, cb = t0 - rb * ntc;
-    int s = 0, round = 0;
-    for (int t = t0, it = 0; t < t1 && ok; ++t, cb = (cb + 1 == ntc) ? 0 : cb + 1, rb += (cb == 0)) {
+    int s = 0, round = 0, gi = 0;
+    for (int t = t0, g = 1; t < t1 && ok; t += g, cb += g, rb += (cb >= ntc), cb -= (cb >= ntc) ? ntc : 0) {
+      g = 1;
       if (!active(t)) continue;
+      g = group_size(t, cb);
       if (rb != cur_rb) {
         if (!warp_wait(&sh->a_full, a_uses & 1, lim, st, abort_flag, 23)) { ok = false; break; }
         ++a_uses;
         cur_rb = rb;
       }
       if (!warp_wait(&sh->b_full[s], round & 1, lim, st, abort_flag, 24)) { ok = false; break; }
-      const int ab = it % kTcAcc;
-      if (it >= kTcAcc && !warp_wait(&sh->acc_empty[ab], ((it / kTcAcc) - 1) & 1, lim, st, abort_flag, 25)) {
+      const int ps = gi & 1;   // accumulator pair
+      if (gi >= 2 && !warp_wait(&sh->acc_empty[ps], ((gi >> 1) - 1) & 1, lim, st, abort_flag, 25)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t d = tmem_base + static_cast<uint32_t>(ab * kTcN);
-      const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes;
-      // is this the row block's last contracted tile (then its A block is released)?
+      // is this the row block's last contracted group (then its A block is released)?
       bool last_in_rb;
       if (!tile_max) {
-        last_in_rb = t + 1 == t1 || cb + 1 == ntc;
+        last_in_rb = t + g == t1 || cb + g == ntc;
       } else {
         int tn = t + 1;   // next tile that is contracted
         while (tn < t1 && !active(tn)) ++tn;
         last_in_rb = tn == t1 || tn / ntc != rb;
       }
       if (lane == 0) {
-        for (int k = 0; k < ksteps; ++k) {
-          const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
-          const uint64_t ah = umma_desc_img(a_base + hi_off);
-          const uint64_t al = umma_desc_img(a_base + lo_off);
-          const uint64_t bh = umma_desc_img(bs + hi_off);
-          const uint64_t bl = umma_desc_img(bs + lo_off);
-          tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
-          tc_mma(d, ah, bl, idesc, 1u);
-          tc_mma(d, al, bh, idesc, 1u);
+        for (int j = 0; j < g; ++j) {
+          const uint32_t d = tmem_base + static_cast<uint32_t>((2 * ps + j) * kTcN);
+          const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes + j * load_bytes;
+          for (int k = 0; k < ksteps; ++k) {
+            const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
+            const uint64_t ah = umma_desc_img(a_base + hi_off);
+            const uint64_t al = umma_desc_img(a_base + lo_off);
+            const uint64_t bh = umma_desc_img(bs + hi_off);
+            const uint64_t bl = umma_desc_img(bs + lo_off);
+            tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
+            tc_mma(d, ah, bl, idesc, 1u);
+            tc_mma(d, al, bh, idesc, 1u);
+          }
         }
         tc_commit(&sh->b_empty[s]);
-        tc_commit(&sh->acc_full[ab]);
+        tc_commit(&sh->acc_full[ps]);
         if (last_in_rb) tc_commit(&sh->a_empty);
       }
       __syncwarp();
-      ++it;
-      n_it = it;
+      ++gi;
+      n_g = gi;
       if (++s == stages) { s = 0; ++round; }
     }
     if (!ok) {
       if (lane == 0) sh->abort = 1;
-    } else if (n_it > 0) {
+    } else if (n_g > 0) {
       // quiesce: the last commits have landed before the barriers are re-initialised
-      for (int s = 0; s < stages && s < n_it; ++s) {
-        const int last_it = s + ((n_it - 1 - s) / stages) * stages;
-        if (!warp_wait(&sh->b_empty[s], (last_it / stages) & 1, lim, st, abort_flag, 26)) { ok = false; break; }
+      for (int q = 0; q < stages && q < n_g; ++q) {
+        const int last_g = q + ((n_g - 1 - q) / stages) * stages;
+        if (!warp_wait(&sh->b_empty[q], (last_g / stages) & 1, lim, st, abort_flag, 26)) { ok = false; break; }
       }
       if (ok && !warp_wait(&sh->a_empty, (a_uses - 1) & 1, lim, st, abort_flag, 27)) ok = false;
       if (!ok && lane == 0) sh->abort = 1;
@@ -526,62 +540,68 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16);
     float acc = 0.f;
     int cur_rb = -1;
-    auto flush = [&](int rb) {
-      const int row = rb * kTcM + r;
+    auto flush = [&](int rbf) {
+      const int row = rbf * kTcM + r;
       if (!dump && row < nx) {
-        const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * ntc);
+        const int j = cta - tile_owner(T, G, static_cast<long long>(rbf) * ntc);
         rpart32[static_cast<size_t>(row) * cmax + j] = acc;
       }
     };
     int rb = t0 / ntc, cb = t0 - rb * ntc;
-    for (int t = t0, it = 0; t < t1; ++t, cb = (cb + 1 == ntc) ? 0 : cb + 1, rb += (cb == 0)) {
+    int gi = 0;
+    for (int t = t0, g = 1; t < t1; t += g, cb += g, rb += (cb >= ntc), cb -= (cb >= ntc) ? ntc : 0) {
+      g = 1;
       if (rb != cur_rb) {
         if (cur_rb >= 0) flush(cur_rb);
         acc = 0.f;
         cur_rb = rb;
       }
       if (!active(t)) continue;
-      const int itc = it++;
-      const int ab = itc % kTcAcc;
+      g = group_size(t, cb);
+      const int ps = gi & 1;
       // each lane leaves its wait on its own; the TMEM loads below are warp-collective
       // (.sync.aligned), so the warp reconverges (and agrees on the outcome) first
-      if (!warp_wait(&sh->acc_full[ab], (itc / kTcAcc) & 1, lim, st, abort_flag, 28)) { ok = false; break; }
+      if (!warp_wait(&sh->acc_full[ps], (gi >> 1) & 1, lim, st, abort_flag, 28)) { ok = false; break; }
+      ++gi;
       tc_fence_after();
-      const int col0 = cb * kTcN;
-      const float* wt;
-      float wscale = 1.f;
-      if (tmid < 0) {
-        wt = wl + col0;
-      } else {
-        const int jm = col0 / n_last_pad;
-        wt = wl + (col0 - jm * n_last_pad);
-        wscale = wm[jm];
-      }
-      // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
-      // instruction; four interleaved sums (columns 0, 1, 2, 3 mod 4)
-      float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
-      const float2 m1 = make_float2(-1.f, -1.f);
-#pragma unroll
-      for (int q = 0; q < kTcN / 32; ++q) {
-        float v[32];
-        tmem_ld32(lane_base + static_cast<uint32_t>(ab * kTcN + q * 32), v);
-        if (dump) {
-          const int row = rb * kTcM + r;
-          for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = v[c];
+      for (int j = 0; j < g; ++j) {
+        const int col0 = (cb + j) * kTcN;
+        const float* wt;
+        float wscale = 1.f;
+        if (tmid < 0) {
+          wt = wl + col0;
+        } else {
+          const int jm = col0 / n_last_pad;
+          wt = wl + (col0 - jm * n_last_pad);
+          wscale = wm[jm];
         }
-        const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
+        // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
+        // instruction; four interleaved sums (columns 0, 1, 2, 3 mod 4)
+        float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const uint32_t acol = static_cast<uint32_t>((2 * ps + j) * kTcN);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 ww = w4[c];
-          const float2 u01 = make_float2(v[4 * c], v[4 * c + 1]), u23 = make_float2(v[4 * c + 2], v[4 * c + 3]);
-          a01 = __ffma2_rn(__fmul2_rn(u01, __ffma2_rn(u01, u01, m1)), make_float2(ww.x, ww.y), a01);
-          a23 = __ffma2_rn(__fmul2_rn(u23, __ffma2_rn(u23, u23, m1)), make_float2(ww.z, ww.w), a23);
+        for (int q = 0; q < kTcN / 32; ++q) {
+          float v[32];
+          tmem_ld32(lane_base + acol + static_cast<uint32_t>(q * 32), v);
+          if (dump) {
+            const int row = rb * kTcM + r;
+            for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = v[c];
+          }
+          const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 ww = w4[c];
+            const float2 u01 = make_float2(v[4 * c], v[4 * c + 1]), u23 = make_float2(v[4 * c + 2], v[4 * c + 3]);
+            a01 = __ffma2_rn(__fmul2_rn(u01, __ffma2_rn(u01, u01, m1)), make_float2(ww.x, ww.y), a01);
+            a23 = __ffma2_rn(__fmul2_rn(u23, __ffma2_rn(u23, u23, m1)), make_float2(ww.z, ww.w), a23);
+          }
         }
+        const float at = (a01.x + a01.y) + (a23.x + a23.y);
+        acc = __fmaf_rn(wscale, at, acc);
       }
-      const float at = (a01.x + a01.y) + (a23.x + a23.y);
       tc_fence_before();
-      mbar_arrive(&sh->acc_empty[ab]);
-      acc = __fmaf_rn(wscale, at, acc);
+      mbar_arrive(&sh->acc_empty[ps]);
     }
     if (ok && cur_rb >= 0) flush(cur_rb);
     if (!ok) sh->abort = 1;
