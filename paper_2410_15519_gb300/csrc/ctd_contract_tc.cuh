@@ -300,21 +300,21 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
 // FP32 column weights 4 a0 omega_d v_d of dimension d into shared memory (zero padded),
 // entries [lo, hi) of [0, npad).
 __device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, int d, float* w, int npad,
-                                  int lo = 0, int hi = 1 << 30) {
+                                  int lo, int hi, int tid, int nthr) {
   const Dim& dd = P.d[d];
   const float s = static_cast<float>(4.0 * P.a0);
   if (hi > npad) hi = npad;
   constexpr int kGroup = 8;   // loads of eight entries first, so that their latencies overlap
-  for (int i0 = lo + threadIdx.x; i0 < hi; i0 += kGroup * blockDim.x) {
+  for (int i0 = lo + tid; i0 < hi; i0 += kGroup * nthr) {
     float2 x[kGroup];
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
-      const int i = i0 + g * blockDim.x;
+      const int i = i0 + g * nthr;
       x[g] = i < dd.n ? dd.v[i] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
-      const int i = i0 + g * blockDim.x;
+      const int i = i0 + g * nthr;
       if (i < hi) w[i] = i < dd.n ? s * kc_omega(kc, i).x * (x[g].x + x[g].y) : 0.f;
     }
   }
@@ -386,21 +386,6 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     for (int a = 0; a < kTcAcc; ++a) { mbar_init(&sh->acc_full[a], 1); mbar_init(&sh->acc_empty[a], 128); }
     sh->abort = 0;
     fence_barrier_init();
-  }
-  // column weights of the fixed factors; in 2D only those of this CTA's column blocks
-  if (tmid >= 0) {
-    tc_weights(P, kc[td.last], td.last, wl, wl_n);
-    tc_weights(P, kc[tmid], tmid, wm, wm_n);
-  } else if (t1 - t0 >= ntc) {
-    tc_weights(P, kc[td.last], td.last, wl, wl_n);
-  } else if (t1 > t0) {
-    const int cb_lo = t0 % ntc, cb_hi = (t1 - 1) % ntc;
-    if (cb_lo <= cb_hi) {
-      tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, (cb_hi + 1) * kTcN);
-    } else {   // the range wraps into the next row block
-      tc_weights(P, kc[td.last], td.last, wl, wl_n, 0, (cb_hi + 1) * kTcN);
-      tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, wl_n);
-    }
   }
   // The arena held generic-proxy data of earlier phases (Gram staging, solver vectors) where
   // the bulk copies and the MMAs now write and read through the async proxy: every thread
@@ -537,6 +522,23 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   } else if (warp >= 4) {
     // ---------------- epilogue: one TMEM lane (tile row) per thread
     const int r = (warp - 4) * 32 + lane;
+    // column weights of the fixed factors (in 2D only those of this CTA's column blocks),
+    // formed by the epilogue's 128 threads while the first copies and MMAs are in flight
+    if (tmid >= 0) {
+      tc_weights(P, kc[td.last], td.last, wl, wl_n, 0, wl_n, r, 128);
+      tc_weights(P, kc[tmid], tmid, wm, wm_n, 0, wm_n, r, 128);
+    } else if (t1 - t0 >= ntc) {
+      tc_weights(P, kc[td.last], td.last, wl, wl_n, 0, wl_n, r, 128);
+    } else if (t1 > t0) {
+      const int cb_lo = t0 % ntc, cb_hi = (t1 - 1) % ntc;
+      if (cb_lo <= cb_hi) {
+        tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, (cb_hi + 1) * kTcN, r, 128);
+      } else {   // the range wraps into the next row block
+        tc_weights(P, kc[td.last], td.last, wl, wl_n, 0, (cb_hi + 1) * kTcN, r, 128);
+        tc_weights(P, kc[td.last], td.last, wl, wl_n, cb_lo * kTcN, wl_n, r, 128);
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");   // the epilogue warps only
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16);
     float acc = 0.f;
     int cur_rb = -1;
