@@ -20,6 +20,9 @@ Readings (the paper is silent or defers to another paper that is not available):
     ``M_dd = diag(omega)``; the stiffness integral is exact (Gauss-Legendre, 5 points per
     element, exact because ``N~`` is a polynomial of degree <= 4 on each element when the
     kernel's break points fall on element ends, which holds for a = 12, s <= 3).
+  * The Gauss variant (``gauss_quadrature``, ``quadrature_basis``) evaluates the shape
+    functions at ``q`` Gauss points per element instead; with ``q >= 5`` the mass
+    ``Phi^T diag(omega) Phi`` is the exact consistent mass of Eq. KxxMxx.
 """
 from __future__ import annotations
 
@@ -159,6 +162,37 @@ def consistent_mass_matrix(n, length, s, p, a, gauss_points=5):
         support, N, _ = element_shape(e, n, s, p, a, xg)
         M[np.ix_(support, support)] += (h / 2.0) * (N.T * wg) @ N
     return M
+
+
+def gauss_quadrature(n, length, q):
+    """Composite ``q``-point Gauss-Legendre rule over the ``n - 1`` elements of ``[0, length]``.
+
+    Returns ``(x, omega)`` of length ``q (n - 1)``, ordered element by element: on element
+    ``e`` the points are ``x_e + (1 + xi_g) h / 2`` with weights ``w_g h / 2`` (the Gauss
+    points of each element of Section 3.3).
+    """
+    h = length / (n - 1)
+    xg, wg = gauss_legendre(q)
+    e = np.arange(n - 1)[:, None]
+    x = (e * h + (1.0 + xg[None, :]) * (h / 2.0)).reshape(-1)
+    omega = np.tile(wg * (h / 2.0), n - 1)
+    return x, omega
+
+
+def quadrature_basis(n, length, s, p, a, q):
+    """``Phi[r, j] = N~_j(x_r)`` at the composite Gauss points of ``gauss_quadrature``
+    (Eq. CFEM-1D evaluated element by element), as a scipy CSR matrix of shape
+    ``(q (n - 1), n)``.  A field with nodal coefficients ``c`` has values ``Phi c`` there."""
+    xg, _ = gauss_legendre(q)
+    rows, cols, vals = [], [], []
+    for e in range(n - 1):
+        support, N, _ = element_shape(e, n, s, p, a, xg)
+        rr, cc = np.meshgrid(e * q + np.arange(q), support, indexing="ij")
+        rows.append(rr.ravel())
+        cols.append(cc.ravel())
+        vals.append(N.ravel())
+    return sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(q * (n - 1), n)).tocsr()
 
 
 def nodal_weights(n, length):

@@ -19,9 +19,14 @@ What is computed (paper passages):
 
 Readings of silent or ambiguous points (each also listed in the design notes):
   * Quadrature (the paper only mentions "Gauss points" for the reduced domain): all
-    mass-type integrals -- ``M_dd``, ``M_xy`` and ``int F`` in the energy -- use the nodal
-    trapezoid rule, so ``M_dd = diag(omega_d)`` and ``[M_xy]_ij = L omega_x[i] omega_y[j]
-    w(u^k(x_i, y_j))``; the stiffness is integrated exactly (see ``cfem``).
+    mass-type integrals -- ``M_dd``, ``M_xy`` and ``int F`` in the energy -- share one rule;
+    the stiffness is integrated exactly (see ``cfem``).  The default (``quad_rule =
+    "nodal"``) is the nodal trapezoid rule, so ``M_dd = diag(omega_d)`` and ``[M_xy]_ij = L
+    omega_x[i] omega_y[j] w(u^k(x_i, y_j))``.  ``quad_rule = "gauss"`` takes ``quad_q``
+    Gauss points per element (weights ``omega_d``, shape function values ``Phi_d``):
+    ``M_dd = Phi_d^T diag(omega_d) Phi_d`` (the exact consistent mass of Eq. KxxMxx for
+    ``quad_q >= 5``), ``w(u^k)`` is evaluated at the tensor-product Gauss points and its
+    integral against ``N~_x N~_y`` is ``Phi_x^T`` of the weighted sums there.
   * The 3D equations follow from the same derivation as App. D with one more factor.
   * Start of a mode: the previous step's mode of the same index if it exists and is not
     identically zero, else the SplitMix64 vector of ``splitmix``.
@@ -45,7 +50,7 @@ Readings of silent or ambiguous points (each also listed in the design notes):
 from __future__ import annotations
 
 import dataclasses
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 import scipy.linalg as sla
@@ -80,6 +85,8 @@ class Problem:
     reduced_block: int = 128   # nodes per dimension of the element blocks it keeps or drops
     nonlinear_form: str = "grid"   # "grid" (Eq. KxxMxx) or "separated" (Eq. MxySep)
     separated_max_modes: int = 16  # separated form only for steps with M_k up to this
+    quad_rule: str = "nodal"       # "nodal" (trapezoid at the nodes) or "gauss" (see above)
+    quad_q: int = 5                # Gauss points per element for quad_rule == "gauss"
 
     @property
     def c_t(self) -> float:
@@ -92,19 +99,42 @@ class Problem:
 
 @dataclasses.dataclass
 class Operators:
-    omega: List[np.ndarray]       # nodal quadrature weights per dimension
-    M: List[sp.csr_matrix]        # M_dd = diag(omega_d)
+    omega: List[np.ndarray]       # quadrature weights per dimension (the nodes' for "nodal")
+    M: List[sp.csr_matrix]        # M_dd = Phi_d^T diag(omega_d) Phi_d (diag(omega_d) for "nodal")
     K: List[sp.csr_matrix]        # K_dd = int B~^T B~
+    Phi: Optional[List[sp.csr_matrix]] = None   # shape functions at the Gauss points, or None
 
 
 def build_operators(prob: Problem) -> Operators:
-    omega, M, K = [], [], []
+    omega, M, K, Phi = [], [], [], []
     for d in range(prob.dim):
-        w = cfem.nodal_weights(prob.n[d], prob.length[d])
+        n, length = prob.n[d], prob.length[d]
+        if prob.quad_rule == "nodal":
+            w = cfem.nodal_weights(n, length)
+            M.append(sp.diags(w).tocsr())
+        elif prob.quad_rule == "gauss":
+            _, w = cfem.gauss_quadrature(n, length, prob.quad_q)
+            ph = cfem.quadrature_basis(n, length, prob.s, prob.p, prob.a, prob.quad_q)
+            Phi.append(ph)
+            M.append((ph.T @ sp.diags(w) @ ph).tocsr())
+        else:
+            raise ValueError(f"unknown quadrature rule {prob.quad_rule!r}")
         omega.append(w)
-        M.append(sp.diags(w).tocsr())
-        K.append(cfem.stiffness_matrix(prob.n[d], prob.length[d], prob.s, prob.p, prob.a))
-    return Operators(omega, M, K)
+        K.append(cfem.stiffness_matrix(n, length, prob.s, prob.p, prob.a))
+    return Operators(omega, M, K, Phi if Phi else None)
+
+
+def at_quadrature(ops: Operators, d: int, f: np.ndarray) -> np.ndarray:
+    """Values at the quadrature points of dimension ``d`` of 1D functions with nodal
+    coefficients ``f`` (a vector or an n_d x m matrix): ``Phi_d f``, or ``f`` itself under
+    the nodal rule (Kronecker delta property)."""
+    return f if ops.Phi is None else ops.Phi[d] @ f
+
+
+def from_quadrature(ops: Operators, d: int, r: np.ndarray) -> np.ndarray:
+    """``Phi_d^T r``: from weighted values at the quadrature points to the integrals against
+    each shape function of dimension ``d`` (identity under the nodal rule)."""
+    return r if ops.Phi is None else ops.Phi[d].T @ r
 
 
 def w_of_u(u, a0):
@@ -151,21 +181,26 @@ def reduced_domain_mask(prob: Problem, W: np.ndarray) -> np.ndarray:
 
 
 def nonlinear_tensor(prob: Problem, ops: Operators, A: Sequence[np.ndarray]) -> np.ndarray:
-    """The nonlinear operator of Eq. KxxMxx under the nodal rule, as a D-way array:
+    """The nonlinear operator of Eq. KxxMxx at the quadrature points, as a D-way array:
     ``Mxy[i, j(, l)] = L prod_d omega_d w(u^k(x_i, y_j(, z_l)))``, zero outside the reduced
-    domain when one is set."""
-    U = reconstruct(A)
+    domain when one is set (nodal rule only: its blocks are blocks of nodes)."""
+    if ops.Phi is not None and prob.reduced_tol > 0.0:
+        raise ValueError("the reduced integration domain is defined for the nodal rule only")
+    U = reconstruct([at_quadrature(ops, d, A[d]) for d in range(prob.dim)])
     W = w_of_u(U, prob.a0)
     return prob.L * grid_weights(ops) * W * reduced_domain_mask(prob, W)
 
 
-def separated_nonlinear_terms(prob: Problem, A: Sequence[np.ndarray]):
+def separated_nonlinear_terms(prob: Problem, A: Sequence[np.ndarray], ops: Optional[Operators] = None):
     """Exact separated form of ``w(u^k) = 4 a0 (u^3 - u)`` for ``u^k = sum_m prod_d A[d][:, m]``
     (Eq. energyfunction for w; used by Eq. MxySep): a list of ``(c_q, [f_q,d for d])`` with
     ``w = sum_q c_q prod_d f_q,d``.  The cubic gives one term per multiset m1 <= m2 <= m3
     (``f = A[:, m1] A[:, m2] A[:, m3]``, ``c = 4 a0`` times the multiset's orderings); the
-    linear part gives ``c = -4 a0``, ``f = A[:, m]``."""
+    linear part gives ``c = -4 a0``, ``f = A[:, m]``.  The ``f`` are values at the
+    quadrature points of ``ops`` (at the nodes when ``ops`` is None or nodal)."""
     D = prob.dim
+    if ops is not None:
+        A = [at_quadrature(ops, d, A[d]) for d in range(D)]
     Mk = A[0].shape[1]
     terms = []
     for m1 in range(Mk):
@@ -180,16 +215,17 @@ def separated_nonlinear_terms(prob: Problem, A: Sequence[np.ndarray]):
 
 
 def separated_contraction(prob: Problem, ops: Operators, terms, v: Sequence[np.ndarray], x: int) -> np.ndarray:
-    """``M_xy`` of Eq. MxySep applied to the fixed factors: ``sum_q L c_q (omega_x f_q,x)
-    prod_{d != x} (f_q,d . omega_d v_d)`` (nodal rule for every 1D integral)."""
-    out = np.zeros(prob.n[x])
+    """``M_xy`` of Eq. MxySep applied to the fixed factors: ``sum_q L c_q Phi_x^T (omega_x
+    f_q,x) prod_{d != x} (f_q,d . omega_d Phi_d v_d)`` (the shared rule for every 1D integral;
+    ``Phi = I`` under the nodal rule)."""
+    out = np.zeros(len(ops.omega[x]))
     for c, f in terms:
         s = prob.L * c
         for d in range(prob.dim):
             if d != x:
-                s = s * float(f[d] @ (ops.omega[d] * v[d]))
+                s = s * float(f[d] @ (ops.omega[d] * at_quadrature(ops, d, v[d])))
         out = out + s * (ops.omega[x] * f[x])
-    return out
+    return from_quadrature(ops, x, out)
 
 
 def nonlinear_projection(prob: Problem, ops: Operators, nl, v: Sequence[np.ndarray], x: int) -> np.ndarray:
@@ -197,7 +233,8 @@ def nonlinear_projection(prob: Problem, ops: Operators, nl, v: Sequence[np.ndarr
     ``("separated", terms)``."""
     kind, data = nl
     if kind == "grid":
-        return contract_except(data, v, x)
+        vq = [at_quadrature(ops, d, v[d]) for d in range(prob.dim)]
+        return from_quadrature(ops, x, contract_except(data, vq, x))
     return separated_contraction(prob, ops, data, v, x)
 
 
@@ -205,7 +242,7 @@ def nonlinear_operator(prob: Problem, ops: Operators, A: Sequence[np.ndarray]):
     """The nonlinear term of a step in the form the problem asks for (see the readings)."""
     Mk = A[0].shape[1]
     if prob.nonlinear_form == "separated" and 0 < Mk <= prob.separated_max_modes:
-        return ("separated", separated_nonlinear_terms(prob, A))
+        return ("separated", separated_nonlinear_terms(prob, A, ops))
     return ("grid", nonlinear_tensor(prob, ops, A))
 
 
@@ -395,11 +432,22 @@ def step(prob: Problem, ops: Operators, A: Sequence[np.ndarray], step_index: int
 def energy(prob: Problem, ops: Operators, modes: Sequence[np.ndarray]) -> float:
     """Discrete energy ``E_h(u) = sum_grid omega F(u) + 1/2 kappa u^T K_grad u``.
 
-    ``F`` is integrated with the nodal rule; the gradient term uses the exact 1D stiffness
-    along one axis and the nodal mass along the others (same operators as the step).
+    ``F`` is integrated with the step's rule (at the nodes or the Gauss points); the
+    gradient term uses the exact 1D stiffness along one axis and the mass along the others
+    (same operators as the step).
     """
     U = reconstruct(modes)
     Wg = grid_weights(ops)
+    if ops.Phi is not None:
+        Uq = reconstruct([at_quadrature(ops, d, modes[d]) for d in range(prob.dim)])
+        bulk = float(np.sum(Wg * prob.a0 * (Uq ** 2 - 1.0) ** 2))
+        grad = 0.0
+        for d in range(prob.dim):
+            T = U
+            for e in range(prob.dim):
+                T = apply_along(ops.K[e] if e == d else ops.M[e], T, e)
+            grad += float(np.sum(U * T))
+        return bulk + 0.5 * prob.kappa * grad
     bulk = float(np.sum(Wg * prob.a0 * (U ** 2 - 1.0) ** 2))
     grad = 0.0
     for d in range(prob.dim):
@@ -415,6 +463,14 @@ def energy(prob: Problem, ops: Operators, modes: Sequence[np.ndarray]) -> float:
                 other_w = other_w * ops.omega[e].reshape(sh)
         grad += float(np.sum(U * KT * other_w))
     return bulk + 0.5 * prob.kappa * grad
+
+
+def apply_along(mat, T: np.ndarray, axis: int) -> np.ndarray:
+    """Multiply the D-way array ``T`` by the matrix ``mat`` along ``axis``."""
+    Tm = np.moveaxis(T, axis, 0)
+    shape = Tm.shape
+    out = (mat @ Tm.reshape(shape[0], -1)).reshape((mat.shape[0],) + shape[1:])
+    return np.moveaxis(out, 0, axis)
 
 
 def run(prob: Problem, ops: Operators, A0: Sequence[np.ndarray], nsteps: int,
