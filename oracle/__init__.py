@@ -7,8 +7,10 @@ helpers with ``paper_2410_15519_gb300`` and never imports it.
 
 Modules
 -------
+actd      Adaptive CTD (Section 3.3, "Adaptivity"): the full-grid C-FEM step by fast
+          diagonalisation when a step needs more than M_c modes.
 cfem      1D C-FEM shape functions (App. B radial basis interpolation, App. C), the 1D
-          stiffness matrix (Eq. KxxMxx) and the nodal quadrature weights.
+          stiffness matrix (Eq. KxxMxx), the nodal and Gauss quadrature rules.
 ctd       The stabilized semi-implicit step (Eq. AC-discrete-semi-stable-K) solved in
           separated form by greedy enrichment + alternating fixed point (Section 3.3,
           Eq. ux, Eq. KxQx, Eq. KyQy, App. D), the discrete energy, reconstruction.

@@ -180,6 +180,16 @@ def reduced_domain_mask(prob: Problem, W: np.ndarray) -> np.ndarray:
     return keep
 
 
+def from_quadrature_grid(ops: Operators, G: np.ndarray) -> np.ndarray:
+    """``(x)_d Phi_d^T G``: integrals against every product shape function of a D-way array
+    of weighted values at the quadrature points (``G`` itself under the nodal rule)."""
+    if ops.Phi is None:
+        return G
+    for d in range(G.ndim):
+        G = apply_along(ops.Phi[d].T, G, d)
+    return G
+
+
 def nonlinear_tensor(prob: Problem, ops: Operators, A: Sequence[np.ndarray]) -> np.ndarray:
     """The nonlinear operator of Eq. KxxMxx at the quadrature points, as a D-way array:
     ``Mxy[i, j(, l)] = L prod_d omega_d w(u^k(x_i, y_j(, z_l)))``, zero outside the reduced
@@ -371,15 +381,17 @@ def init_mode(prob: Problem, A: Sequence[np.ndarray], step_index: int, m: int):
 
 
 def step(prob: Problem, ops: Operators, A: Sequence[np.ndarray], step_index: int = 0,
-         trace=None):
+         trace=None, nl=None):
     """One time step u^k -> u^{k+1}; ``A[d]`` holds u^k's factors (n_d x M_k).
 
     Returns ``(B, stats)`` with ``B[d]`` the n_d x M factors of u^{k+1}.  ``trace``, if a
-    list, receives ``(mode, sweep, x, v_copy)`` after every half-sweep (for tests).
+    list, receives ``(mode, sweep, x, v_copy)`` after every half-sweep (for tests).  ``nl``,
+    if given, replaces the nonlinear operator built from ``A`` (the adaptive scheme passes
+    a full-grid one, with ``A`` empty).
     """
     D = prob.dim
     A = [np.asarray(a, dtype=np.float64) for a in A]
-    Mxy = nonlinear_operator(prob, ops, A)
+    Mxy = nonlinear_operator(prob, ops, A) if nl is None else nl
     B = [np.zeros((prob.n[d], 0)) for d in range(D)]
     stats = {"modes": 0, "als_iters": [], "als_delta": [], "amplitude": [],
              "capped": False, "als_not_converged": False}
