@@ -188,3 +188,33 @@ def test_gauss_rule_refuses_the_reduced_domain():
         ctd.nonlinear_tensor(prob, ops, A)
     with pytest.raises(ValueError):
         ctd.build_operators(make_problem(quad_rule="simpson"))
+
+
+def test_gauss_separated_step_equals_gauss_grid_step():
+    # the decomposition of the cubic is exact at the Gauss points too: same decisions, same field
+    w = workloads.preset("c0", n=(14, 12), M_max=6)
+    kw = dict(dim=2, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
+              alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+              tol_enrich=w.tol_enrich, seed=w.seed, quad_rule="gauss", quad_q=3)
+    pg = ctd.Problem(**kw)
+    ps = ctd.Problem(**kw, nonlinear_form="separated")
+    ops = ctd.build_operators(pg)
+    Ag = As = workloads.initial_modes(w)
+    for k in range(2):
+        Ag, sg = ctd.step(pg, ops, Ag, k)
+        As, ss = ctd.step(ps, ops, As, k)
+        assert sg["modes"] == ss["modes"] and sg["als_iters"] == ss["als_iters"], (k, sg, ss)
+        assert ctd.rel_l2_between(As, Ag) < 1e-12, k
+
+
+def test_gauss_ctd_energy_non_increasing_on_small_run():
+    # the energy law carried to the separated solution (tolerances 1e-8 / 1e-4)
+    prob = make_problem(n=24, s=1, p=1, q=3, eps=0.05, dt=0.01, M_max=12)
+    ops = ctd.build_operators(prob)
+    A = workloads.cosine_modes(prob.n, prob.length, 4, 4, 0)
+    E = ctd.energy(prob, ops, A)
+    for k in range(6):
+        A, st = ctd.step(prob, ops, A, k)
+        E1 = ctd.energy(prob, ops, A)
+        assert E1 <= E + 1e-10 * abs(E)
+        E = E1
