@@ -168,6 +168,19 @@ const char* ctd_status_string(int status);
 ctd_status ctd_probe_cfem(const ctd_config* cfg, int d, double* omega, double* kband,
                           int* half_bandwidth);
 
+/* Host-side operators of the Gauss-point quadrature rule of dimension d (no GPU work; the
+ * consistent-mass variant of Eq. KxxMxx, Section 3.3's Gauss points of each element).  q
+ * points per element, 1 <= q <= 16, n_q = q (n[d] - 1) points ordered element by element:
+ *   x_q[n_q], omega_q[n_q]   points and weights of the composite q-point Gauss-Legendre rule;
+ *   phi[n_q][2s+2], phi_col0[n_q]   shape function values, phi[r][k] = N~_{phi_col0[r]+k}(x_r),
+ *                            zero past the support of the point's element (nodes e-s .. e+1+s);
+ *   mband[n[d]][2b+1]        the mass Phi^T diag(omega) Phi in the layout of ctd_probe_cfem's
+ *                            kband (b = 2s+1); for q >= 5 the exact consistent mass.
+ * Any output may be NULL; the caller owns every buffer.  CTD_ERR_ARG for an invalid
+ * configuration, d or q.  Not yet used by ctd_step, which takes the nodal rule. */
+ctd_status ctd_probe_cfem_gauss(const ctd_config* cfg, int d, int q, double* x_q, double* omega_q, double* phi,
+                                int* phi_col0, double* mband);
+
 /* Nonlinear contraction of Eq. KxxMxx for direction x with the current field as u^k:
  * out[i] = sum over the other indices of w(u^k) * prod_{d != x} (omega_d v_d), i.e.
  * M_xy u_y / (L omega_x[i]) under the nodal rule.  v[d] are host arrays of n[d] values

@@ -11,6 +11,10 @@
 // Stiffness K_dd = int B~^T B~ dx (Eq. KxxMxx) per element with 5-point Gauss-Legendre,
 // dx = (h/2) dxi, d/dx = (2/h) d/dxi.  Exact when every break point of the kernel lies on
 // an element end (true for a = 12 with s <= 3).  Nodal weights: trapezoid rule.
+//
+// Gauss-point rule (build_cfem_gauss_1d): q points per element, the shape function values
+// there and the mass Phi^T diag(omega) Phi, which is the exact consistent mass of Eq. KxxMxx
+// for q >= 5 (N~ is a polynomial of degree <= 4 on each element under the same condition).
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -96,7 +100,109 @@ bool patch_coefficients(const std::vector<double>& xs, double a, int p,
   return true;
 }
 
+// q-point Gauss-Legendre rule on [-1, 1], ascending: the roots of the Legendre polynomial
+// P_q by Newton's method (P_q and P_q-1 from the three-term recurrence
+// (k + 1) P_k+1 = (2k + 1) x P_k - k P_k-1, P_q' = q (x P_q - P_q-1) / (x^2 - 1)), started
+// from the asymptotic guess cos(pi (i + 3/4) / (q + 1/2)); weights 2 / ((1 - x^2) P_q'(x)^2).
+bool gauss_legendre(int q, double* xs, double* ws) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (q + 1) / 2; ++i) {
+    double x = std::cos(pi * (i + 0.75) / (q + 0.5)), dp = 1.0;   // p0, p1 end as P_q-1, P_q
+    bool done = false;
+    for (int it = 0; it < 100 && !done; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 1; k < q; ++k) {
+        const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      done = std::fabs(dx) <= 4e-16;
+    }
+    if (!done) return false;
+    // recompute the derivative at the converged root for the weight
+    double p0 = 1.0, p1 = x;
+    for (int k = 1; k < q; ++k) {
+      const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = q * (x * p1 - p0) / (x * x - 1.0);
+    const double w = 2.0 / ((1.0 - x * x) * dp * dp);
+    xs[q - 1 - i] = x;        // largest root first from the guess: fill from the top
+    ws[q - 1 - i] = w;
+    xs[i] = -x;
+    ws[i] = w;
+  }
+  if (q % 2 == 1) xs[q / 2] = 0.0;
+  return true;
+}
+
+// Values N~_k(xi) at natural points xi[0..nx) of element e for every supporting node
+// k = s0 .. s1 (s0 = max(0, e - s), s1 = min(n - 1, e + 1 + s)): N[g * ns + k - s0].
+bool element_values(int e, int n, int s, int p, double a, const double* xi, int nx, std::vector<double>& N) {
+  const int s0 = std::max(0, e - s), s1 = std::min(n - 1, e + 1 + s), ns = s1 - s0 + 1;
+  N.assign(static_cast<size_t>(nx) * ns, 0.0);
+  for (int end = 0; end < 2; ++end) {
+    const int i = e + end;
+    const int p0 = std::max(0, i - s), p1 = std::min(n - 1, i + s), np = p1 - p0 + 1;
+    std::vector<double> xs(np);
+    for (int j = 0; j < np; ++j) xs[j] = -1.0 + 2.0 * (p0 + j - e);
+    std::vector<double> Kc, Lc;
+    if (!patch_coefficients(xs, a, p, Kc, Lc)) return false;
+    for (int g = 0; g < nx; ++g) {
+      const double Ni = end == 0 ? 0.5 * (1.0 - xi[g]) : 0.5 * (1.0 + xi[g]);
+      for (int j = 0; j < np; ++j) {
+        double W = 0.0;
+        for (int l = 0; l < np; ++l) W += kernel(std::fabs(xi[g] - xs[l]) / a) * Kc[l * np + j];
+        double pv = 1.0;
+        for (int qq = 0; qq <= p; ++qq) {
+          W += pv * Lc[qq * np + j];
+          pv *= xi[g];
+        }
+        N[static_cast<size_t>(g) * ns + (p0 + j - s0)] += Ni * W;
+      }
+    }
+  }
+  return true;
+}
+
 }  // namespace
+
+int build_cfem_gauss_1d(int n, double length, int s, int p, double a, int q, double* x_q, double* omega_q,
+                        double* phi, int* phi_col0, double* mband) {
+  if (n < 2 || s < 1 || p < 0 || p > s || !(a > 0.0) || !(length > 0.0) || q < 1 || q > kMaxGaussPoints)
+    return -1;
+  double gx[kMaxGaussPoints], gw[kMaxGaussPoints];
+  if (!gauss_legendre(q, gx, gw)) return -2;
+  const int b = 2 * s + 1, w = 2 * b + 1, wphi = 2 * s + 2;
+  const double h = length / (n - 1);
+  if (mband) std::memset(mband, 0, sizeof(double) * static_cast<size_t>(n) * w);
+  std::vector<double> N;
+  for (int e = 0; e < n - 1; ++e) {
+    const int s0 = std::max(0, e - s), s1 = std::min(n - 1, e + 1 + s), ns = s1 - s0 + 1;
+    if (!element_values(e, n, s, p, a, gx, q, N)) return -2;
+    for (int g = 0; g < q; ++g) {
+      const size_t r = static_cast<size_t>(e) * q + g;
+      const double om = gw[g] * (0.5 * h);
+      if (x_q) x_q[r] = e * h + (1.0 + gx[g]) * (0.5 * h);
+      if (omega_q) omega_q[r] = om;
+      if (phi_col0) phi_col0[r] = s0;
+      if (phi)
+        for (int k = 0; k < wphi; ++k) phi[r * wphi + k] = k < ns ? N[static_cast<size_t>(g) * ns + k] : 0.0;
+      if (mband)
+        for (int k = 0; k < ns; ++k)
+          for (int l = 0; l < ns; ++l) {
+            const int row = s0 + k, col = s0 + l;
+            mband[static_cast<size_t>(row) * w + (col - row + b)] +=
+                om * N[static_cast<size_t>(g) * ns + k] * N[static_cast<size_t>(g) * ns + l];
+          }
+    }
+  }
+  return 0;
+}
 
 int build_cfem_1d(int n, double length, int s, int p, double a, double* omega, double* kband) {
   if (n < 2 || s < 1 || p < 0 || p > s || !(a > 0.0) || !(length > 0.0)) return -1;

@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
     lib.ctd_status_string.argtypes = [i]
     lib.ctd_status_string.restype = ctypes.c_char_p
     lib.ctd_probe_cfem.argtypes = [pcfg, i, vp, vp, ctypes.POINTER(i)]
+    lib.ctd_probe_cfem_gauss.argtypes = [pcfg, i, i, vp, vp, vp, vp, vp]
     lib.ctd_probe_contract.argtypes = [vp, i, ctypes.POINTER(vp), vp]
     lib.ctd_probe_solve.argtypes = [vp, i, d, d, vp, vp]
     lib.ctd_probe_trace.argtypes = [vp, i, vp, i]
@@ -143,6 +144,26 @@ def probe_cfem(cfg: Config, d: int):
     _check(lib, None, lib.ctd_probe_cfem(ctypes.byref(cfg), d, om.ctypes.data, kb.ctypes.data, ctypes.byref(b)),
            "probe_cfem")
     return om, kb, b.value
+
+
+def probe_cfem_gauss(cfg: Config, d: int, q: int):
+    """Host-side Gauss-rule operators of dimension d: (x_q, omega_q, Phi as a dense n_q x n
+    array, mass band [n x (2b+1)])."""
+    lib = load()
+    n, s = cfg.n[d], cfg.s
+    nq, wphi, w = q * (n - 1), 2 * s + 2, 2 * (2 * s + 1) + 1
+    xq, om = np.zeros(nq), np.zeros(nq)
+    phi = np.zeros((nq, wphi))
+    col0 = np.zeros(nq, dtype=np.int32)
+    mb = np.zeros((n, w))
+    _check(lib, None, lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), d, q, xq.ctypes.data, om.ctypes.data,
+                                               phi.ctypes.data, col0.ctypes.data, mb.ctypes.data),
+           "probe_cfem_gauss")
+    dense = np.zeros((nq, n))
+    for r in range(nq):
+        k = min(wphi, n - int(col0[r]))
+        dense[r, col0[r]:col0[r] + k] = phi[r, :k]
+    return xq, om, dense, mb
 
 
 _batch_keep: List = []

@@ -87,6 +87,39 @@ def test_host_cfem_matches_oracle(ctd, n, s, p):
     assert np.array_equal(om, cfem.nodal_weights(n, 1.0))
 
 
+@pytest.mark.parametrize("n,s,p,q", [(33, 1, 1, 2), (40, 2, 2, 5), (29, 3, 3, 3), (17, 2, 1, 7), (12, 2, 2, 16)])
+def test_host_gauss_rule_matches_oracle(ctd, n, s, p, q):
+    # the Gauss-point operators of the consistent-mass variant against the oracle's own
+    # (numpy's Gauss-Legendre rule, the App. B / App. C shape functions, Phi^T diag(omega) Phi)
+    from scipy import sparse
+    cfg = ctd.config_from_workload(workloads.preset("c0", n=(n, n), s=s, p=p))
+    xq, om, Phi, mb = ctd.probe_cfem_gauss(cfg, 0, q)
+    x_ref, om_ref = cfem.gauss_quadrature(n, 1.0, q)
+    # points to 1e-15; weights to 2e-14 (the three-term recurrence rounds a few ulps at q = 16)
+    assert np.max(np.abs(xq - x_ref)) <= 1e-15 and np.max(np.abs(om - om_ref)) <= 2e-14 * np.max(om_ref)
+    Phi_ref = cfem.quadrature_basis(n, 1.0, s, p, 12.0, q).toarray()
+    assert np.max(np.abs(Phi - Phi_ref)) <= 1e-12
+    M_ref = (sparse.csr_matrix(Phi_ref).T @ sparse.diags(om_ref) @ sparse.csr_matrix(Phi_ref)).toarray()
+    b = 2 * s + 1
+    M = np.zeros((n, n))
+    for i in range(n):
+        for k in range(-b, b + 1):
+            if 0 <= i + k < n:
+                M[i, i + k] = mb[i, k + b]
+            else:
+                assert mb[i, k + b] == 0.0
+    assert np.max(np.abs(M - M_ref)) <= 1e-13 * np.max(np.abs(M_ref))
+
+
+def test_host_gauss_rule_refuses_bad_point_counts(ctd):
+    cfg = ctd.config_from_workload(workloads.preset("c0"))
+    lib = ctd.load()
+    err_arg = -1   # CTD_ERR_ARG
+    for q in (0, 17):
+        assert lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), 0, q, None, None, None, None, None) == err_arg
+    assert lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), 2, 5, None, None, None, None, None) == err_arg
+
+
 def test_calls_without_a_handle_fail_cleanly(ctd):
     lib = ctd.load()
     st = ctd.StepStats()
