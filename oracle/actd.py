@@ -28,7 +28,7 @@ from typing import Sequence
 import numpy as np
 import scipy.linalg as sla
 
-from . import ctd
+from . import ctd, fullgrid
 
 
 def eigenpairs(ops: ctd.Operators, d: int):
@@ -81,8 +81,7 @@ def step(prob: ctd.Problem, ops: ctd.Operators, state, M_c: int, step_index: int
     else:
         empty = [np.zeros((prob.n[d], 0)) for d in range(prob.dim)]
         B, st = ctd.step(sub, ops, empty, step_index, nl=("grid", grid_source(prob, ops, data)))
-    if st["modes"] <= M_c:
-        st["capped"] = st["capped"] and budget == prob.M_max
+    if st["modes"] <= M_c:       # (a capped step here has M_max <= M_c modes)
         st["switched"] = False
         return ("modes", B), st
     U = data if kind == "grid" else ctd.reconstruct(data)
@@ -96,10 +95,10 @@ def field(state) -> np.ndarray:
 
 
 def energy(prob: ctd.Problem, ops: ctd.Operators, state) -> float:
+    """Discrete energy of a state (``ctd.energy`` on factors, ``fullgrid.energy`` on a grid)."""
     kind, data = state
     if kind == "modes":
         return ctd.energy(prob, ops, data)
-    from . import fullgrid
     return fullgrid.energy(prob, ops, data)
 
 
