@@ -111,6 +111,18 @@ def test_host_gauss_rule_matches_oracle(ctd, n, s, p, q):
     assert np.max(np.abs(M - M_ref)) <= 1e-13 * np.max(np.abs(M_ref))
 
 
+def test_host_gauss_legendre_rule_for_every_point_count(ctd):
+    # 8 nodes on [0, 7] (h = 1): element e holds the points e + (1 + xi_g) / 2 with weights w_g / 2
+    cfg = ctd.config_from_workload(workloads.preset("c0", n=(8, 8), length=(7.0, 7.0), s=1, p=1))
+    for q in range(1, 17):
+        xq, om, Phi, mb = ctd.probe_cfem_gauss(cfg, 0, q)
+        xg, wg = np.polynomial.legendre.leggauss(q)
+        for e in range(7):
+            assert np.max(np.abs(xq[e * q:(e + 1) * q] - (e + 0.5 * (1.0 + xg)))) <= 1e-14, (q, e)
+            assert np.max(np.abs(om[e * q:(e + 1) * q] - 0.5 * wg)) <= 2e-14 * np.max(wg), (q, e)
+        assert np.max(np.abs(Phi.sum(axis=1) - 1.0)) <= 1e-13, q      # partition of unity
+
+
 def test_host_gauss_rule_refuses_bad_point_counts(ctd):
     cfg = ctd.config_from_workload(workloads.preset("c0"))
     lib = ctd.load()
