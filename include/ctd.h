@@ -175,11 +175,15 @@ ctd_status ctd_probe_cfem(const ctd_config* cfg, int d, double* omega, double* k
  *   phi[n_q][2s+2], phi_col0[n_q]   shape function values, phi[r][k] = N~_{phi_col0[r]+k}(x_r),
  *                            zero past the support of the point's element (nodes e-s .. e+1+s);
  *   mband[n[d]][2b+1]        the mass Phi^T diag(omega) Phi in the layout of ctd_probe_cfem's
- *                            kband (b = 2s+1); for q >= 5 the exact consistent mass.
+ *                            kband (b = 2s+1); for q >= 5 the exact consistent mass;
+ *   mass_bounds[2]           lo <= lambda <= hi for every eigenvalue of diag(M)^-1 M (the
+ *                            bounds of a Chebyshev solve preconditioned by diag(M)): banded
+ *                            Cholesky tests of M - lo diag(M) and hi diag(M) - M, widened by 1e-6.
  * Any output may be NULL; the caller owns every buffer.  CTD_ERR_ARG for an invalid
- * configuration, d or q.  Not yet used by ctd_step, which takes the nodal rule. */
+ * configuration, d or q, or a mass that is not positive definite.  Not yet used by
+ * ctd_step, which takes the nodal rule. */
 ctd_status ctd_probe_cfem_gauss(const ctd_config* cfg, int d, int q, double* x_q, double* omega_q, double* phi,
-                                int* phi_col0, double* mband);
+                                int* phi_col0, double* mband, double* mass_bounds);
 
 /* Nonlinear contraction of Eq. KxxMxx for direction x with the current field as u^k:
  * out[i] = sum over the other indices of w(u^k) * prod_{d != x} (omega_d v_d), i.e.

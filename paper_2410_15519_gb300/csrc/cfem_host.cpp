@@ -169,10 +169,64 @@ bool element_values(int e, int n, int s, int p, double a, const double* xi, int 
   return true;
 }
 
+// True if the symmetric band A (n x (2b+1), entry (i, j-i+b) = A[i][j]) is positive definite:
+// banded Cholesky without pivoting succeeds with positive pivots (Sylvester's criterion).  A
+// pivot must exceed 1e-12 of its diagonal entry, so that a matrix singular up to rounding
+// fails; in the bisections below this only widens the bounds.
+bool band_is_spd(const std::vector<double>& A, int n, int b) {
+  const int w = 2 * b + 1;
+  std::vector<double> L(static_cast<size_t>(n) * (b + 1), 0.0);   // L[i][k] = L(i, i - b + k)
+  for (int i = 0; i < n; ++i) {
+    for (int j = std::max(0, i - b); j <= i; ++j) {
+      double acc = A[static_cast<size_t>(i) * w + (j - i + b)];
+      for (int k = std::max(0, i - b); k < j; ++k)
+        acc -= L[static_cast<size_t>(i) * (b + 1) + (k - i + b)] * L[static_cast<size_t>(j) * (b + 1) + (k - j + b)];
+      if (j == i) {
+        if (!(acc > 1e-12 * std::fabs(A[static_cast<size_t>(i) * w + b]))) return false;
+        L[static_cast<size_t>(i) * (b + 1) + b] = std::sqrt(acc);
+      } else {
+        L[static_cast<size_t>(i) * (b + 1) + (j - i + b)] = acc / L[static_cast<size_t>(j) * (b + 1) + b];
+      }
+    }
+  }
+  return true;
+}
+
+// Bounds [lo, hi] of the spectrum of diag(M)^-1 M for the SPD band M: lo is the largest c found
+// by bisection with M - c diag(M) positive definite, hi the smallest with c diag(M) - M
+// positive definite (both tested by banded Cholesky), each moved outward by a relative 1e-6.
+void mass_spectrum_bounds(const std::vector<double>& M, int n, int b, double* lo, double* hi) {
+  const int w = 2 * b + 1;
+  double gersh = 0.0;            // Gershgorin: every eigenvalue is below max_i sum_j |M_ij| / M_ii
+  for (int i = 0; i < n; ++i) {
+    double r = 0.0;
+    for (int k = 0; k < w; ++k) r += std::fabs(M[static_cast<size_t>(i) * w + k]);
+    gersh = std::max(gersh, r / M[static_cast<size_t>(i) * w + b]);
+  }
+  std::vector<double> T(M.size());
+  auto shifted = [&](double c, double sign) {   // sign (M - c diag(M)), diagonal shift only
+    for (size_t e = 0; e < M.size(); ++e) T[e] = sign * M[e];
+    for (int i = 0; i < n; ++i) T[static_cast<size_t>(i) * w + b] -= sign * c * M[static_cast<size_t>(i) * w + b];
+    return band_is_spd(T, n, b);
+  };
+  double a0 = 0.0, a1 = 1.0;     // M - 0 D is SPD; M - 1 D is not (its diagonal is zero)
+  for (int it = 0; it < 60; ++it) {
+    const double c = 0.5 * (a0 + a1);
+    (shifted(c, 1.0) ? a0 : a1) = c;
+  }
+  double b0 = 1.0, b1 = gersh * (1.0 + 1e-12) + 1e-12;   // c D - M: not SPD at 1, SPD above Gershgorin
+  for (int it = 0; it < 60; ++it) {
+    const double c = 0.5 * (b0 + b1);
+    (shifted(c, -1.0) ? b1 : b0) = c;
+  }
+  *lo = a0 * (1.0 - 1e-6);
+  *hi = b1 * (1.0 + 1e-6);
+}
+
 }  // namespace
 
 int build_cfem_gauss_1d(int n, double length, int s, int p, double a, int q, double* x_q, double* omega_q,
-                        double* phi, int* phi_col0, double* mband) {
+                        double* phi, int* phi_col0, double* mband, double* mass_bounds) {
   if (n < 2 || s < 1 || p < 0 || p > s || !(a > 0.0) || !(length > 0.0) || q < 1 || q > kMaxGaussPoints)
     return -1;
   double gx[kMaxGaussPoints], gw[kMaxGaussPoints];
@@ -180,7 +234,11 @@ int build_cfem_gauss_1d(int n, double length, int s, int p, double a, int q, dou
   const int b = 2 * s + 1, w = 2 * b + 1, wphi = 2 * s + 2;
   const double h = length / (n - 1);
   if (mband) std::memset(mband, 0, sizeof(double) * static_cast<size_t>(n) * w);
-  std::vector<double> N;
+  std::vector<double> N, Mown;
+  if (!mband && mass_bounds) {   // the bounds need the band: assemble into a private copy
+    Mown.assign(static_cast<size_t>(n) * w, 0.0);
+    mband = Mown.data();
+  }
   for (int e = 0; e < n - 1; ++e) {
     const int s0 = std::max(0, e - s), s1 = std::min(n - 1, e + 1 + s), ns = s1 - s0 + 1;
     if (!element_values(e, n, s, p, a, gx, q, N)) return -2;
@@ -200,6 +258,13 @@ int build_cfem_gauss_1d(int n, double length, int s, int p, double a, int q, dou
                 om * N[static_cast<size_t>(g) * ns + k] * N[static_cast<size_t>(g) * ns + l];
           }
     }
+  }
+  if (mass_bounds) {
+    const std::vector<double> M(mband, mband + static_cast<size_t>(n) * w);
+    for (int i = 0; i < n; ++i)
+      if (!(M[static_cast<size_t>(i) * w + b] > 0.0)) return -2;
+    if (!band_is_spd(M, n, b)) return -2;
+    mass_spectrum_bounds(M, n, b, &mass_bounds[0], &mass_bounds[1]);
   }
   return 0;
 }

@@ -322,12 +322,12 @@ ctd_status ctd_probe_cfem(const ctd_config* cfg, int d, double* omega, double* k
 }
 
 ctd_status ctd_probe_cfem_gauss(const ctd_config* cfg, int d, int q, double* x_q, double* omega_q, double* phi,
-                                int* phi_col0, double* mband) {
+                                int* phi_col0, double* mband, double* mass_bounds) {
   ctd_status v = validate(cfg);
   if (v != CTD_OK) return v;
   if (d < 0 || d >= cfg->dim || q < 1 || q > ctd::kMaxGaussPoints) return CTD_ERR_ARG;
   if (ctd::build_cfem_gauss_1d(cfg->n[d], cfg->length[d], cfg->s, cfg->p, cfg->a, q, x_q, omega_q, phi, phi_col0,
-                               mband) != 0)
+                               mband, mass_bounds) != 0)
     return CTD_ERR_ARG;
   return CTD_OK;
 }

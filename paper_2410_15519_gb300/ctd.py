@@ -74,7 +74,7 @@ def load() -> ctypes.CDLL:
     lib.ctd_status_string.argtypes = [i]
     lib.ctd_status_string.restype = ctypes.c_char_p
     lib.ctd_probe_cfem.argtypes = [pcfg, i, vp, vp, ctypes.POINTER(i)]
-    lib.ctd_probe_cfem_gauss.argtypes = [pcfg, i, i, vp, vp, vp, vp, vp]
+    lib.ctd_probe_cfem_gauss.argtypes = [pcfg, i, i, vp, vp, vp, vp, vp, vp]
     lib.ctd_probe_contract.argtypes = [vp, i, ctypes.POINTER(vp), vp]
     lib.ctd_probe_solve.argtypes = [vp, i, d, d, vp, vp]
     lib.ctd_probe_trace.argtypes = [vp, i, vp, i]
@@ -146,9 +146,10 @@ def probe_cfem(cfg: Config, d: int):
     return om, kb, b.value
 
 
-def probe_cfem_gauss(cfg: Config, d: int, q: int):
+def probe_cfem_gauss(cfg: Config, d: int, q: int, bounds: bool = True):
     """Host-side Gauss-rule operators of dimension d: (x_q, omega_q, Phi as a dense n_q x n
-    array, mass band [n x (2b+1)])."""
+    array, mass band [n x (2b+1)], (lo, hi) bounds of the spectrum of diag(M)^-1 M, or None
+    when ``bounds`` is False)."""
     lib = load()
     n, s = cfg.n[d], cfg.s
     nq, wphi, w = q * (n - 1), 2 * s + 2, 2 * (2 * s + 1) + 1
@@ -156,14 +157,16 @@ def probe_cfem_gauss(cfg: Config, d: int, q: int):
     phi = np.zeros((nq, wphi))
     col0 = np.zeros(nq, dtype=np.int32)
     mb = np.zeros((n, w))
+    bd = np.zeros(2)
     _check(lib, None, lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), d, q, xq.ctypes.data, om.ctypes.data,
-                                               phi.ctypes.data, col0.ctypes.data, mb.ctypes.data),
+                                               phi.ctypes.data, col0.ctypes.data, mb.ctypes.data,
+                                               bd.ctypes.data if bounds else None),
            "probe_cfem_gauss")
     dense = np.zeros((nq, n))
     for r in range(nq):
         k = min(wphi, n - int(col0[r]))
         dense[r, col0[r]:col0[r] + k] = phi[r, :k]
-    return xq, om, dense, mb
+    return xq, om, dense, mb, ((float(bd[0]), float(bd[1])) if bounds else None)
 
 
 _batch_keep: List = []

@@ -93,7 +93,7 @@ def test_host_gauss_rule_matches_oracle(ctd, n, s, p, q):
     # (numpy's Gauss-Legendre rule, the App. B / App. C shape functions, Phi^T diag(omega) Phi)
     from scipy import sparse
     cfg = ctd.config_from_workload(workloads.preset("c0", n=(n, n), s=s, p=p))
-    xq, om, Phi, mb = ctd.probe_cfem_gauss(cfg, 0, q)
+    xq, om, Phi, mb, bounds = ctd.probe_cfem_gauss(cfg, 0, q)
     x_ref, om_ref = cfem.gauss_quadrature(n, 1.0, q)
     # points to 1e-15; weights to 2e-14 (the three-term recurrence rounds a few ulps at q = 16)
     assert np.max(np.abs(xq - x_ref)) <= 1e-15 and np.max(np.abs(om - om_ref)) <= 2e-14 * np.max(om_ref)
@@ -109,13 +109,18 @@ def test_host_gauss_rule_matches_oracle(ctd, n, s, p, q):
             else:
                 assert mb[i, k + b] == 0.0
     assert np.max(np.abs(M - M_ref)) <= 1e-13 * np.max(np.abs(M_ref))
+    # spectrum bounds of diag(M)^-1 M: enclose the exact extreme eigenvalues, tightly
+    from scipy import linalg
+    lam = linalg.eigh(M_ref, np.diag(np.diag(M_ref)), eigvals_only=True)
+    lo, hi = bounds
+    assert lo <= lam[0] <= lo * (1 + 1e-4) and hi * (1 - 1e-4) <= lam[-1] <= hi, (bounds, lam[0], lam[-1])
 
 
 def test_host_gauss_legendre_rule_for_every_point_count(ctd):
     # 8 nodes on [0, 7] (h = 1): element e holds the points e + (1 + xi_g) / 2 with weights w_g / 2
     cfg = ctd.config_from_workload(workloads.preset("c0", n=(8, 8), length=(7.0, 7.0), s=1, p=1))
     for q in range(1, 17):
-        xq, om, Phi, mb = ctd.probe_cfem_gauss(cfg, 0, q)
+        xq, om, Phi, mb, _ = ctd.probe_cfem_gauss(cfg, 0, q, bounds=False)
         xg, wg = np.polynomial.legendre.leggauss(q)
         for e in range(7):
             assert np.max(np.abs(xq[e * q:(e + 1) * q] - (e + 0.5 * (1.0 + xg)))) <= 1e-14, (q, e)
@@ -127,9 +132,14 @@ def test_host_gauss_rule_refuses_bad_point_counts(ctd):
     cfg = ctd.config_from_workload(workloads.preset("c0"))
     lib = ctd.load()
     err_arg = -1   # CTD_ERR_ARG
+    # one point per element: 7 points for 8 nodes leave the mass singular, so no bounds
+    c8 = ctd.config_from_workload(workloads.preset("c0", n=(8, 8), length=(7.0, 7.0), s=1, p=1))
+    bd = np.zeros(2)
+    assert lib.ctd_probe_cfem_gauss(ctypes.byref(c8), 0, 1, None, None, None, None, None, bd.ctypes.data) == err_arg
+    assert lib.ctd_probe_cfem_gauss(ctypes.byref(c8), 0, 2, None, None, None, None, None, bd.ctypes.data) == 0
     for q in (0, 17):
-        assert lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), 0, q, None, None, None, None, None) == err_arg
-    assert lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), 2, 5, None, None, None, None, None) == err_arg
+        assert lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), 0, q, None, None, None, None, None, None) == err_arg
+    assert lib.ctd_probe_cfem_gauss(ctypes.byref(cfg), 2, 5, None, None, None, None, None, None) == err_arg
 
 
 def test_calls_without_a_handle_fail_cleanly(ctd):
