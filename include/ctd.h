@@ -35,7 +35,8 @@ extern "C" {
 typedef enum {
   CTD_OK = 0,
   CTD_STATUS_CAPPED = 1,            /* a step reached M_max modes (Section 3.3 adaptivity cap) */
-  CTD_STATUS_ALS_NOT_CONVERGED = 2, /* some mode used I_max sweeps without meeting tol_als   */
+  CTD_STATUS_ALS_NOT_CONVERGED = 2, /* some mode ended its sweeps without meeting tol_als: at
+                                       I_max sweeps, or by the stall rule (als_stall_tol)     */
   CTD_ERR_ARG = -1,                 /* invalid argument or configuration                     */
   CTD_ERR_WORKSPACE = -2,           /* workspace missing, too small or misaligned            */
   CTD_ERR_CUDA = -3,                /* a CUDA runtime call failed                            */
@@ -85,6 +86,17 @@ typedef struct {
                                integral becomes a 1D sum, no grid pass.  Requires
                                M_max <= 16 and reduced_tol == 0 (CTD_ERR_ARG otherwise);
                                ctd_step_batch refuses it (CTD_ERR_UNSUPPORTED).            */
+  double als_stall_tol;     /* > 0: stall rule of the fixed-point sweeps (Section 3.3's loop
+                               until the mode stops changing, read with the paper's absolute
+                               example test, the change of the rank-1 term in field units):
+                               after at least 3 sweeps a mode whose relative change delta
+                               satisfies delta * amp <= als_stall_tol * amp_lead and
+                               delta >= delta_prev / 2 ends its sweeps (amp = prod_d max|v_d|,
+                               amp_lead that of the step's first mode, the mode's own for the
+                               first).  Such a mode has not met tol_als: it is counted in
+                               ctd_step_stats.als_stalled and the step returns
+                               CTD_STATUS_ALS_NOT_CONVERGED.  0: off (tol_als or I_max only).
+                               Same rule for every precision.                              */
 } ctd_config;
 
 enum { CTD_NONLINEAR_GRID = 0, CTD_NONLINEAR_SEPARATED = 1 };
@@ -94,8 +106,9 @@ typedef struct {
   int als_sweeps;           /* fixed-point sweeps over all modes tried in the step          */
   int als_sweeps_max;       /* largest per-mode sweep count                                 */
   int capped;               /* 1 if the step ended at M_max                                 */
-  int not_converged;        /* 1 if some mode ended at I_max without meeting tol_als       */
+  int not_converged;        /* 1 if some mode ended without meeting tol_als (I_max or stall) */
   int status;               /* ctd_status of the step                                       */
+  int als_stalled;          /* modes whose sweeps the stall rule ended (als_stall_tol)      */
 } ctd_step_stats;
 
 typedef struct ctd_ctx* ctd_handle;
@@ -188,11 +201,17 @@ ctd_status ctd_probe_cfem_gauss(const ctd_config* cfg, int d, int q, double* x_q
 /* Nonlinear contraction of Eq. KxxMxx for direction x with the current field as u^k:
  * out[i] = sum over the other indices of w(u^k) * prod_{d != x} (omega_d v_d), i.e.
  * M_xy u_y / (L omega_x[i]) under the nodal rule.  v[d] are host arrays of n[d] values
- * (v[x] ignored).  Uses cfg.precision. */
+ * (v[x] ignored).  Uses cfg.precision.  The v[d] are copied into the handle's trial factors,
+ * which a probe may overwrite (every mode of the next ctd_step starts afresh, so its result
+ * is unchanged). */
 ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, double* out);
 
 /* Solve (alpha1 diag(omega_x) + alpha2 K_x) y = q with the step's banded solver (FP32
- * block cyclic reduction + FP64-accurate iterative refinement); host arrays of n[x]. */
+ * Chebyshev semi-iteration on the diag(omega)-scaled operator, or FP32 block cyclic
+ * reduction where the Chebyshev row split does not fit, inside iterative refinement with
+ * double-float residuals); host arrays of n[x].  Uses the handle's solver vectors and trial
+ * factor v[x] as scratch: the next ctd_step starts its modes afresh, so this does not change
+ * its result. */
 ctd_status ctd_probe_solve(ctd_handle h, int x, double alpha1, double alpha2,
                            const double* q, double* y);
 
@@ -200,7 +219,8 @@ ctd_status ctd_probe_solve(ctd_handle h, int x, double alpha1, double alpha2,
  * handles only): out[i * ncols_pad + c] for the n_pad[x] x ncols_pad tile grid of direction
  * x (rows: nodes of x padded to 128; columns: nodes of the other dimension (2D) or the
  * other dimensions' index pairs (3D, last one padded to 128)), FP32.  scratch: device
- * buffer of at least the output size.  Synchronises. */
+ * buffer of at least the output size.  Synchronises.  Sets the handle's trial factors to
+ * ones (the next ctd_step starts its modes afresh, so its result is unchanged). */
 ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch, size_t scratch_bytes);
 
 /* ctd_probe_reconstruct without a caller scratch buffer; the paper has no counterpart (it is

@@ -38,6 +38,14 @@ Readings of silent or ambiguous points (each also listed in the design notes):
   * Enrichment stop (paper: ``max|u_x u_y^T| <= eps2``): ``prod_d max|v_d| <= tol_enrich``
     (exactly the max of the rank-1 tensor); the failing mode is discarded.  Reaching
     ``M_max`` committed modes ends the step with the "capped" flag.
+  * Stall rule (optional, ``als_stall_tol > 0``; off by default): the paper's own example
+    test is an absolute one, ``max|Delta(u_x u_y^T)| <= eps1``, i.e. a change measured in
+    the units of the field.  Read that way, a mode whose change, in units of the step's
+    leading mode (``delta * amp <= als_stall_tol * amp_lead``, ``amp = prod_d max|v_d|``,
+    ``amp_lead`` the leading mode's amplitude, the mode's own for mode 0), is small and no
+    longer shrinking (``delta >= delta_prev / 2``) after at least 3 sweeps ends its sweeps.
+    Such a mode has not met ``tol_als``: it is counted as stalled and the step reports
+    ``als_not_converged``.
   * If a solve returns an all-zero factor the mode is zero: its sweep stops at once and the
     enrichment test discards it.
   * Separated nonlinearity (the paper names SVD or HOPGD for the decomposition of w(u^k)):
@@ -81,6 +89,7 @@ class Problem:
     seed: int = 0
     fixed_als_iters: int = 0   # >0: exactly this many sweeps per mode (strict-parity mode)
     fixed_modes: int = 0       # >0: exactly this many modes per step (strict-parity mode)
+    als_stall_tol: float = 0.0  # >0: stall rule of the fixed-point sweeps (see the readings)
     reduced_tol: float = 0.0   # >0: reduced integration domain (Section 3.3), see below
     reduced_block: int = 128   # nodes per dimension of the element blocks it keeps or drops
     nonlinear_form: str = "grid"   # "grid" (Eq. KxxMxx) or "separated" (Eq. MxySep)
@@ -394,13 +403,15 @@ def step(prob: Problem, ops: Operators, A: Sequence[np.ndarray], step_index: int
     Mxy = nonlinear_operator(prob, ops, A) if nl is None else nl
     B = [np.zeros((prob.n[d], 0)) for d in range(D)]
     stats = {"modes": 0, "als_iters": [], "als_delta": [], "amplitude": [],
-             "capped": False, "als_not_converged": False}
+             "capped": False, "als_not_converged": False, "als_stalled": 0}
     n_modes = prob.fixed_modes if prob.fixed_modes > 0 else prob.M_max
     stopped = False
+    amp_lead = 0.0
     for m in range(n_modes):
         v = init_mode(prob, A, step_index, m)
         zero_mode = False
         delta = np.inf
+        delta_prev = np.inf
         it = 0
         n_it = prob.fixed_als_iters if prob.fixed_als_iters > 0 else prob.I_max
         for it in range(1, n_it + 1):
@@ -421,10 +432,20 @@ def step(prob: Problem, ops: Operators, A: Sequence[np.ndarray], step_index: int
             delta = rel_change(v, v_old)
             if prob.fixed_als_iters == 0 and delta <= prob.tol_als:
                 break
+            if prob.als_stall_tol > 0.0 and prob.fixed_als_iters == 0 and it >= 3:
+                # stall rule (readings): the change in units of the leading mode, no longer shrinking
+                amp = float(np.prod([np.max(np.abs(y)) for y in v]))
+                lead = amp if m == 0 else amp_lead
+                if delta * amp <= prob.als_stall_tol * lead and delta >= 0.5 * delta_prev:
+                    stats["als_stalled"] += 1
+                    break
+            delta_prev = delta
         converged = zero_mode or prob.fixed_als_iters > 0 or delta <= prob.tol_als
         if not converged:
             stats["als_not_converged"] = True
         amp = 0.0 if zero_mode else float(np.prod([np.max(np.abs(x)) for x in v]))
+        if m == 0:
+            amp_lead = amp
         stats["als_iters"].append(it)
         stats["als_delta"].append(0.0 if zero_mode else float(delta))
         stats["amplitude"].append(amp)

@@ -186,7 +186,7 @@ const char* status_text(int s) {
   switch (s) {
     case CTD_OK: return "ok";
     case CTD_STATUS_CAPPED: return "a step reached the mode cap M_max";
-    case CTD_STATUS_ALS_NOT_CONVERGED: return "a mode reached I_max sweeps without meeting tol_als";
+    case CTD_STATUS_ALS_NOT_CONVERGED: return "a mode ended its sweeps without meeting tol_als (I_max or stall rule)";
     case CTD_ERR_ARG: return "invalid argument";
     case CTD_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case CTD_ERR_CUDA: return "CUDA runtime error";
@@ -211,6 +211,7 @@ ctd_status validate(const ctd_config* c) {
   if (!(c->dt > 0.0) || !std::isfinite(c->dt)) return CTD_ERR_ARG;
   if (c->M_max < 1 || c->M_max > ctd::kMaxModes || c->I_max < 1) return CTD_ERR_ARG;
   if (!(c->tol_als >= 0.0) || !(c->tol_enrich >= 0.0)) return CTD_ERR_ARG;
+  if (!(c->als_stall_tol >= 0.0) || !std::isfinite(c->als_stall_tol)) return CTD_ERR_ARG;
   if (c->fixed_als_iters < 0 || c->fixed_modes < 0 || c->fixed_modes > c->M_max) return CTD_ERR_ARG;
   if (c->precision != CTD_PREC_FP64 && c->precision != CTD_PREC_SPLIT_BF16) return CTD_ERR_ARG;
   if (c->grid_ctas > kGridMax) return CTD_ERR_ARG;
@@ -384,6 +385,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   }
   P.tol_als = cfg->tol_als;
   P.tol_enrich = cfg->tol_enrich;
+  P.als_stall = cfg->als_stall_tol;
   P.reduced_tol = cfg->reduced_tol;
   P.nl_form = cfg->nonlinear_form;
   P.sep_q = h->plan.sep_q;
@@ -596,6 +598,7 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
         o.als_sweeps_max = rec[k].als_sweeps_max;
         o.capped = rec[k].capped;
         o.not_converged = rec[k].not_converged;
+        o.als_stalled = rec[k].als_stalled;
         o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
         if (o.status < 0) worst = static_cast<ctd_status>(o.status);
         else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -680,6 +683,7 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
           o.als_sweeps_max = rec[k].als_sweeps_max;
           o.capped = rec[k].capped;
           o.not_converged = rec[k].not_converged;
+          o.als_stalled = rec[k].als_stalled;
           o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
           if (o.status < 0) worst = static_cast<ctd_status>(o.status);
           else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);

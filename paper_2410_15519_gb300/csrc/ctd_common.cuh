@@ -53,6 +53,7 @@ struct StepStatsDev {
   int capped;
   int not_converged;
   int status;
+  int als_stalled;
 };
 
 struct StepParams {
@@ -64,6 +65,7 @@ struct StepParams {
   double c_t, c_k, L, a0;
   float2 ct_df, ck_df, L_df;   // the same constants as double-float (converted on the host)
   double tol_als, tol_enrich;
+  double als_stall;        // > 0: stall rule of the fixed-point sweeps (0: off)
   int I_max, M_max, fixed_als, fixed_modes;
   unsigned long long seed;
   unsigned long long wait_ns;

@@ -302,7 +302,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
   }
   trace_mark(P, tmark, kTrPrologue);
 
-  int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0;
+  int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0, n_stalled = 0;
   double amp0 = 0.0;   // amplitude max|(x)v| of the step's leading mode
   bool stopped = false;
   const int n_modes = P.fixed_modes > 0 ? P.fixed_modes : P.M_max;
@@ -424,15 +424,15 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
         __syncthreads();
       }
       if (P.fixed_als == 0 && delta <= P.tol_als) break;
-      // Tensor-core arithmetic: the contraction's FP32 rounding sets a floor on how far a mode
-      // can still move.  Once the change of the mode, measured against the step's leading mode
-      // (delta * amp against amp_lead; delta alone for the leading mode), is below 1e-6 and
-      // no longer shrinking, further sweeps only move the mode within that floor.
-      const double amp_lead = m == 0 ? amp : amp0;
-      if (P.precision != 0 && P.fixed_als == 0 && it >= 3 && delta * amp <= 1e-6 * amp_lead &&
-          delta >= 0.5 * delta_prev) {
-        delta = P.tol_als;
-        break;
+      // Stall rule (optional): the change of the mode in units of the step's leading mode
+      // (delta * amp against amp_lead; delta alone for the leading mode) is below als_stall
+      // and no longer shrinking.  The mode has not met tol_als; it is counted as stalled.
+      if (P.als_stall > 0.0 && P.fixed_als == 0 && it >= 3) {
+        const double amp_lead = m == 0 ? amp : amp0;
+        if (delta * amp <= P.als_stall * amp_lead && delta >= 0.5 * delta_prev) {
+          ++n_stalled;
+          break;
+        }
       }
       delta_prev = delta;
     }
@@ -468,6 +468,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     r.capped = (P.fixed_modes == 0 && !stopped) ? 1 : 0;
     r.not_converged = not_conv;
     r.status = 0;
+    r.als_stalled = n_stalled;
     *P.stats = r;
   }
 }

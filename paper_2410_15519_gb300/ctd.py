@@ -34,12 +34,14 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("fixed_als_iters", ctypes.c_int),
                 ("fixed_modes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int),
-                ("reduced_tol", ctypes.c_double), ("nonlinear_form", ctypes.c_int)]
+                ("reduced_tol", ctypes.c_double), ("nonlinear_form", ctypes.c_int),
+                ("als_stall_tol", ctypes.c_double)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("als_sweeps_max", ctypes.c_int),
-                ("capped", ctypes.c_int), ("not_converged", ctypes.c_int), ("status", ctypes.c_int)]
+                ("capped", ctypes.c_int), ("not_converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("als_stalled", ctypes.c_int)]
 
 
 class CTDError(RuntimeError):
@@ -93,7 +95,7 @@ def load() -> ctypes.CDLL:
 
 def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
                 precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
-                grid_ctas=0, reduced_tol=0.0, nonlinear_form=0) -> Config:
+                grid_ctas=0, reduced_tol=0.0, nonlinear_form=0, als_stall_tol=0.0) -> Config:
     c = Config()
     c.dim = dim
     for k in range(3):
@@ -107,6 +109,7 @@ def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, 
     c.seed, c.wait_limit_s, c.grid_ctas = int(seed), float(wait_limit_s), int(grid_ctas)
     c.reduced_tol = float(reduced_tol)
     c.nonlinear_form = int(nonlinear_form)
+    c.als_stall_tol = float(als_stall_tol)
     return c
 
 
@@ -202,7 +205,8 @@ def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True,
     out = []
     for i in range(count):
         out.append([dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
-                         capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status)
+                         capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
+                         als_stalled=r.als_stalled)
                     for r in rec[i * nsteps:(i + 1) * nsteps]])
     return out
 
@@ -264,7 +268,8 @@ class Solver:
         st = self.lib.ctd_step(self.h, nsteps, rec)
         _check(self.lib, self.h, st, "ctd_step")
         return [dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
-                     capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status) for r in rec]
+                     capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
+                         als_stalled=r.als_stalled) for r in rec]
 
     def energy(self) -> float:
         e = ctypes.c_double(0.0)

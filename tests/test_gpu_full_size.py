@@ -97,3 +97,50 @@ def test_3d_tensor_core_contraction_sampled_rows(lib, name):
         assert np.linalg.norm(got[rows] - rb[:, 0]) <= 2e-4 * np.linalg.norm(rb[:, 0]), x
         assert np.all(np.isfinite(got))
     s.close()
+
+
+def field_rel_l2(A, B):
+    """||u_A - u_B|| / ||u_B|| on the nodes of two separated fields, rebuilt in FP64 on the GPU
+    slab by slab (a Gram-matrix form would cancel at the differences measured here)."""
+    import torch
+    ta = [torch.as_tensor(a, dtype=torch.float64, device="cuda") for a in A]
+    tb = [torch.as_tensor(b, dtype=torch.float64, device="cuda") for b in B]
+    n0 = ta[0].shape[0]
+    num = den = 0.0
+    step = 64 if len(ta) == 3 else n0
+    for i0 in range(0, n0, step):
+        i1 = min(n0, i0 + step)
+        if len(ta) == 2:
+            ua, ub = ta[0][i0:i1] @ ta[1].T, tb[0][i0:i1] @ tb[1].T
+        else:
+            ua = torch.einsum("im,jm,km->ijk", ta[0][i0:i1], ta[1], ta[2])
+            ub = torch.einsum("im,jm,km->ijk", tb[0][i0:i1], tb[1], tb[2])
+        num += float(torch.sum((ua - ub) ** 2))
+        den += float(torch.sum(ub ** 2))
+    return (num / den) ** 0.5
+
+
+@pytest.mark.parametrize("name,nsteps", [("c2", 2), ("c3", 1)])
+def test_3d_whole_steps_mixed_vs_fp64(lib, name, nsteps):
+    # The full 3D configurations step for step: the split-BF16 tensor-core form against the
+    # plain FP64 form on the GPU (the oracle cannot hold these grids), both under the same
+    # stop rules; field and energy within the mixed-precision bar, energy non-increasing.
+    w = workloads.preset(name)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        p = lib.PREC_FP64 if prec == "fp64" else lib.PREC_SPLIT_BF16
+        s = lib.Solver(lib.config_from_workload(w, precision=p, als_stall_tol=1e-6))
+        s.set_initial_modes(workloads.initial_modes(w))
+        E = [s.energy()]
+        st = []
+        for _ in range(nsteps):
+            st.append(s.step(1)[0])
+            E.append(s.energy())
+        out[prec] = (s.get_modes(), E, st)
+        s.close()
+    (G64, E64, s64), (Gmx, Emx, smx) = out["fp64"], out["mixed"]
+    assert all(r["status"] >= 0 for r in s64 + smx)
+    assert field_rel_l2(Gmx, G64) < 1e-5
+    assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1])
+    for E in (E64, Emx):
+        assert all(e1 <= e0 + 1e-10 * abs(e0) for e0, e1 in zip(E, E[1:])), E

@@ -91,7 +91,8 @@ def run_pair(lib, w, nsteps, energies=False, **cfg_over):
         G = solver.get_modes()
         e_u = octd.rel_l2_between(G, A) if st_o["modes"] else float(np.abs(octd.reconstruct(G)).max())
         rec = dict(k=k, modes_o=st_o["modes"], modes_g=st_g["modes"], its_o=sum(st_o["als_iters"]),
-                   its_g=st_g["als_sweeps"], err_u=e_u)
+                   its_g=st_g["als_sweeps"], err_u=e_u, stalled_o=st_o["als_stalled"], stalled_g=st_g["als_stalled"],
+                   nc_o=st_o["als_not_converged"], nc_g=st_g["not_converged"])
         if energies:
             eo = octd.energy(prob, ops, A)
             eg = solver.energy()
@@ -109,6 +110,28 @@ def test_c0_first_steps_match_oracle(lib):
         assert r["its_g"] == r["its_o"], r
         assert r["err_u"] < TOL, r
         assert r["err_E"] < TOL, r
+
+
+def test_c0_all_steps_match_oracle(lib):
+    # the whole C0 run (100 steps): same modes and sweeps every step, field and energy 1e-12
+    w = workloads.preset("c0")
+    res = run_pair(lib, w, w.steps, energies=True)
+    for r in res:
+        assert r["modes_g"] == r["modes_o"] and r["its_g"] == r["its_o"], r
+        assert r["err_u"] < TOL and r["err_E"] < TOL, r
+
+
+@pytest.mark.parametrize("case", [dict(), dict(n=(77, 130), s=2, p=2, eps=0.04, M_max=12)])
+def test_stall_rule_matches_oracle(lib, case):
+    # a stall tolerance at which the rule fires in FP64 (the trailing mode of steps 2..4);
+    # the GPU makes the same decisions, counts the same stalled modes and flags the steps
+    w = workloads.preset("c0", **case)
+    res = run_pair(lib, w, 4, energies=True, als_stall_tol=1e-3)
+    assert sum(r["stalled_o"] for r in res) >= 2
+    for r in res:
+        assert r["modes_g"] == r["modes_o"] and r["its_g"] == r["its_o"], r
+        assert r["stalled_g"] == r["stalled_o"] and r["nc_g"] == r["nc_o"], r
+        assert r["err_u"] < TOL and r["err_E"] < TOL, r
 
 
 def test_ragged_2d_s2_matches_oracle(lib):
