@@ -97,9 +97,23 @@ typedef struct {
                                ctd_step_stats.als_stalled and the step returns
                                CTD_STATUS_ALS_NOT_CONVERGED.  0: off (tol_als or I_max only).
                                Same rule for every precision.                              */
+  int quad_rule;            /* rule shared by every mass-type integral (M_dd, the nonlinear
+                               term M_xy of Eq. KxxMxx, int F in the energy):
+                               CTD_QUAD_NODAL: trapezoid weights at the nodes, M_dd =
+                               diag(omega) (the default);
+                               CTD_QUAD_GAUSS: quad_q Gauss points per element (Section 3.3's
+                               Gauss points of each element), M_dd = Phi^T diag(omega_q) Phi,
+                               the exact consistent mass for quad_q >= 5, and w(u^k) evaluated
+                               at the tensor-product Gauss points and integrated against the
+                               shape functions.  Gauss: 1 <= quad_q <= 16, nonlinear_form GRID,
+                               reduced_tol 0 and sum over the other dimensions of
+                               quad_q (n[d] - 1) <= 12288 for every direction
+                               (CTD_ERR_UNSUPPORTED otherwise); ctd_step_batch refuses it.   */
+  int quad_q;               /* Gauss points per element (CTD_QUAD_GAUSS)                     */
 } ctd_config;
 
 enum { CTD_NONLINEAR_GRID = 0, CTD_NONLINEAR_SEPARATED = 1 };
+enum { CTD_QUAD_NODAL = 0, CTD_QUAD_GAUSS = 1 };
 
 typedef struct {
   int modes;                /* M of u^{k+1}                                                  */
@@ -154,7 +168,8 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
 
 /* Discrete energy of the current field, E_h = sum_grid omega F(u) + 1/2 kappa u^T K_grad u
  * (energy functional of Section 2.1 with F of Eq. energyfunction; F integrated with the
- * nodal rule, gradient with the exact stiffness).  FP64.  Synchronises. */
+ * configured rule -- at the nodes, or at the Gauss points with u^k evaluated there -- and
+ * the gradient with the exact stiffness and the rule's mass).  FP64.  Synchronises. */
 ctd_status ctd_energy(ctd_handle h, double* energy);
 
 /* Copy the current field's factors out: *rank receives M; if M <= capacity, factor d is
@@ -193,15 +208,16 @@ ctd_status ctd_probe_cfem(const ctd_config* cfg, int d, double* omega, double* k
  *                            bounds of a Chebyshev solve preconditioned by diag(M)): banded
  *                            Cholesky tests of M - lo diag(M) and hi diag(M) - M, widened by 1e-6.
  * Any output may be NULL; the caller owns every buffer.  CTD_ERR_ARG for an invalid
- * configuration, d or q, or a mass that is not positive definite.  Not yet used by
- * ctd_step, which takes the nodal rule. */
+ * configuration, d or q, or a mass that is not positive definite.  A handle created with
+ * quad_rule = CTD_QUAD_GAUSS uses the same operators in every step. */
 ctd_status ctd_probe_cfem_gauss(const ctd_config* cfg, int d, int q, double* x_q, double* omega_q, double* phi,
                                 int* phi_col0, double* mband, double* mass_bounds);
 
 /* Nonlinear contraction of Eq. KxxMxx for direction x with the current field as u^k:
- * out[i] = sum over the other indices of w(u^k) * prod_{d != x} (omega_d v_d), i.e.
- * M_xy u_y / (L omega_x[i]) under the nodal rule.  v[d] are host arrays of n[d] values
- * (v[x] ignored).  Uses cfg.precision.  The v[d] are copied into the handle's trial factors,
+ * nodal rule: out[i] = sum over the other indices of w(u^k) * prod_{d != x} (omega_d v_d),
+ * i.e. M_xy u_y / (L omega_x[i]); Gauss rule: out = M_xy u_y / L = Phi_x^T of the weighted
+ * sums of w(u^k) at the Gauss points against omega_q (Phi_d v_d) of the other dimensions.
+ * v[d] are host arrays of n[d] values (v[x] ignored).  Uses cfg.precision.  The v[d] are copied into the handle's trial factors,
  * which a probe may overwrite (every mode of the next ctd_step starts afresh, so its result
  * is unchanged). */
 ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, double* out);

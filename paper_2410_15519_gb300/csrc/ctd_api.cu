@@ -42,7 +42,7 @@ struct Carver {
 };
 
 struct Plan {
-  int D, n[3], b[3], n_pad[3], Mcap, Kpad, sep_q, grid, rchunks[3];
+  int D, n[3], nq[3], quad, b[3], n_pad[3], Mcap, Kpad, sep_q, grid, rchunks[3];
   long long N;
   size_t rpart_len, rpart32_len;
   ctd::TcDir dirs[3];
@@ -61,7 +61,7 @@ ctd::TcDir tc_dir(const Plan& p, int x, int G) {
     t.mid = x == 0 ? 1 : 0;
     t.last = x == 2 ? 1 : 2;
     t.n_last_pad = p.n_pad[t.last];
-    t.ncols_pad = p.n[t.mid] * t.n_last_pad;
+    t.ncols_pad = p.nq[t.mid] * t.n_last_pad;
   }
   t.ntc = t.ncols_pad / ctd::kTcN;
   const long long T = static_cast<long long>(t.nrb) * t.ntc;
@@ -77,18 +77,19 @@ ctd::TcDir tc_dir(const Plan& p, int x, int G) {
 
 int half_bandwidth(int s) { return 2 * s + 1; }
 
-int chunks_for(const ctd_config& c, int x, int grid) {
-  const int D = c.dim, nc = c.n[x];
+// Chunks of the FP64 contraction for direction x over a grid of nd[] points per dimension
+int chunks_for(int D, const int* nd, int x, int grid) {
+  const int nc = nd[x];
   const long long tw = static_cast<long long>(grid) * ctd::kWarps;
   long long C;
   if (x == D - 1) {
     long long rows = 1;
     for (int d = 0; d < D; ++d)
-      if (d != x) rows *= c.n[d];
+      if (d != x) rows *= nd[d];
     const long long cblocks = (nc + 31) / 32;
     C = std::min<long long>(rows, std::max<long long>(1, (4 * tw + cblocks - 1) / cblocks));
   } else {
-    const int extent = (D == 2) ? c.n[1] : (x == 0 ? c.n[1] : c.n[0]);
+    const int extent = (D == 2) ? nd[1] : (x == 0 ? nd[1] : nd[0]);
     C = std::min<long long>(extent, std::max<long long>(1, (4 * tw + nc - 1) / nc));
   }
   return static_cast<int>(C);
@@ -98,11 +99,14 @@ Plan make_plan(const ctd_config& c, int grid) {
   Plan p{};
   p.D = c.dim;
   p.N = 1;
+  p.quad = c.quad_rule == CTD_QUAD_GAUSS ? 1 : 0;
   for (int d = 0; d < c.dim; ++d) {
     p.n[d] = c.n[d];
+    // grid of the nonlinear term: the nodes, or q Gauss points per element
+    p.nq[d] = p.quad ? c.quad_q * (c.n[d] - 1) : c.n[d];
     p.b[d] = half_bandwidth(c.s);
-    p.n_pad[d] = (c.n[d] + ctd::kTileRows - 1) / ctd::kTileRows * ctd::kTileRows;
-    p.N *= c.n[d];
+    p.n_pad[d] = (p.nq[d] + ctd::kTileRows - 1) / ctd::kTileRows * ctd::kTileRows;
+    p.N *= p.nq[d];
   }
   p.Mcap = c.M_max;
   p.Kpad = (c.M_max + 63) / 64 * 64;
@@ -111,19 +115,20 @@ Plan make_plan(const ctd_config& c, int grid) {
   p.rpart_len = 0;
   p.rpart32_len = 0;
   for (int x = 0; x < c.dim; ++x) {
-    p.rchunks[x] = chunks_for(c, x, grid);
-    p.rpart_len = std::max(p.rpart_len, static_cast<size_t>(c.n[x]) * p.rchunks[x]);
+    p.rchunks[x] = chunks_for(c.dim, p.nq, x, grid);
+    p.rpart_len = std::max(p.rpart_len, static_cast<size_t>(p.nq[x]) * p.rchunks[x]);
   }
   for (int x = 0; x < c.dim; ++x) {
     p.dirs[x] = tc_dir(p, x, grid);
-    p.rpart32_len = std::max(p.rpart32_len, static_cast<size_t>(c.n[x]) * p.dirs[x].cmax);
+    p.rpart32_len = std::max(p.rpart32_len, static_cast<size_t>(p.nq[x]) * p.dirs[x].cmax);
   }
   return p;
 }
 
 // Lay out every workspace piece; fills P and X pointers when base != null.
 size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Extra* X,
-             float2** kc_store, double** energy_part, double** energy_gram, StepStatsDev** stats) {
+             float2** kc_store, float2** mc_store, double** energy_part, double** energy_gram,
+             StepStatsDev** stats) {
   Carver cv(base);
   StepParams p{};
   Extra x{};
@@ -147,6 +152,20 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
                 ? cv.take<__nv_bfloat16>(static_cast<size_t>(pl.n_pad[d]) * 2 * pl.Kpad) : nullptr;
     kc_store[d] = cv.take<float2>(static_cast<size_t>(n + 1) * w);
     x.Af[d] = cv.take<double>(static_cast<size_t>(pl.Mcap) * n);
+    dd.nq = pl.nq[d];
+    if (pl.quad) {
+      const int nq = pl.nq[d];
+      dd.wq = cv.take<double>(nq);
+      dd.phi = cv.take<float2>(static_cast<size_t>(nq) * ctd::kPhiW);
+      dd.phi0 = cv.take<int>(nq);
+      dd.mband = cv.take<double>(static_cast<size_t>(n) * w);
+      dd.MA = cv.take<float2>(static_cast<size_t>(pl.Mcap) * n);
+      dd.MB = cv.take<float2>(static_cast<size_t>(pl.Mcap) * n);
+      dd.Aq = cv.take<float2>(static_cast<size_t>(pl.Mcap) * nq);
+      mc_store[d] = cv.take<float2>(static_cast<size_t>(n + 1) * w);
+    } else {
+      mc_store[d] = nullptr;
+    }
   }
   int nmax = 0;
   for (int d = 0; d < D; ++d) nmax = std::max(nmax, pl.n[d]);
@@ -220,7 +239,49 @@ ctd_status validate(const ctd_config* c) {
   if (c->nonlinear_form != CTD_NONLINEAR_GRID && c->nonlinear_form != CTD_NONLINEAR_SEPARATED) return CTD_ERR_ARG;
   if (c->nonlinear_form == CTD_NONLINEAR_SEPARATED && (c->reduced_tol > 0.0 || c->M_max > ctd::kMaxSepModes))
     return CTD_ERR_ARG;
+  if (c->quad_rule != CTD_QUAD_NODAL && c->quad_rule != CTD_QUAD_GAUSS) return CTD_ERR_ARG;
+  if (c->quad_rule == CTD_QUAD_GAUSS) {
+    if (c->quad_q < 1 || c->quad_q > ctd::kMaxGaussPoints) return CTD_ERR_ARG;
+    if (c->nonlinear_form != CTD_NONLINEAR_GRID || c->reduced_tol > 0.0) return CTD_ERR_UNSUPPORTED;
+    // the FP64 contraction keeps the other dimensions' weights at their points in shared memory
+    for (int x = 0; x < c->dim; ++x) {
+      long long tot = 0;
+      for (int d = 0; d < c->dim; ++d)
+        if (d != x) tot += (static_cast<long long>(c->quad_q) * (c->n[d] - 1) + 1) & ~1LL;
+      if (tot > static_cast<long long>(ctd::kMaxDim) * ctd::kMaxN) return CTD_ERR_UNSUPPORTED;
+    }
+  }
   return CTD_OK;
+}
+
+// Compressed band (double-float): rows [0, lead) and [n - tail, n) explicit, the interior
+// rows [2s+1, n-2-2s] equal to one stencil when the mesh makes them identical (else every row
+// explicit).  Layout: (lead + tail) rows, then the stencil.
+std::vector<float2> compress_band(const std::vector<double>& band, int n, int s, int w, int* lead_out, int* tail_out) {
+  int lead = 2 * s + 1, tail = 2 * s + 1;
+  bool uniform = n > lead + tail;
+  if (uniform) {
+    const double* ref = &band[static_cast<size_t>(lead) * w];
+    for (int i = lead; i < n - tail && uniform; ++i)
+      for (int k = 0; k < w; ++k)
+        if (band[static_cast<size_t>(i) * w + k] != ref[k]) { uniform = false; break; }
+  }
+  if (!uniform) { lead = n; tail = 0; }
+  auto to_df = [](double v) {
+    const float hi = static_cast<float>(v);
+    return make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
+  };
+  std::vector<float2> kc(static_cast<size_t>(lead + tail + 1) * w);
+  for (int i = 0; i < lead; ++i)
+    for (int k = 0; k < w; ++k) kc[static_cast<size_t>(i) * w + k] = to_df(band[static_cast<size_t>(i) * w + k]);
+  for (int t = 0; t < tail; ++t)
+    for (int k = 0; k < w; ++k)
+      kc[static_cast<size_t>(lead + t) * w + k] = to_df(band[static_cast<size_t>(n - tail + t) * w + k]);
+  const int srow = uniform ? lead : 0;
+  for (int k = 0; k < w; ++k) kc[static_cast<size_t>(lead + tail) * w + k] = to_df(band[static_cast<size_t>(srow) * w + k]);
+  *lead_out = lead;
+  *tail_out = tail;
+  return kc;
 }
 
 }  // namespace
@@ -234,6 +295,9 @@ struct ctd_ctx {
   StepParams P;
   Extra X;
   float2* kc_store[3];
+  float2* mc_store[3];
+  std::vector<double> gphi[3];   // Gauss rule: shape function values at the points [nq][2s+2]
+  std::vector<int> gcol0[3];     // and their first nodes
   double* energy_part;
   double* energy_gram;
   StepStatsDev* stats_dev;
@@ -299,13 +363,14 @@ ctd_status ctd_workspace_size(const ctd_config* cfg, size_t* bytes) {
   if (v != CTD_OK) return v;
   if (!bytes) return CTD_ERR_ARG;
   float2* kc[3];
+  float2* mc[3];
   double *ep, *eg;
   StepStatsDev* sd;
   size_t best = 0;
   // every grid size 1..kGridMax fits (rpart32 depends on the split of tiles over CTAs)
   for (int g : {1, 2, 4, 8, 16, 32, 64, 128, 132, 144, 148, 152, 160, 256, kGridMax}) {
     const Plan pl = make_plan(*cfg, g);
-    best = std::max(best, carve(*cfg, pl, nullptr, nullptr, nullptr, kc, &ep, &eg, &sd));
+    best = std::max(best, carve(*cfg, pl, nullptr, nullptr, nullptr, kc, mc, &ep, &eg, &sd));
   }
   *bytes = best + static_cast<size_t>(2) * kGridMax * ctd::kMaxN * sizeof(float);
   return CTD_OK;
@@ -360,13 +425,16 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   grid = std::min(grid, sms);
   h->grid = grid;
   h->plan = make_plan(*cfg, grid);
-  carve(*cfg, h->plan, workspace, &h->P, &h->X, h->kc_store, &h->energy_part, &h->energy_gram, &h->stats_dev);
+  carve(*cfg, h->plan, workspace, &h->P, &h->X, h->kc_store, h->mc_store, &h->energy_part, &h->energy_gram,
+        &h->stats_dev);
   h->P.vgrid = grid;   // each CTA sets its own rank in its shared-memory copy
   h->P.vrank = 0;
 
   StepParams& P = h->P;
   Extra& X = h->X;
   P.dim = cfg->dim;
+  P.quad = h->plan.quad;
+  P.quad_q = h->plan.quad ? cfg->quad_q : 1;
   P.Mcap = h->plan.Mcap;
   P.Kpad = h->plan.Kpad;
   P.precision = cfg->precision;
@@ -431,30 +499,53 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
                                 sizeof(double) * n * w, cudaMemcpyHostToDevice, h->stream));
     // interior rows [2s+1, n-2-2s] share one stencil when the mesh is uniform
     const int s = cfg->s;
-    int lead = 2 * s + 1, tail = 2 * s + 1;
-    bool uniform = n > lead + tail;
-    if (uniform) {
-      const double* ref = &h->kband[d][static_cast<size_t>(lead) * w];
-      for (int i = lead; i < n - tail && uniform; ++i)
-        for (int k = 0; k < w; ++k)
-          if (h->kband[d][static_cast<size_t>(i) * w + k] != ref[k]) { uniform = false; break; }
-    }
-    if (!uniform) { lead = n; tail = 0; }
-    std::vector<float2> kc(static_cast<size_t>(lead + tail + 1) * w);
+    int lead = 0, tail = 0;
+    const std::vector<float2> kc = compress_band(h->kband[d], n, s, w, &lead, &tail);
+    CTD_CUDA(h, cudaMemcpyAsync(h->kc_store[d], kc.data(), sizeof(float2) * kc.size(), cudaMemcpyHostToDevice,
+                                h->stream));
     auto to_df = [](double v) {
       const float hi = static_cast<float>(v);
       return make_float2(hi, static_cast<float>(v - static_cast<double>(hi)));
     };
-    for (int i = 0; i < lead; ++i)
-      for (int k = 0; k < w; ++k) kc[static_cast<size_t>(i) * w + k] = to_df(h->kband[d][static_cast<size_t>(i) * w + k]);
-    for (int t = 0; t < tail; ++t)
-      for (int k = 0; k < w; ++k)
-        kc[static_cast<size_t>(lead + t) * w + k] = to_df(h->kband[d][static_cast<size_t>(n - tail + t) * w + k]);
-    const int srow = uniform ? lead : 0;
-    for (int k = 0; k < w; ++k) kc[static_cast<size_t>(lead + tail) * w + k] = to_df(h->kband[d][static_cast<size_t>(srow) * w + k]);
-    CTD_CUDA(h, cudaMemcpyAsync(h->kc_store[d], kc.data(), sizeof(float2) * kc.size(), cudaMemcpyHostToDevice,
-                                h->stream));
     ctd::KCompressed& k = X.kc[d];
+    k.mrows = nullptr;
+    k.mstencil = nullptr;
+    k.mlead = k.mtail = 0;
+    if (h->plan.quad) {
+      // Gauss rule: points, weights, shape function values and the consistent mass band
+      const int q = cfg->quad_q, nq = h->plan.nq[d], wphi = 2 * s + 2;
+      std::vector<double> xq(nq), wq(nq), phi(static_cast<size_t>(nq) * wphi), mb(static_cast<size_t>(n) * w);
+      std::vector<int> col0(nq);
+      if (ctd::build_cfem_gauss_1d(n, cfg->length[d], s, cfg->p, cfg->a, q, xq.data(), wq.data(), phi.data(),
+                                   col0.data(), mb.data(), nullptr) != 0) {
+        ctd_status st = fail(h, CTD_ERR_ARG, "Gauss-rule construction failed");
+        delete h;
+        return st;
+      }
+      std::vector<float2> phid(static_cast<size_t>(nq) * ctd::kPhiW, make_float2(0.f, 0.f));
+      for (int r = 0; r < nq; ++r)
+        for (int j = 0; j < wphi; ++j) phid[static_cast<size_t>(r) * ctd::kPhiW + j] = to_df(phi[static_cast<size_t>(r) * wphi + j]);
+      Dim& dd = P.d[d];
+      CTD_CUDA(h, cudaMemcpyAsync(const_cast<double*>(dd.wq), wq.data(), sizeof(double) * nq, cudaMemcpyHostToDevice,
+                                  h->stream));
+      CTD_CUDA(h, cudaMemcpyAsync(const_cast<float2*>(dd.phi), phid.data(), sizeof(float2) * phid.size(),
+                                  cudaMemcpyHostToDevice, h->stream));
+      CTD_CUDA(h, cudaMemcpyAsync(const_cast<int*>(dd.phi0), col0.data(), sizeof(int) * nq, cudaMemcpyHostToDevice,
+                                  h->stream));
+      CTD_CUDA(h, cudaMemcpyAsync(const_cast<double*>(dd.mband), mb.data(), sizeof(double) * mb.size(),
+                                  cudaMemcpyHostToDevice, h->stream));
+      int ml = 0, mt = 0;
+      const std::vector<float2> mc = compress_band(mb, n, s, w, &ml, &mt);
+      CTD_CUDA(h, cudaMemcpyAsync(h->mc_store[d], mc.data(), sizeof(float2) * mc.size(), cudaMemcpyHostToDevice,
+                                  h->stream));
+      CTD_CUDA(h, cudaStreamSynchronize(h->stream));   // the host vectors above are freed next
+      k.mlead = ml;
+      k.mtail = mt;
+      k.mrows = h->mc_store[d];
+      k.mstencil = h->mc_store[d] + static_cast<size_t>(ml + mt) * w;
+      h->gphi[d] = phi;
+      h->gcol0[d] = col0;
+    }
     k.n = n;
     k.b = b;
     k.nlead = lead;
@@ -492,7 +583,10 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
       if (!ctd::cheb_layout(cfg->n[d], X.kc[d].nlead, X.kc[d].ntail, X.kc[d].b, ctd::kThreads - 32, lay))
         cheb_split = false;
     }
-    if (cheb_split && worst_its <= 200 && fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
+    // the Chebyshev split is built around the nodal rule's diagonal mass; the Gauss rule's
+    // consistent mass takes block cyclic reduction
+    if (!h->plan.quad && cheb_split && worst_its <= 200 &&
+        fixed + ctd::step_arena_bytes(n_max, chf, 3) + margin <= static_cast<size_t>(optin))
       P.solver_mode = 3;
     else if (fixed + ctd::step_arena_bytes(n_max, crf, 0) + margin <= static_cast<size_t>(optin)) P.solver_mode = 0;
     else if (fixed + ctd::step_arena_bytes(n_max, l0f, 1) + margin <= static_cast<size_t>(optin)) P.solver_mode = 1;
@@ -507,7 +601,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
         for (int x = 0; x < cfg->dim; ++x) {
           const ctd::TcDir& td = h->plan.dirs[x];
           const int wl = td.mid < 0 ? td.ncols_pad : td.n_last_pad;
-          const int wm = td.mid < 0 ? 0 : cfg->n[td.mid];
+          const int wm = td.mid < 0 ? 0 : h->plan.nq[td.mid];
           tcb = std::max(tcb, ctd::tc_layout(chunks, stages, wl, wm).total);
         }
         if (fixed + 1024 + tcb + 1024 <= static_cast<size_t>(optin)) {
@@ -637,6 +731,7 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
     if (h->device != dev) return fail(h, CTD_ERR_STATE, "instance on another device");
     if (h->P.nl_form != CTD_NONLINEAR_GRID)
       return fail(h, CTD_ERR_UNSUPPORTED, "batched steps integrate the nonlinear term over the grid only");
+    if (h->P.quad) return fail(h, CTD_ERR_UNSUPPORTED, "batched steps take the nodal rule only");
   }
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   // one entry per instance; the largest instances start first
@@ -786,33 +881,46 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
   // partial slots of CTAs without a tile in a row block are not written: start from zero
   CTD_CUDA(h, cudaMemsetAsync(h->X.rpart32, 0, sizeof(float) * std::max<size_t>(1, h->plan.rpart32_len), h->stream));
   CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, nullptr, h->stream));
-  const int n = h->cfg.n[x];
+  const int n = h->cfg.n[x], nq = h->plan.nq[x];
+  std::vector<double> rq(nq);   // weighted sums at the points of direction x (the nodes, nodal rule)
   if (h->cfg.precision == CTD_PREC_FP64) {
     const int C = h->plan.rchunks[x];
-    std::vector<double> part(static_cast<size_t>(n) * C);
+    std::vector<double> part(static_cast<size_t>(nq) * C);
     CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->P.rpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
                                 h->stream));
     CTD_CUDA(h, cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < nq; ++i) {
       double r = 0.0;
       for (int k = 0; k < C; ++k) r += part[static_cast<size_t>(i) * C + k];
-      out[i] = r;
+      rq[i] = r;
     }
   } else {
     const ctd::TcDir& td = h->plan.dirs[x];
-    std::vector<float> part(static_cast<size_t>(n) * td.cmax);
+    std::vector<float> part(static_cast<size_t>(nq) * td.cmax);
     CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->X.rpart32, sizeof(float) * part.size(), cudaMemcpyDeviceToHost,
                                 h->stream));
     CTD_CUDA(h, cudaStreamSynchronize(h->stream));
     const long long T = static_cast<long long>(td.nrb) * td.ntc;
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < nq; ++i) {
       const int rb = i / ctd::kTcM;
       const int c0 = ctd::tile_owner(T, h->grid, static_cast<long long>(rb) * td.ntc);
       const int c1 = ctd::tile_owner(T, h->grid, static_cast<long long>(rb) * td.ntc + td.ntc - 1);
       double r = 0.0;
       for (int k = 0; k <= c1 - c0; ++k) r += part[static_cast<size_t>(i) * td.cmax + k];
-      out[i] = r / (4.0 * h->cfg.a0);
+      rq[i] = r;
     }
+  }
+  if (h->plan.quad) {
+    // Gauss rule: Phi_x^T of the point sums
+    const int wphi = 2 * h->cfg.s + 2;
+    for (int i = 0; i < n; ++i) out[i] = 0.0;
+    for (int r = 0; r < nq; ++r)
+      for (int k = 0; k < wphi; ++k) {
+        const int i = h->gcol0[x][r] + k;
+        if (i < n) out[i] += h->gphi[x][static_cast<size_t>(r) * wphi + k] * rq[r];
+      }
+  } else {
+    for (int i = 0; i < n; ++i) out[i] = rq[i];
   }
   InstState st;
   ctd_status rs = read_state(h, &st);

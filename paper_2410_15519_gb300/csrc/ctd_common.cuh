@@ -18,6 +18,7 @@ constexpr int kMaxSepModes = 16;
 constexpr int kMaxSep = kMaxSepModes * (kMaxSepModes + 1) * (kMaxSepModes + 2) / 6;
 __host__ __device__ constexpr int sep_terms(int Mk) { return Mk * (Mk + 1) * (Mk + 2) / 6; }
 constexpr int kTileRows = 128;         // tensor-core tile rows (operand rows padded to this)
+constexpr int kPhiW = 8;               // shape functions nonzero on one element: 2s + 2 <= 8
 
 // status bits written by the kernels (host maps them to ctd_status)
 constexpr int kErrTimeout = 1;
@@ -36,6 +37,17 @@ struct Dim {
   float2* vold;            // [n] trial factor at the start of the sweep
   __nv_bfloat16* op;       // [n_pad][2*Kpad] tensor-core operand: hi | lo split of u^k
   float mu_max;            // Gershgorin bound of the generalised eigenvalues of (K, diag(omega))
+  // Quadrature points of the mass-type integrals: the nodes (nodal rule, nq = n) or q Gauss
+  // points per element (Gauss rule, nq = q (n - 1)); the grid of the nonlinear term is the
+  // tensor product of the points.  Gauss rule only (null otherwise):
+  int nq;                  // points
+  const double* wq;        // [nq] weights
+  const float2* phi;       // [nq][kPhiW] shape function values N~_{phi0[r]+k}(x_r) (double-float)
+  const int* phi0;         // [nq] first node of each point's shape function row
+  const double* mband;     // [n][2b+1] consistent mass band (FP64)
+  float2* MA;              // [Mcap][n] M a of u^k's factors (double-float)
+  float2* MB;              // [Mcap][n] M b of u^{k+1}'s committed factors (double-float)
+  float2* Aq;              // [Mcap][nq] Phi a: u^k's factors at the points (double-float)
 };
 
 struct InstState {
@@ -62,6 +74,8 @@ struct StepParams {
   int Mcap;                // columns per bank
   int Kpad;                // padded mode count of the tensor-core operands (multiple of 64)
   int precision;           // 0 FP64, 1 split BF16 tensor cores
+  int quad;                // 0 nodal rule (M = diag(omega)), 1 Gauss rule (consistent mass)
+  int quad_q;              // Gauss points per element
   double c_t, c_k, L, a0;
   float2 ct_df, ck_df, L_df;   // the same constants as double-float (converted on the host)
   double tol_als, tol_enrich;

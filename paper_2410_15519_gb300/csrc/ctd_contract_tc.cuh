@@ -250,8 +250,12 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
     *reinterpret_cast<uint4*>(op + o + kTcImgElems) = *reinterpret_cast<const uint4*>(lo);
   };
   if (ksteps == 0) return;
+  // rows: the nodes (nodal rule, factors) or the Gauss points (Gauss rule, factors there)
+  auto src_of = [&](const Dim& dd) { return P.quad ? dd.Aq : dd.bank[pb]; };
   for (int d = 0; d < P.dim; ++d) {
     const Dim& dd = P.d[d];
+    const float2* src = src_of(dd);
+    const int rows = dd.nq;
     const long long total = static_cast<long long>(dd.n_pad) * ksteps * 2;
     for (long long u = t0; u < total; u += stride) {
       long long i;
@@ -262,8 +266,8 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
       for (int e = 0; e < 8; ++e) {
         const int k = k0 + e;
         a[e] = 0.f;
-        if (i < dd.n && k < Mk) {
-          const float2 v = dd.bank[pb][static_cast<size_t>(k) * dd.n + i];
+        if (i < rows && k < Mk) {
+          const float2 v = src[static_cast<size_t>(k) * rows + i];
           a[e] = v.x + v.y;
         }
       }
@@ -281,14 +285,16 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
       int k0;
       unit(u, row, k0);
       const int j = static_cast<int>(row / td.n_last_pad), l = static_cast<int>(row - static_cast<long long>(j) * td.n_last_pad);
+      const float2* sm = src_of(dm);
+      const float2* sl = src_of(dl);
       float a[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int k = k0 + e;
         a[e] = 0.f;
-        if (j < dm.n && l < dl.n && k < Mk) {
-          const float2 vm = dm.bank[pb][static_cast<size_t>(k) * dm.n + j];
-          const float2 vl = dl.bank[pb][static_cast<size_t>(k) * dl.n + l];
+        if (j < dm.nq && l < dl.nq && k < Mk) {
+          const float2 vm = sm[static_cast<size_t>(k) * dm.nq + j];
+          const float2 vl = sl[static_cast<size_t>(k) * dl.nq + l];
           a[e] = (vm.x + vm.y) * (vl.x + vl.y);
         }
       }
@@ -298,12 +304,29 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
 }
 
 // FP32 column weights 4 a0 omega_d v_d of dimension d into shared memory (zero padded),
-// entries [lo, hi) of [0, npad).
+// entries [lo, hi) of [0, npad); under the Gauss rule 4 a0 omega_q (Phi_d v_d) at the points.
 __device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, int d, float* w, int npad,
                                   int lo, int hi, int tid, int nthr) {
   const Dim& dd = P.d[d];
   const float s = static_cast<float>(4.0 * P.a0);
   if (hi > npad) hi = npad;
+  if (P.quad) {
+    for (int r = lo + tid; r < hi; r += nthr) {
+      float v = 0.f;
+      if (r < dd.nq) {
+        float acc = 0.f;
+        const int j0 = dd.phi0[r];
+        for (int k = 0; k <= dd.b; ++k)
+          if (j0 + k < dd.n) {
+            const float2 ph = dd.phi[static_cast<size_t>(r) * kPhiW + k], vv = dd.v[j0 + k];
+            acc = __fmaf_rn(ph.x + ph.y, vv.x + vv.y, acc);
+          }
+        v = s * static_cast<float>(dd.wq[r]) * acc;
+      }
+      w[r] = v;
+    }
+    return;
+  }
   constexpr int kGroup = 8;   // loads of eight entries first, so that their latencies overlap
   for (int i0 = lo + tid; i0 < hi; i0 += kGroup * nthr) {
     float2 x[kGroup];
@@ -352,7 +375,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   // Parameters the role loops use, in registers: P and td live in shared memory, and every
   // asm statement below (waits, MMAs, commits) is a memory clobber that would reload them.
   const int ntc = td.ntc, nrb = td.nrb, tmid = td.mid, cmax = td.cmax, n_last_pad = td.n_last_pad;
-  const int ncols_pad = td.ncols_pad, nx = P.d[x].n;
+  const int ncols_pad = td.ncols_pad, nx = P.d[x].nq;
   InstState* const st = P.st;
   auto active = [=](int t) -> bool {
     if (!tile_max) return true;
@@ -367,7 +390,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   const uint32_t load_bytes = 2u * ksteps * kTcImgBytes;
   const size_t block_elems = static_cast<size_t>(P.Kpad / 16) * 2 * kTcImgElems;
   const int wl_n = tmid < 0 ? ncols_pad : n_last_pad;
-  const int wm_n = tmid < 0 ? 0 : P.d[tmid].n;
+  const int wm_n = tmid < 0 ? 0 : P.d[tmid].nq;
   const TcLayout Ly = tc_layout(chunks, stages, wl_n, wm_n);
   TcShared* sh = reinterpret_cast<TcShared*>(base + Ly.shared_off);
   unsigned char* As = base + Ly.a_off;

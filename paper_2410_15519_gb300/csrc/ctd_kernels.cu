@@ -190,6 +190,18 @@ CTD_LOCAL __device__ __noinline__ void convergence_partials(const StepParams& P,
   }
 }
 
+// Gauss rule, tensor-core path: the point rows' tile partials are read by several nodes'
+// right-hand sides, so they are cleared after the right-hand sides (during the solve, by the
+// CTAs that do not solve), not as they are read.
+CTD_LOCAL __device__ __noinline__ void clear_point_partials(const StepParams& P, const Extra& X, int x) {
+  const int parts = P.vgrid > 1 ? P.vgrid - 1 : 1, me = P.vgrid > 1 ? P.vrank - 1 : 0;
+  if (me < 0) return;
+  const size_t total = static_cast<size_t>(P.d[x].nq) * X.dirs[x].cmax;
+  int lo, hi;
+  slice_of(static_cast<int>(total), parts, me, lo, hi);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) X.rpart32[i] = 0.f;
+}
+
 // Save the current trial factors (own slices) at the start of a sweep.
 CTD_LOCAL __device__ __noinline__ void save_old(const StepParams& P) {
   for (int d = 0; d < P.dim; ++d) {
@@ -211,6 +223,7 @@ CTD_LOCAL __device__ __noinline__ void commit_mode(const StepParams& P, const Ex
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
       st_df(dd.bank[cb] + static_cast<size_t>(M) * dd.n + i, df_mul(ld_df(dd.v + i), sc));
       st_df(dd.KB + static_cast<size_t>(M) * dd.n + i, df_mul(kv_row(X.kc[d], dd.v, i), sc));
+      if (P.quad) st_df(dd.MB + static_cast<size_t>(M) * dd.n + i, df_mul(mv_row(X.kc[d], dd.v, i), sc));
     }
   }
 }
@@ -275,15 +288,21 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
   if constexpr (kSepTU) {
   } else if (P.precision == 0) {
     convert_prev_modes(P, X, pb, Mk);
+    if (P.quad) gauss_prologue(P, X, pb, Mk);
     if (!sync_all(P, epoch, 1)) return;
-    materialise_w(P, X, Mk);
+    if (P.quad) materialise_w_gauss(P, Mk);
+    else materialise_w(P, X, Mk);
   } else {
+    if (P.quad) {
+      gauss_prologue(P, X, pb, Mk);
+      if (!sync_all(P, epoch, 1)) return;
+    }
     tc_prepare(P, X.dirs, X.kr, pb, Mk);
     fence_proxy_async_global();
     // contraction partial slots start the step at zero (see rhs_rows)
     size_t nslot = 0;
     for (int d = 0; d < D; ++d) {
-      const size_t v = static_cast<size_t>(P.d[d].n) * X.dirs[d].cmax;
+      const size_t v = static_cast<size_t>(P.d[d].nq) * X.dirs[d].cmax;
       nslot = v > nslot ? v : nslot;
     }
     for (size_t i = static_cast<size_t>(P.vrank) * blockDim.x + threadIdx.x; i < nslot;
@@ -331,8 +350,14 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
         const unsigned long long tcon = tr_last ? global_ns() : 0ull;
         if constexpr (kSepTU) {
         } else if (P.precision == 0) {
-          load_weights_fp64(P, X, x, ar.wv);
-          contract_fp64(P, x, ar.wv);
+          GridW g;
+          if (P.quad) {
+            g = load_weights_gauss(P, x, ar.wv);
+          } else {
+            load_weights_fp64(P, X, x, ar.wv);
+            g = nodal_grid(P, ar.wv);
+          }
+          contract_fp64(P, x, g);
         } else {
           const TcDir& td = X.dirs[x];
           const __nv_bfloat16* qop = (D == 2) ? P.d[td.last].op : X.kr[x];
@@ -357,6 +382,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
           tau0 = fminf(fmaxf(static_cast<float>(kSolveTolMixed / (4.0 * fmax(delta, 1e-30))), kFirstPassTau),
                        3.90625e-3f);
         if (P.vrank == 0) solve_direction(P, X, x, sm, ar, it > 1, tau0);
+        if (!kSepTU && P.quad && P.precision != 0) clear_point_partials(P, X, x);
         if (!sync_all(P, epoch, 5)) return;
         trace_mark(P, tmark, kTrSolve);
         const int zflag = *reinterpret_cast<volatile int*>(X.ctrl + 0);
@@ -553,13 +579,25 @@ __global__ void __launch_bounds__(kThreads, 1) batch_step_kernel(const BatchEntr
 __global__ void __launch_bounds__(kThreads) energy_bulk_kernel(const StepParams P, const Extra X, int Mk,
                                                                double* part) {
   const int D = P.dim;
-  const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
+  const int n0 = P.d[0].nq, n1 = P.d[1].nq, n2 = D == 3 ? P.d[2].nq : 1;
   const long long N = static_cast<long long>(n0) * n1 * n2;
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   double acc = 0.0;
   for (long long p = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; p < N; p += stride) {
     double u = 0.0, w;
-    if (D == 2) {
+    if (P.quad) {
+      // Gauss rule: u^k at the Gauss points from the factors there, weights omega_q
+      const int l = static_cast<int>(p % n2);
+      const long long ij = p / n2;
+      const int j = static_cast<int>(ij % n1), i = static_cast<int>(ij / n1);
+      for (int m = 0; m < Mk; ++m) {
+        double t = f2_to_double(P.d[0].Aq[static_cast<size_t>(m) * n0 + i]) *
+                   f2_to_double(P.d[1].Aq[static_cast<size_t>(m) * n1 + j]);
+        if (D == 3) t *= f2_to_double(P.d[2].Aq[static_cast<size_t>(m) * n2 + l]);
+        u += t;
+      }
+      w = P.d[0].wq[i] * P.d[1].wq[j] * (D == 3 ? P.d[2].wq[l] : 1.0);
+    } else if (D == 2) {
       const int i = static_cast<int>(p / n1), j = static_cast<int>(p - static_cast<long long>(i) * n1);
       for (int m = 0; m < Mk; ++m)
         u = fma(X.Af[0][static_cast<size_t>(m) * n0 + i], X.Af[1][static_cast<size_t>(m) * n1 + j], u);
@@ -587,6 +625,20 @@ __global__ void __launch_bounds__(kThreads) energy_bulk_kernel(const StepParams 
   }
 }
 
+// Gauss rule: the current factors at the Gauss points (whole arrays, double-float)
+__global__ void gauss_points_kernel(const StepParams P, int bank, int Mk) {
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    const long long total = static_cast<long long>(Mk) * dd.nq;
+    for (long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += static_cast<long long>(gridDim.x) * blockDim.x) {
+      const int m = static_cast<int>(t / dd.nq), r = static_cast<int>(t - static_cast<long long>(m) * dd.nq);
+      const dfloat v = phi_row(dd, dd.b + 1, dd.bank[bank] + static_cast<size_t>(m) * dd.n, r);
+      dd.Aq[t] = make_float2(v.hi, v.lo);
+    }
+  }
+}
+
 // FP64 copies of the current factors (whole arrays)
 __global__ void convert_modes_kernel(const StepParams P, const Extra X, int bank, int Mk) {
   for (int d = 0; d < P.dim; ++d) {
@@ -609,7 +661,14 @@ __global__ void energy_gram_kernel(const StepParams P, const Extra X, int Mk, do
   double sm = 0.0, sk = 0.0;
   const int w = 2 * dd.b + 1;
   for (int i = threadIdx.x; i < dd.n; i += blockDim.x) {
-    sm = fma(a[i] * dd.omega[i], c[i], sm);
+    if (dd.mband) {   // Gauss rule: consistent mass band
+      double mc = 0.0;
+      for (int j = max(0, i - dd.b); j <= min(dd.n - 1, i + dd.b); ++j)
+        mc = fma(dd.mband[static_cast<size_t>(i) * w + (j - i + dd.b)], c[j], mc);
+      sm = fma(a[i], mc, sm);
+    } else {
+      sm = fma(a[i] * dd.omega[i], c[i], sm);
+    }
     double kc = 0.0;
     for (int j = max(0, i - dd.b); j <= min(dd.n - 1, i + dd.b); ++j)
       kc = fma(dd.kband[static_cast<size_t>(i) * w + (j - i + dd.b)], c[j], kc);
@@ -637,12 +696,24 @@ __device__ void probe_contract_body(const StepParams& P, const Extra& X, int x, 
   const InstState st0 = *P.st;
   if (P.precision == 0) {
     convert_prev_modes(P, X, st0.bank, st0.Mk);
+    if (P.quad) gauss_prologue(P, X, st0.bank, st0.Mk);
     if (!sync_all(P, epoch, 11)) return;
-    materialise_w(P, X, st0.Mk);
+    if (P.quad) materialise_w_gauss(P, st0.Mk);
+    else materialise_w(P, X, st0.Mk);
     if (!sync_all(P, epoch, 12)) return;
-    load_weights_fp64(P, X, x, ar.wv);
-    contract_fp64(P, x, ar.wv);
+    GridW g;
+    if (P.quad) {
+      g = load_weights_gauss(P, x, ar.wv);
+    } else {
+      load_weights_fp64(P, X, x, ar.wv);
+      g = nodal_grid(P, ar.wv);
+    }
+    contract_fp64(P, x, g);
   } else {
+    if (P.quad) {
+      gauss_prologue(P, X, st0.bank, st0.Mk);
+      if (!sync_all(P, epoch, 13)) return;
+    }
     tc_prepare(P, X.dirs, X.kr, st0.bank, st0.Mk);
     fence_proxy_async_global();
     if (!sync_all(P, epoch, 11)) return;
@@ -764,6 +835,7 @@ cudaError_t launch_probe_solve(const StepParams& P, const Extra& X, int x, doubl
 
 cudaError_t launch_convert_modes(const StepParams& P, const Extra& X, int bank, int Mk, cudaStream_t s) {
   convert_modes_kernel<<<256, kThreads, 0, s>>>(P, X, bank, Mk);
+  if (P.quad && Mk > 0) gauss_points_kernel<<<256, kThreads, 0, s>>>(P, bank, Mk);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,11 @@ struct KCompressed {
   const float2* stencil;   // [2b+1]
   float2 omega_in, omega_end;   // nodal weights inside / at the two ends
   float inv_omega_in, inv_omega_end;
+  // Consistent mass of the Gauss rule in the same compressed form (null: the nodal rule's
+  // diagonal mass diag(omega))
+  int mlead, mtail;
+  const float2* mrows;
+  const float2* mstencil;
 };
 __device__ __forceinline__ float kc_inv_omega(const KCompressed& k, int i) {
   return (i == 0 || i == k.n - 1) ? k.inv_omega_end : k.inv_omega_in;
@@ -35,6 +40,14 @@ __device__ __forceinline__ float2 kc_entry(const KCompressed& k, int i, int off 
 }
 __device__ __forceinline__ float2 kc_omega(const KCompressed& k, int i) {
   return (i == 0 || i == k.n - 1) ? k.omega_end : k.omega_in;
+}
+// Mass entry M[i][i + off]: the consistent band (Gauss rule) or diag(omega) (nodal rule)
+__device__ __forceinline__ float2 kc_mass(const KCompressed& k, int i, int off /* -b..b */) {
+  if (!k.mrows) return off == 0 ? kc_omega(k, i) : make_float2(0.f, 0.f);
+  const int w = 2 * k.b + 1;
+  if (i < k.mlead) return k.mrows[i * w + off + k.b];
+  if (i >= k.n - k.mtail) return k.mrows[(k.mlead + i - (k.n - k.mtail)) * w + off + k.b];
+  return k.mstencil[off + k.b];
 }
 
 struct CRBuffers {
@@ -125,16 +138,21 @@ __device__ inline void cr_build(const CRBuffers& s, const KCompressed& k, float 
     const int I = t / bsz, e = t - I * bsz, r = e / b, c = e - r * b;
     const int row = I * b + r, col = I * b + c;
     float dv;
-    if (row < n && col < n) {
+    if (row < n && col < n && (row - col <= b && col - row <= b)) {
       dv = a2 * kc_entry(k, row, col - row).x;
-      if (row == col) dv += a1 * kc_omega(k, row).x;
+      if (k.mrows) dv += a1 * kc_mass(k, row, col - row).x;
+      else if (row == col) dv += a1 * kc_omega(k, row).x;
     } else {
       dv = (r == c) ? 1.f : 0.f;
+      if (row < n && col < n) dv = 0.f;
     }
     s.D[t] = dv;
     const int row2 = row + b;
     float ev = 0.f;
-    if (I + 1 < s.nb && row2 < n && col < n && row2 - col <= b) ev = a2 * kc_entry(k, row2, col - row2).x;
+    if (I + 1 < s.nb && row2 < n && col < n && row2 - col <= b) {
+      ev = a2 * kc_entry(k, row2, col - row2).x;
+      if (k.mrows) ev += a1 * kc_mass(k, row2, col - row2).x;
+    }
     s.E[t] = ev;
   }
 }
@@ -390,7 +408,8 @@ __device__ __forceinline__ void band_diag_block(const KCompressed& k, int I, flo
       float v;
       if (row < k.n && col < k.n) {
         v = a2 * kc_entry(k, row, col - row).x;
-        if (r == c) v += a1 * kc_omega(k, row).x;
+        if (k.mrows) v += a1 * kc_mass(k, row, col - row).x;
+        else if (r == c) v += a1 * kc_omega(k, row).x;
       } else {
         v = (r == c) ? 1.f : 0.f;
       }
@@ -399,14 +418,18 @@ __device__ __forceinline__ void band_diag_block(const KCompressed& k, int I, flo
 }
 // E_I: rows of block I+1, columns of block I (zero past the end)
 template <int B>
-__device__ __forceinline__ void band_coupling_block(const KCompressed& k, int I, int nb, float a2, float (&e)[B * B]) {
+__device__ __forceinline__ void band_coupling_block(const KCompressed& k, int I, int nb, float a1, float a2,
+                                                    float (&e)[B * B]) {
 #pragma unroll
   for (int r = 0; r < B; ++r)
 #pragma unroll
     for (int c = 0; c < B; ++c) {
       const int row = (I + 1) * B + r, col = I * B + c;
       float v = 0.f;
-      if (I + 1 < nb && row < k.n && col < k.n && row - col <= B) v = a2 * kc_entry(k, row, col - row).x;
+      if (I + 1 < nb && row < k.n && col < k.n && row - col <= B) {
+        v = a2 * kc_entry(k, row, col - row).x;
+        if (k.mrows) v += a1 * kc_mass(k, row, col - row).x;
+      }
       e[r * B + c] = v;
     }
 }
@@ -425,7 +448,7 @@ __device__ inline bool l0_factor_t(const L0Buffers& s, const KCompressed& k, flo
       float L[BB], e[BB];
       band_diag_block<B>(k, i - 1, a1, a2, L);
       blk_chol<B>(L);
-      band_coupling_block<B>(k, i - 1, nb, a2, e);
+      band_coupling_block<B>(k, i - 1, nb, a1, a2, e);
 #pragma unroll
       for (int c = 0; c < B; ++c) {
         float x[B];
@@ -442,7 +465,7 @@ __device__ inline bool l0_factor_t(const L0Buffers& s, const KCompressed& k, flo
       float L[BB], e[BB], e3[BB], g[BB];
       band_diag_block<B>(k, i + 1, a1, a2, L);
       blk_chol<B>(L);
-      band_coupling_block<B>(k, i, nb, a2, e);
+      band_coupling_block<B>(k, i, nb, a1, a2, e);
 #pragma unroll
       for (int c = 0; c < B; ++c) {
         float x[B];
@@ -462,7 +485,7 @@ __device__ inline bool l0_factor_t(const L0Buffers& s, const KCompressed& k, flo
           d[r * B + c] = acc;
         }
       if (i + 2 < nb) {
-        band_coupling_block<B>(k, i + 1, nb, a2, e3);
+        band_coupling_block<B>(k, i + 1, nb, a1, a2, e3);
 #pragma unroll
         for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -505,7 +528,7 @@ __device__ inline void l0_solve_t(const L0Buffers& s, const KCompressed& k, floa
     for (int r = 0; r < B; ++r) f[r] = s.F[i * B + r];
     if (i >= 1) {                                                    // - E_{i-1} y_{i-1}
       float e[BB];
-      band_coupling_block<B>(k, i - 1, nb, a2, e);
+      band_coupling_block<B>(k, i - 1, nb, a1, a2, e);
 #pragma unroll
       for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -513,7 +536,7 @@ __device__ inline void l0_solve_t(const L0Buffers& s, const KCompressed& k, floa
     }
     if (i + 1 < nb) {                                                // - E_i^T y_{i+1}
       float e[BB];
-      band_coupling_block<B>(k, i, nb, a2, e);
+      band_coupling_block<B>(k, i, nb, a1, a2, e);
 #pragma unroll
       for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -534,13 +557,13 @@ __device__ inline void l0_solve_t(const L0Buffers& s, const KCompressed& k, floa
     float t[B], e[BB], L[BB];
 #pragma unroll
     for (int r = 0; r < B; ++r) t[r] = 0.f;
-    band_coupling_block<B>(k, j - 1, nb, a2, e);                      // E_{j-1} x_{j-1}
+    band_coupling_block<B>(k, j - 1, nb, a1, a2, e);                      // E_{j-1} x_{j-1}
 #pragma unroll
     for (int r = 0; r < B; ++r)
 #pragma unroll
       for (int l = 0; l < B; ++l) t[r] += e[r * B + l] * s.X[(j - 1) * B + l];
     if (j + 1 < nb) {                                                 // E_j^T x_{j+1}
-      band_coupling_block<B>(k, j, nb, a2, e);
+      band_coupling_block<B>(k, j, nb, a1, a2, e);
 #pragma unroll
       for (int r = 0; r < B; ++r)
 #pragma unroll
@@ -1230,9 +1253,21 @@ __device__ inline void residual_df_t(const KCompressed& kref, dfloat a1, dfloat 
         kx = df_add(kx, df_mul(dfloat{kij.x, kij.y}, dfloat{xj.x, xj.y}));
       }
     }
-    const float2 om = kc_omega(k, i);
-    const float2 xi = x[i];
-    const dfloat ax = df_add(df_mul(a2, kx), df_mul(a1, df_mul(dfloat{om.x, om.y}, dfloat{xi.x, xi.y})));
+    dfloat mx;
+    if (k.mrows) {   // consistent mass (Gauss rule): band product
+      mx = {0.f, 0.f};
+      const int j0 = max(0, i - B), j1 = min(n - 1, i + B);
+      for (int j = j0; j <= j1; ++j) {
+        const float2 mij = kc_mass(k, i, j - i);
+        const float2 xj = x[j];
+        mx = df_add(mx, df_mul(dfloat{mij.x, mij.y}, dfloat{xj.x, xj.y}));
+      }
+    } else {
+      const float2 om = kc_omega(k, i);
+      const float2 xi = x[i];
+      mx = df_mul(dfloat{om.x, om.y}, dfloat{xi.x, xi.y});
+    }
+    const dfloat ax = df_add(df_mul(a2, kx), df_mul(a1, mx));
     const dfloat rr = df_add(dfloat{q[i].x, q[i].y}, df_neg(ax));
     out[i] = rr.hi + rr.lo;
   }

@@ -81,6 +81,42 @@ __device__ inline dfloat kv_row(const KCompressed& k, const float2* v, int i) {
   return acc;
 }
 
+// M v at row i of dimension d (double-float): the consistent mass band of the Gauss rule, or
+// omega_i v_i under the nodal rule
+__device__ inline dfloat mv_row(const KCompressed& k, const float2* v, int i) {
+  if (!k.mrows) {
+    const float2 om = kc_omega(k, i);
+    return df_mul(dfloat{om.x, om.y}, ld_df(v + i));
+  }
+  constexpr int kW = 2 * 7 + 1;   // widest band (s = 3)
+  float2 mv[kW], vv[kW];
+#pragma unroll
+  for (int o = 0; o < kW; ++o) {   // all loads first, so that their latencies overlap
+    const int j = i + o - k.b;
+    const bool ok = o <= 2 * k.b && j >= 0 && j < k.n;
+    mv[o] = ok ? kc_mass(k, i, o - k.b) : make_float2(0.f, 0.f);
+    vv[o] = ok ? v[j] : make_float2(0.f, 0.f);
+  }
+  dfloat acc = {0.f, 0.f};
+#pragma unroll
+  for (int o = 0; o < kW; ++o)
+    if (o <= 2 * k.b) acc = df_fma(acc, dfloat{mv[o].x, mv[o].y}, dfloat{vv[o].x, vv[o].y});
+  return acc;
+}
+
+// Value at Gauss point r of dimension d of the 1D function with nodal coefficients f
+// (double-float): sum_k N~_{phi0[r]+k}(x_r) f[phi0[r]+k] (Gauss rule)
+__device__ inline dfloat phi_row(const Dim& dd, int phiw, const float2* f, int r) {
+  const int j0 = dd.phi0[r];
+  const float2* ph = dd.phi + static_cast<size_t>(r) * kPhiW;
+  dfloat acc = {0.f, 0.f};
+  for (int k = 0; k < phiw; ++k) {
+    const int j = j0 + k;
+    if (j < dd.n) acc = df_fma(acc, ld_df(ph + k), ld_df(f + j));
+  }
+  return acc;
+}
+
 // Reduce a double-float value over the `tp` consecutive lanes of a group (tp power of 2 <=
 // 32), fixed xor tree.
 __device__ inline dfloat group_sum(dfloat v, int tp) {
@@ -141,7 +177,7 @@ static __device__ __noinline__ void gram_partials(const StepParams& P, const Ext
         const dfloat v = ld_df(dd.v + i);
         const float2 om = kc_omega(X.kc[d], i);
         st_df(sv + i - c0, v);
-        st_df(sdv + i - c0, df_mul(dfloat{om.x, om.y}, v));
+        st_df(sdv + i - c0, P.quad ? mv_row(X.kc[d], dd.v, i) : df_mul(dfloat{om.x, om.y}, v));
         st_df(skv + i - c0, kv_row(X.kc[d], dd.v, i));
       }
       __syncthreads();
@@ -293,6 +329,39 @@ static __device__ __noinline__ void build_coefficients(const StepParams& P, int 
   __syncthreads();
 }
 
+// Gauss rule: Phi_x^T of the point sums of the nonlinear contraction at node i, i.e. the sum
+// over the points r of the elements whose support holds node i of N~_i(x_r) R_q[r], where R_q
+// is the weighted sum of w(u^k) over the other dimensions' points (FP64 path: the chunk
+// partials in rpart; tensor-core path: the tile partials in rpart32).
+__device__ inline double gauss_row_integral(const StepParams& P, const Extra& X, int x, int i) {
+  const Dim& dd = P.d[x];
+  const int q = P.quad_q, s = (dd.b - 1) / 2;
+  const int e0 = max(0, i - 1 - s), e1 = min(dd.n - 2, i + s);
+  const int C = P.rchunks[x];
+  double R = 0.0;
+  for (int r = e0 * q; r < (e1 + 1) * q; ++r) {
+    const int k = i - dd.phi0[r];
+    if (k < 0 || k >= kPhiW) continue;
+    const double ph = f2_to_double(dd.phi[static_cast<size_t>(r) * kPhiW + k]);
+    if (ph == 0.0) continue;
+    double rq = 0.0;
+    if (P.precision == 0) {
+      const double* rp = P.rpart + static_cast<size_t>(r) * C;
+      for (int kk = 0; kk < C; ++kk) rq += rp[kk];
+    } else {
+      const TcDir& td = X.dirs[x];
+      const long long T = static_cast<long long>(td.nrb) * td.ntc;
+      const int rb = r / kTcM;
+      const int Cr = tile_owner(T, P.vgrid, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
+                     tile_owner(T, P.vgrid, static_cast<long long>(rb) * td.ntc) + 1;
+      const float* rp = X.rpart32 + static_cast<size_t>(r) * td.cmax;
+      for (int kk = 0; kk < Cr; ++kk) rq += static_cast<double>(rp[kk]);
+    }
+    R = fma(ph, rq, R);
+  }
+  return R;
+}
+
 // Right-hand side rows of this CTA's slice of direction x (Eq. KxQx), written as
 // double-float into P.Q.  R_i (the nonlinear contraction, without L omega_i) comes from the
 // partial buffers.
@@ -329,8 +398,12 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
     const bool live = i < hi;
     dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f}, s4 = {0.f, 0.f};
     if (live) {
+      // Gauss rule: M a and M b of the factors (consistent mass), nodal rule: a and b (the
+      // diagonal mass joins below)
+      const float2* Acol = P.quad ? dd.MA : dd.bank[pb];
+      const float2* Bcol = P.quad ? dd.MB : dd.bank[cb];
       for (int m = lane; m < Mk; m += tpr) {
-        const dfloat ami = ld_df(dd.bank[pb] + static_cast<size_t>(m) * dd.n + i), h = ld_df(c->H + m);
+        const dfloat ami = ld_df(Acol + static_cast<size_t>(m) * dd.n + i), h = ld_df(c->H + m);
         s1 = df_fma(s1, ami, h);
         if (sep) s4 = df_add(s4, df_neg(df_mul(ami, h)));   // -u part of w (Eq. MxySep)
       }
@@ -343,7 +416,7 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         s4 = df_fma(s4, df_mul(df_mul(a1, a2), a3), ld_df(c->T + q));
       }
       for (int m = lane; m < M; m += tpr) {
-        const dfloat bmi = ld_df(dd.bank[cb] + static_cast<size_t>(m) * dd.n + i);
+        const dfloat bmi = ld_df(Bcol + static_cast<size_t>(m) * dd.n + i);
         const dfloat gm = ld_df(c->GM + m);
         s1 = df_add(s1, df_neg(df_mul(bmi, gm)));
         s2 = df_fma(s2, ld_df(dd.KB + static_cast<size_t>(m) * dd.n + i), gm);
@@ -358,6 +431,8 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
       dfloat R;
       if (sep) {
         R = df_mul(df_of(4.0 * P.a0), s4);
+      } else if (P.quad) {
+        R = df_of(gauss_row_integral(P, X, x, i));
       } else if (P.precision == 0) {
         const double* rp = P.rpart + static_cast<size_t>(i) * C;
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
@@ -390,27 +465,52 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         for (int k = 8; k < Cr; ++k) R = df_add(R, dfloat{rp[k], 0.f});
         for (int k = 0; k < Cr; ++k) rp[k] = 0.f;
       }
-      const float2 om2 = kc_omega(X.kc[x], i);
-      const dfloat om = {om2.x, om2.y};
-      // Q = c_t om s1 - c_k s2 - c_k om s3 - L om R
-      dfloat q = df_mul(df_mul(ct, om), s1);
-      q = df_add(q, df_neg(df_mul(ck, s2)));
-      q = df_add(q, df_neg(df_mul(df_mul(ck, om), s3)));
-      q = df_add(q, df_neg(df_mul(df_mul(L, om), R)));
+      dfloat q;
+      if (P.quad) {
+        // Gauss rule: Q = c_t (M A H - M B GM) - c_k K B GM - c_k M B GK - L Phi^T (weighted sums)
+        q = df_mul(ct, s1);
+        q = df_add(q, df_neg(df_mul(ck, s2)));
+        q = df_add(q, df_neg(df_mul(ck, s3)));
+        q = df_add(q, df_neg(df_mul(L, R)));
+      } else {
+        const float2 om2 = kc_omega(X.kc[x], i);
+        const dfloat om = {om2.x, om2.y};
+        // Q = c_t om s1 - c_k s2 - c_k om s3 - L om R
+        q = df_mul(df_mul(ct, om), s1);
+        q = df_add(q, df_neg(df_mul(ck, s2)));
+        q = df_add(q, df_neg(df_mul(df_mul(ck, om), s3)));
+        q = df_add(q, df_neg(df_mul(df_mul(L, om), R)));
+      }
       st_df(P.Q + i, q);
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// FP64 nonlinear contraction of the materialised w(u^k) grid (Eq. KxxMxx, nodal rule):
-// rpart[c * C + k] = partial over chunk k of sum_{other indices} W * prod_{d != x} wv_d,
-// wv_d = omega_d v_d in FP64 (shared memory, wv + d * kMaxN).
-static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, const double* wv) {
+// Grid of the nonlinear term: points per dimension and the FP64 weights of the fixed factors
+// at those points (shared memory)
+struct GridW {
+  int n[kMaxDim];
+  const double* w[kMaxDim];
+};
+__device__ __forceinline__ GridW nodal_grid(const StepParams& P, const double* wv) {
+  GridW g;
+  for (int d = 0; d < kMaxDim; ++d) {
+    g.n[d] = d < P.dim ? P.d[d].n : 1;
+    g.w[d] = wv + d * kMaxN;
+  }
+  return g;
+}
+
+// FP64 nonlinear contraction of the materialised w(u^k) grid (Eq. KxxMxx):
+// rpart[c * C + k] = partial over chunk k of sum_{other indices} W * prod_{d != x} wv_d, with
+// wv_d the weights of the fixed factors at the grid points: omega_d v_d (nodal rule), or
+// omega_q,d (Phi_d v_d) at the Gauss points.
+static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, const GridW& g) {
   const int D = P.dim;
-  const int n0 = P.d[0].n, n1 = P.d[1].n, n2 = D == 3 ? P.d[2].n : 1;
+  const int n0 = g.n[0], n1 = g.n[1], n2 = D == 3 ? g.n[2] : 1;
   const int C = P.rchunks[x];
-  const int nc = P.d[x].n;
+  const int nc = g.n[x];
   const int warp_g = P.vrank * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   const int total_warps = P.vgrid * kWarps;
   const double* W = P.W;
@@ -437,7 +537,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
           for (; r + 1 < r1; r += 2) {
             const double2 w0 = __ldcs(W2 + static_cast<size_t>(r) * ncp + cp);
             const double2 w1 = __ldcs(W2 + static_cast<size_t>(r + 1) * ncp + cp);
-            const double f0 = wv[r], f1 = wv[r + 1];
+            const double f0 = g.w[0][r], f1 = g.w[0][r + 1];
             a0 = fma(w0.x, f0, a0);
             a1 = fma(w0.y, f0, a1);
             b0 = fma(w1.x, f1, b0);
@@ -445,8 +545,8 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
           }
           if (r < r1) {
             const double2 w0 = __ldcs(W2 + static_cast<size_t>(r) * ncp + cp);
-            a0 = fma(w0.x, wv[r], a0);
-            a1 = fma(w0.y, wv[r], a1);
+            a0 = fma(w0.x, g.w[0][r], a0);
+            a1 = fma(w0.y, g.w[0][r], a1);
           }
           P.rpart[static_cast<size_t>(2 * cp) * C + k] = a0 + b0;
           P.rpart[static_cast<size_t>(2 * cp + 1) * C + k] = a1 + b1;
@@ -454,7 +554,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
       }
     } else {
       // row dots R[r] = sum_q W[r, q] wv1[q]; units (row, column chunk)
-      const double2* wl2 = reinterpret_cast<const double2*>(wv + kMaxN);
+      const double2* wl2 = reinterpret_cast<const double2*>(g.w[1]);
       const int units = nc * C;
       for (int u = warp_g; u < units; u += total_warps) {
         const int c = u / C, k = u - c * C;
@@ -487,7 +587,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
       for (int rb = r0; rb < r1; rb += 32) {
         const int r = rb + lane;
         double wr = 0.0;
-        if (r < r1) wr = (D == 2) ? wv[r] : wv[r / n1] * wv[kMaxN + (r % n1)];
+        if (r < r1) wr = (D == 2) ? g.w[0][r] : g.w[0][r / n1] * g.w[1][r % n1];
         const int cnt = min(32, r1 - rb);
         for (int t = 0; t < cnt; ++t) {
           const double w = __shfl_sync(0xffffffffu, wr, t);
@@ -499,7 +599,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
   } else {
     // row dots over the last axis
     const int nl = (D == 2) ? n1 : n2;
-    const double* wl = wv + (D - 1) * kMaxN;   // weights of the last dimension
+    const double* wl = g.w[D - 1];   // weights of the last dimension
     const int units = nc * C;
     for (int u = warp_g; u < units; u += total_warps) {
       const int c = u / C, k = u - c * C;
@@ -511,7 +611,7 @@ static __device__ __noinline__ void contract_fp64(const StepParams& P, int x, co
         for (int q = q0 + lane; q < q1; q += 32) acc = fma(row[q], wl[q], acc);
       } else {               // D == 3, x in {0, 1}: rows over the other leading dimension
         const int no = (x == 0) ? n1 : n0;
-        const double* wo = wv + ((x == 0) ? 1 : 0) * kMaxN;
+        const double* wo = g.w[(x == 0) ? 1 : 0];
         int i0, i1;
         slice_of(no, C, k, i0, i1);
         for (int i = i0; i < i1; ++i) {
@@ -551,6 +651,71 @@ static __device__ __noinline__ void load_weights_fp64(const StepParams& P, const
     }
   }
   __syncthreads();
+}
+
+// Gauss rule: FP64 weights omega_q,d (Phi_d v_d) of every dimension but x at its Gauss points,
+// packed in shared memory (each dimension's block at an even offset, for 16-byte loads).  The
+// host admits the rule only when the blocks fit the phase's kMaxDim * kMaxN doubles.
+static __device__ __noinline__ GridW load_weights_gauss(const StepParams& P, int x, double* wv) {
+  GridW g;
+  int off = 0;
+  for (int d = 0; d < kMaxDim; ++d) {
+    g.n[d] = d < P.dim ? P.d[d].nq : 1;
+    g.w[d] = wv;
+    if (d >= P.dim || d == x) continue;
+    const Dim& dd = P.d[d];
+    g.w[d] = wv + off;
+    const int phiw = dd.b + 1;
+    for (int r = threadIdx.x; r < dd.nq; r += blockDim.x)
+      wv[off + r] = dd.wq[r] * df_to_double(phi_row(dd, phiw, dd.v, r));
+    off += (dd.nq + 1) & ~1;
+  }
+  __syncthreads();
+  return g;
+}
+
+// Gauss rule, step prologue (own slices): u^k's factors at the Gauss points, Aq = Phi a, and
+// the consistent-mass products M a (double-float), for the right-hand sides and the grid.
+static __device__ __noinline__ void gauss_prologue(const StepParams& P, const Extra& X, int pb, int Mk) {
+  for (int d = 0; d < P.dim; ++d) {
+    const Dim& dd = P.d[d];
+    const int phiw = dd.b + 1;
+    int lo, hi;
+    slice_of(dd.nq, P.vgrid, P.vrank, lo, hi);
+    for (int m = 0; m < Mk; ++m) {
+      const float2* col = dd.bank[pb] + static_cast<size_t>(m) * dd.n;
+      for (int r = lo + threadIdx.x; r < hi; r += blockDim.x)
+        st_df(dd.Aq + static_cast<size_t>(m) * dd.nq + r, phi_row(dd, phiw, col, r));
+    }
+    slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
+    for (int m = 0; m < Mk; ++m) {
+      const float2* col = dd.bank[pb] + static_cast<size_t>(m) * dd.n;
+      for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        st_df(dd.MA + static_cast<size_t>(m) * dd.n + i, mv_row(X.kc[d], col, i));
+    }
+  }
+}
+
+// Gauss rule: W = w(u^k) on the grid of Gauss points from the factors at the points Aq (FP64
+// reconstruction; row-major grid).
+static __device__ __noinline__ void materialise_w_gauss(const StepParams& P, int Mk) {
+  const int D = P.dim;
+  const int n0 = P.d[0].nq, n1 = P.d[1].nq, n2 = D == 3 ? P.d[2].nq : 1;
+  const long long N = static_cast<long long>(n0) * n1 * n2;
+  const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
+  for (long long p = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x; p < N; p += stride) {
+    const int l = static_cast<int>(p % n2);
+    const long long ij = p / n2;
+    const int j = static_cast<int>(ij % n1), i = static_cast<int>(ij / n1);
+    double u = 0.0;
+    for (int m = 0; m < Mk; ++m) {
+      double t = f2_to_double(P.d[0].Aq[static_cast<size_t>(m) * n0 + i]) *
+                 f2_to_double(P.d[1].Aq[static_cast<size_t>(m) * n1 + j]);
+      if (D == 3) t *= f2_to_double(P.d[2].Aq[static_cast<size_t>(m) * n2 + l]);
+      u += t;
+    }
+    __stcs(P.W + p, 4.0 * P.a0 * (u * u * u - u));
+  }
 }
 
 // Reduced integration domain on the materialised grid (FP64 path, 2D): every 128 x 128 node

@@ -19,6 +19,8 @@ PREC_FP64 = 0
 PREC_SPLIT_BF16 = 1
 NONLINEAR_GRID = 0         # nonlinear term as the full nodal integral (Eq. KxxMxx)
 NONLINEAR_SEPARATED = 1    # separated form (Eq. MxySep) for steps with M_k <= 16
+QUAD_NODAL = 0             # mass-type integrals with the nodal rule (M = diag(omega))
+QUAD_GAUSS = 1             # Gauss points per element, consistent mass
 
 STATUS = {0: "CTD_OK", 1: "CTD_STATUS_CAPPED", 2: "CTD_STATUS_ALS_NOT_CONVERGED", -1: "CTD_ERR_ARG",
           -2: "CTD_ERR_WORKSPACE", -3: "CTD_ERR_CUDA", -4: "CTD_ERR_NONFINITE", -5: "CTD_ERR_TIMEOUT",
@@ -35,7 +37,7 @@ class Config(ctypes.Structure):
                 ("fixed_modes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int),
                 ("reduced_tol", ctypes.c_double), ("nonlinear_form", ctypes.c_int),
-                ("als_stall_tol", ctypes.c_double)]
+                ("als_stall_tol", ctypes.c_double), ("quad_rule", ctypes.c_int), ("quad_q", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -95,7 +97,8 @@ def load() -> ctypes.CDLL:
 
 def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
                 precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
-                grid_ctas=0, reduced_tol=0.0, nonlinear_form=0, als_stall_tol=0.0) -> Config:
+                grid_ctas=0, reduced_tol=0.0, nonlinear_form=0, als_stall_tol=0.0, quad_rule=0,
+                quad_q=0) -> Config:
     c = Config()
     c.dim = dim
     for k in range(3):
@@ -110,6 +113,7 @@ def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, 
     c.reduced_tol = float(reduced_tol)
     c.nonlinear_form = int(nonlinear_form)
     c.als_stall_tol = float(als_stall_tol)
+    c.quad_rule, c.quad_q = int(quad_rule), int(quad_q)
     return c
 
 

@@ -149,3 +149,28 @@ def test_calls_without_a_handle_fail_cleanly(ctd):
     e = ctypes.c_double()
     assert lib.ctd_energy(None, ctypes.byref(e)) == -1
     lib.ctd_destroy(None)
+
+
+@pytest.mark.parametrize("over,status", [
+    (dict(quad_rule=2, quad_q=5), -1),                                 # unknown rule: CTD_ERR_ARG
+    (dict(quad_rule=1, quad_q=0), -1), (dict(quad_rule=1, quad_q=17), -1),
+    (dict(quad_rule=1, quad_q=5, nonlinear_form=1, M_max=8), -7),      # separated form: CTD_ERR_UNSUPPORTED
+    (dict(quad_rule=1, quad_q=5, reduced_tol=1e-3), -7),               # reduced domain
+    (dict(quad_rule=1, quad_q=5, n=(4096, 64)), -7),                   # 20475 points beside direction 1
+    (dict(quad_rule=1, quad_q=2, n=(4096, 4096)), 0), (dict(quad_rule=1, quad_q=5), 0),
+    (dict(als_stall_tol=-1.0), -1), (dict(als_stall_tol=1e-6), 0)])
+def test_gauss_and_stall_configurations(ctd, over, status):
+    w = workloads.preset("c0", **({"n": over.pop("n")} if "n" in over else {}))
+    cfg = ctd.config_from_workload(w, **over)
+    n = ctypes.c_size_t(0)
+    assert ctd.load().ctd_workspace_size(ctypes.byref(cfg), ctypes.byref(n)) == status
+    if status == 0:
+        assert n.value > 0
+
+
+def test_gauss_workspace_holds_the_point_grid(ctd):
+    w = workloads.preset("c0", n=(200, 180))
+    nodal = ctd.workspace_size(ctd.config_from_workload(w))
+    gauss = ctd.workspace_size(ctd.config_from_workload(w, quad_rule=1, quad_q=5))
+    # the FP64 grid of w(u^k) grows from 200 x 180 nodes to 995 x 895 Gauss points
+    assert gauss - nodal >= 8 * (995 * 895 - 200 * 180)

@@ -59,7 +59,7 @@ def test_nonfinite_device_modes_fail_the_step(lib, prec):
 
 
 def test_mode_cap_reports_capped(lib):
-    w = workloads.preset("c0", n=(40, 36), M_max=1)
+    w = workloads.preset("c0", n=(40, 36), M_max=1, ic_rank=1)
     s = lib.Solver(lib.config_from_workload(w))
     s.set_initial_modes(workloads.initial_modes(w))
     st = s.step(2)
