@@ -44,7 +44,7 @@ struct Carver {
 struct Plan {
   int D, n[3], nq[3], quad, b[3], n_pad[3], Mcap, Kpad, sep_q, grid, rchunks[3];
   long long N;
-  size_t rpart_len, rpart32_len;
+  size_t rpart_len, rpart_tc_len;
   ctd::TcDir dirs[3];
 };
 
@@ -113,14 +113,14 @@ Plan make_plan(const ctd_config& c, int grid) {
   p.sep_q = c.nonlinear_form == CTD_NONLINEAR_SEPARATED ? ctd::sep_terms(c.M_max) : 0;
   p.grid = grid;
   p.rpart_len = 0;
-  p.rpart32_len = 0;
+  p.rpart_tc_len = 0;
   for (int x = 0; x < c.dim; ++x) {
     p.rchunks[x] = chunks_for(c.dim, p.nq, x, grid);
     p.rpart_len = std::max(p.rpart_len, static_cast<size_t>(p.nq[x]) * p.rchunks[x]);
   }
   for (int x = 0; x < c.dim; ++x) {
     p.dirs[x] = tc_dir(p, x, grid);
-    p.rpart32_len = std::max(p.rpart32_len, static_cast<size_t>(p.nq[x]) * p.dirs[x].cmax);
+    p.rpart_tc_len = std::max(p.rpart_tc_len, static_cast<size_t>(p.nq[x]) * p.dirs[x].cmax);
   }
   return p;
 }
@@ -173,7 +173,7 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   const int nslots = std::max((D - 1) * spd, D * 6);
   p.gram = cv.take<float2>(static_cast<size_t>(nslots) * Gs);
   p.rpart = cv.take<double>(pl.rpart_len);
-  x.rpart32 = cv.take<float>(std::max<size_t>(1, pl.rpart32_len));
+  x.rpart_tc = cv.take<double>(std::max<size_t>(1, pl.rpart_tc_len));
   for (int k = 0; k < 3; ++k) x.kr[k] = nullptr;
   if (c.precision == CTD_PREC_SPLIT_BF16 && D == 3)
     for (int k = 0; k < 3; ++k)
@@ -298,6 +298,7 @@ struct ctd_ctx {
   float2* mc_store[3];
   std::vector<double> gphi[3];   // Gauss rule: shape function values at the points [nq][2s+2]
   std::vector<int> gcol0[3];     // and their first nodes
+  std::vector<double> gwq[3];    // and the weights of the points
   double* energy_part;
   double* energy_gram;
   StepStatsDev* stats_dev;
@@ -367,7 +368,7 @@ ctd_status ctd_workspace_size(const ctd_config* cfg, size_t* bytes) {
   double *ep, *eg;
   StepStatsDev* sd;
   size_t best = 0;
-  // every grid size 1..kGridMax fits (rpart32 depends on the split of tiles over CTAs)
+  // every grid size 1..kGridMax fits (rpart_tc depends on the split of tiles over CTAs)
   for (int g : {1, 2, 4, 8, 16, 32, 64, 128, 132, 144, 148, 152, 160, 256, kGridMax}) {
     const Plan pl = make_plan(*cfg, g);
     best = std::max(best, carve(*cfg, pl, nullptr, nullptr, nullptr, kc, mc, &ep, &eg, &sd));
@@ -545,6 +546,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
       k.mstencil = h->mc_store[d] + static_cast<size_t>(ml + mt) * w;
       h->gphi[d] = phi;
       h->gcol0[d] = col0;
+      h->gwq[d] = wq;
     }
     k.n = n;
     k.b = b;
@@ -879,7 +881,7 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
   }
   CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
   // partial slots of CTAs without a tile in a row block are not written: start from zero
-  CTD_CUDA(h, cudaMemsetAsync(h->X.rpart32, 0, sizeof(float) * std::max<size_t>(1, h->plan.rpart32_len), h->stream));
+  CTD_CUDA(h, cudaMemsetAsync(h->X.rpart_tc, 0, sizeof(double) * std::max<size_t>(1, h->plan.rpart_tc_len), h->stream));
   CTD_CUDA(h, ctd::launch_probe_contract(h->P, h->X, h->grid, x, nullptr, h->stream));
   const int n = h->cfg.n[x], nq = h->plan.nq[x];
   std::vector<double> rq(nq);   // weighted sums at the points of direction x (the nodes, nodal rule)
@@ -896,8 +898,8 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
     }
   } else {
     const ctd::TcDir& td = h->plan.dirs[x];
-    std::vector<float> part(static_cast<size_t>(nq) * td.cmax);
-    CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->X.rpart32, sizeof(float) * part.size(), cudaMemcpyDeviceToHost,
+    std::vector<double> part(static_cast<size_t>(nq) * td.cmax);
+    CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->X.rpart_tc, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
                                 h->stream));
     CTD_CUDA(h, cudaStreamSynchronize(h->stream));
     const long long T = static_cast<long long>(td.nrb) * td.ntc;
@@ -917,7 +919,7 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
     for (int r = 0; r < nq; ++r)
       for (int k = 0; k < wphi; ++k) {
         const int i = h->gcol0[x][r] + k;
-        if (i < n) out[i] += h->gphi[x][static_cast<size_t>(r) * wphi + k] * rq[r];
+        if (i < n) out[i] += h->gphi[x][static_cast<size_t>(r) * wphi + k] * h->gwq[x][r] * rq[r];
       }
   } else {
     for (int i = 0; i < n; ++i) out[i] = rq[i];

@@ -218,7 +218,7 @@ struct TcDir {
   int ncols_pad;    // padded rows of the column operand
   int n_last_pad;   // 3D: padded length of the last other dimension (tile = one mid index)
   int mid, last;    // other dimensions: 2D mid = -1, last = the other; 3D both set
-  int cmax;         // partial slots per row in rpart32
+  int cmax;         // partial slots per row in rpart_tc
 };
 
 // Split u^k's factors into BF16 hi/lo tile-image operands and, in 3D, the Khatri-Rao operands
@@ -359,7 +359,7 @@ __host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_
 }
 
 // This CTA's share of the contraction for direction x.  Partial row sums go to
-// rpart32[row * cmax + (cta - first owner of the row block)].  If dump != null the raw
+// rpart_tc[row * cmax + (cta - first owner of the row block)].  If dump != null the raw
 // reconstructed values are written to dump[row * ncols_pad + col] instead (test probe).
 // Returns false if a wait expired.
 //
@@ -369,7 +369,7 @@ __host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_
 // the tile of direction 0 (row block of dimension 0, column block of dimension 1).
 static __device__ __noinline__ bool tc_contract(const StepParams& P, const KCompressed* kc, const TcDir& td,
                                    const __nv_bfloat16* Pop, const __nv_bfloat16* Qop, int x, int Mk, int stages,
-                                   unsigned char* base, uint32_t tmem_base, float* rpart32, float* dump,
+                                   unsigned char* base, uint32_t tmem_base, double* rpart_tc, float* dump,
                                    const unsigned* tile_max = nullptr, float on_scale = 0.f, float on_tol = 0.f) {
   const int G = P.vgrid, cta = P.vrank;
   // Parameters the role loops use, in registers: P and td live in shared memory, and every
@@ -424,7 +424,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         const int j = cta - tile_owner(T, G, static_cast<long long>(rb) * ntc);
         for (int r = threadIdx.x; r < kTcM; r += blockDim.x) {
           const int row = rb * kTcM + r;
-          if (row < nx) rpart32[static_cast<size_t>(row) * cmax + j] = 0.f;
+          if (row < nx) rpart_tc[static_cast<size_t>(row) * cmax + j] = 0.0;
         }
       }
     }
@@ -563,13 +563,13 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");   // the epilogue warps only
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16);
-    float acc = 0.f;
+    double acc = 0.0;   // FP32 within a tile, FP64 across the tiles of a row block
     int cur_rb = -1;
     auto flush = [&](int rbf) {
       const int row = rbf * kTcM + r;
       if (!dump && row < nx) {
         const int j = cta - tile_owner(T, G, static_cast<long long>(rbf) * ntc);
-        rpart32[static_cast<size_t>(row) * cmax + j] = acc;
+        rpart_tc[static_cast<size_t>(row) * cmax + j] = acc;
       }
     };
     int rb = t0 / ntc, cb = t0 - rb * ntc;
@@ -578,7 +578,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       g = 1;
       if (rb != cur_rb) {
         if (cur_rb >= 0) flush(cur_rb);
-        acc = 0.f;
+        acc = 0.0;
         cur_rb = rb;
       }
       if (!active(t)) continue;
@@ -623,7 +623,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
           }
         }
         const float at = (a01.x + a01.y) + (a23.x + a23.y);
-        acc = __fmaf_rn(wscale, at, acc);
+        acc = fma(static_cast<double>(wscale), static_cast<double>(at), acc);
       }
       tc_fence_before();
       mbar_arrive(&sh->acc_empty[ps]);

@@ -199,7 +199,7 @@ CTD_LOCAL __device__ __noinline__ void clear_point_partials(const StepParams& P,
   const size_t total = static_cast<size_t>(P.d[x].nq) * X.dirs[x].cmax;
   int lo, hi;
   slice_of(static_cast<int>(total), parts, me, lo, hi);
-  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) X.rpart32[i] = 0.f;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) X.rpart_tc[i] = 0.0;
 }
 
 // Save the current trial factors (own slices) at the start of a sweep.
@@ -307,7 +307,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     }
     for (size_t i = static_cast<size_t>(P.vrank) * blockDim.x + threadIdx.x; i < nslot;
          i += static_cast<size_t>(P.vgrid) * blockDim.x)
-      X.rpart32[i] = 0.f;
+      X.rpart_tc[i] = 0.0;
   }
   if (!kSepTU && P.reduced_tol > 0.0 && Mk > 0) {
     // reduced integration domain (Section 3.3): the nonlinear term is fixed for the step, so
@@ -362,7 +362,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
           const TcDir& td = X.dirs[x];
           const __nv_bfloat16* qop = (D == 2) ? P.d[td.last].op : X.kr[x];
           if (!tc_contract(P, X.kc, td, P.d[x].op, qop, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base,
-                           X.rpart32, nullptr, P.reduced_tol > 0.0 ? P.tile_max : nullptr,
+                           X.rpart_tc, nullptr, P.reduced_tol > 0.0 ? P.tile_max : nullptr,
                            static_cast<float>(4.0 * P.a0), static_cast<float>(P.reduced_tol)))
             return;
         }
@@ -719,7 +719,7 @@ __device__ void probe_contract_body(const StepParams& P, const Extra& X, int x, 
     if (!sync_all(P, epoch, 11)) return;
     const TcDir& td = X.dirs[x];
     const __nv_bfloat16* qop = (P.dim == 2) ? P.d[td.last].op : X.kr[x];
-    tc_contract(P, X.kc, td, P.d[x].op, qop, x, st0.Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart32,
+    tc_contract(P, X.kc, td, P.d[x].op, qop, x, st0.Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart_tc,
                 dump);
   }
 }

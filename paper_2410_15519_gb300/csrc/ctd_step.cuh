@@ -49,7 +49,7 @@ struct Extra {            // per-launch workspace pieces not in StepParams
   double* Af[kMaxDim];    // FP64 copy of u^k factors [Mcap][n] (FP64-path materialisation)
   double* maxpart;        // [kMaxDim][grid]
   int* ctrl;              // [4] solver flags broadcast
-  float* rpart32;         // [n][cmax] FP32 partials (tensor-core path)
+  double* rpart_tc;        // [nq][cmax] partial row sums of the tensor-core contraction (one per CTA)
   TcDir dirs[kMaxDim];    // tensor-core geometry per direction
   __nv_bfloat16* kr[kMaxDim];   // 3D Khatri-Rao operands per direction
   int tc_stages;          // B-operand ring depth
@@ -332,7 +332,7 @@ static __device__ __noinline__ void build_coefficients(const StepParams& P, int 
 // Gauss rule: Phi_x^T of the point sums of the nonlinear contraction at node i, i.e. the sum
 // over the points r of the elements whose support holds node i of N~_i(x_r) R_q[r], where R_q
 // is the weighted sum of w(u^k) over the other dimensions' points (FP64 path: the chunk
-// partials in rpart; tensor-core path: the tile partials in rpart32).
+// partials in rpart; tensor-core path: the tile partials in rpart_tc).
 __device__ inline double gauss_row_integral(const StepParams& P, const Extra& X, int x, int i) {
   const Dim& dd = P.d[x];
   const int q = P.quad_q, s = (dd.b - 1) / 2;
@@ -354,10 +354,10 @@ __device__ inline double gauss_row_integral(const StepParams& P, const Extra& X,
       const int rb = r / kTcM;
       const int Cr = tile_owner(T, P.vgrid, static_cast<long long>(rb) * td.ntc + td.ntc - 1) -
                      tile_owner(T, P.vgrid, static_cast<long long>(rb) * td.ntc) + 1;
-      const float* rp = X.rpart32 + static_cast<size_t>(r) * td.cmax;
-      for (int kk = 0; kk < Cr; ++kk) rq += static_cast<double>(rp[kk]);
+      const double* rp = X.rpart_tc + static_cast<size_t>(r) * td.cmax;
+      for (int kk = 0; kk < Cr; ++kk) rq += rp[kk];
     }
-    R = fma(ph, rq, R);
+    R = fma(ph * dd.wq[r], rq, R);
   }
   return R;
 }
@@ -454,16 +454,16 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         // Slots of CTAs inside the row block's owner range that hold no tile of it are never
         // written: the buffer is zero between half-sweeps (cleared in the step prologue, and
         // every slot read here is cleared again for the next direction)
-        float* rp = X.rpart32 + static_cast<size_t>(i) * td.cmax;
-        float part[8];   // loads first, so that their latencies overlap
+        double* rp = X.rpart_tc + static_cast<size_t>(i) * td.cmax;
+        double part[8];   // loads first, so that their latencies overlap
 #pragma unroll
-        for (int k = 0; k < 8; ++k) part[k] = k < Cr ? rp[k] : 0.f;
-        R = {0.f, 0.f};
+        for (int k = 0; k < 8; ++k) part[k] = k < Cr ? rp[k] : 0.0;
+        double r = 0.0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (k < Cr) R = df_add(R, dfloat{part[k], 0.f});
-        for (int k = 8; k < Cr; ++k) R = df_add(R, dfloat{rp[k], 0.f});
-        for (int k = 0; k < Cr; ++k) rp[k] = 0.f;
+        for (int k = 0; k < 8; ++k) r += part[k];
+        for (int k = 8; k < Cr; ++k) r += rp[k];
+        R = df_of(r);
+        for (int k = 0; k < Cr; ++k) rp[k] = 0.0;
       }
       dfloat q;
       if (P.quad) {
