@@ -53,6 +53,7 @@ PLAN = {"c0": dict(err_steps=10, side_steps=10, oracle_n=None),
         "c2": dict(err_steps=2, side_steps=3, oracle_n=128),
         "c3": dict(err_steps=2, side_steps=2, oracle_n=128)}
 FP64_NOMINAL_TFLOPS = 1.25   # nominal FP64 (non-tensor) rate of the part, from the pool's table
+PRODUCTS = {"mixed": 3, "bf16": 1, "split3": 6}   # BF16 products per mode and grid point
 
 
 def peaks():
@@ -236,7 +237,7 @@ def half_sweep_roof_s(w, precision: str, Mk: int, pk: dict) -> dict:
         t_f = 2.0 * N / (FP64_NOMINAL_TFLOPS * 1e12)
         t_b = 8.0 * N / (pk["hbm_gbs"] * 1e9)
         return {"fp64": t_f, "hbm": t_b}
-    keff = 3 * Mk
+    keff = PRODUCTS[precision] * Mk
     t_tensor = 2.0 * keff * N / (pk["bf16_tflops"] * 1e12)
     t_alu = 3.0 * N / (alu_peak_tops(pk) * 1e12)
     t_hbm = 2.0 * keff * sum(w.n) / (pk["hbm_gbs"] * 1e9)
@@ -261,7 +262,7 @@ def step_roofline(w, precision, ranks_in, stats, times_ms, pk, pk_kind, traffic)
         peak_kind = ("FP32 lane operations (3 per grid point and half-sweep), peak = 152 SMs x 128 lanes x "
                      f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz, derived from unit counts and the maximum clock")
     elif bound == "tensor":
-        flops = sum(2.0 * 3 * mk * N * st["als_sweeps"] * w.dim for mk, st in zip(ranks_in, stats))
+        flops = sum(2.0 * PRODUCTS[precision] * mk * N * st["als_sweeps"] * w.dim for mk, st in zip(ranks_in, stats))
         achieved, peak, unit = flops / t / 1e12, pk["bf16_tflops"], "TFLOP/s"
         peak_kind = f"bf16 dense burst, {pk_kind} (of {pk_kind})"
     elif bound == "fp64":
@@ -292,13 +293,13 @@ def last_cta_tile_share(w, G: int = SMS) -> float:
     return (T - lo) / T
 
 
-def contraction_roof_us(w, Mk: float, pk: dict) -> dict:
+def contraction_roof_us(w, Mk: float, pk: dict, precision: str = "mixed") -> dict:
     """Roofline time of the last CTA's share of one half-sweep's tensor-core contraction (the
     phase is timed on that CTA): the larger of the split reconstruction on the tensor cores
     (2 * 3Mk flops per grid point at one SM's share of the BF16 burst peak) and the fused
     epilogue on the FP32 pipes (3 operations per grid point on 128 lanes at the maximum clock)."""
     n_cta = float(w.grid_points) * last_cta_tile_share(w)
-    t_tensor = 2.0 * 3 * Mk * n_cta / (pk["bf16_tflops"] * 1e12 / SMS)
+    t_tensor = 2.0 * PRODUCTS[precision] * Mk * n_cta / (pk["bf16_tflops"] * 1e12 / SMS)
     t_alu = 3.0 * n_cta / (128 * pk.get("sm_max_mhz", 2070.0) * 1e6)
     bound = "tensor" if t_tensor >= t_alu else "alu"
     return {"roof_us": 1e6 * max(t_tensor, t_alu), "bound": bound, "tensor_us": 1e6 * t_tensor, "alu_us": 1e6 * t_alu,
@@ -332,8 +333,14 @@ def stored_traffic(key: str):
 
 
 # --------------------------------------------------------------------------- GPU legs
+PRECISIONS = ("fp64", "mixed", "bf16", "split3")
+
+
 def prec_code(ctd, precision):
-    return ctd.PREC_FP64 if precision == "fp64" else ctd.PREC_SPLIT_BF16
+    """fp64: FP64 contraction; mixed: split-BF16 (hi + lo) tensor cores; bf16: one BF16 term;
+    split3: hi + mid + lo."""
+    return {"fp64": ctd.PREC_FP64, "mixed": ctd.PREC_SPLIT_BF16, "bf16": ctd.PREC_BF16,
+            "split3": ctd.PREC_SPLIT3_BF16}[precision]
 
 
 def timed_run(ctd, torch, w, precision, steps, warmup, flush, clocks=None, over=None):
@@ -470,6 +477,34 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
                 "fields agree to that truncation level); same_schedule: one step with a fixed mode count and "
                 "sweep count, the arithmetic difference alone; fields compared on the nodes, rebuilt in FP64"}
     out["first_step_modes"] = {"mixed": mx["first"], "fp64": f64["first"]}
+    # the precision ladder of the tensor-core contraction beside the headline's two-term split
+    ladder = {}
+    if args.precision == "mixed":
+        for prec in ("bf16", "split3"):
+            s3, t3, st3, _, _ = timed_run(ctd, torch, w, prec, plan["side_steps"], args.warmup, flush, over=over)
+            s3.close()
+            leg = leg_summary(t3, st3, w)
+            sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **fixed))
+            sv.set_initial_modes(workloads.initial_modes(w))
+            sv.step(1)
+            leg["same_schedule_u_rel_l2_vs_fp64_gpu"] = field_rel_l2(sv.get_modes(), same["fp64"][0])
+            leg["same_schedule_energy_rel_diff"] = abs(sv.energy() - same["fp64"][1]) / abs(same["fp64"][1])
+            sv.close()
+            sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **over))
+            sv.set_initial_modes(workloads.initial_modes(w))
+            energies = [sv.energy()]
+            for k in range(plan["err_steps"]):
+                sv.step(1)
+                energies.append(sv.energy())
+            leg["u_rel_l2_vs_fp64_gpu"] = field_rel_l2(sv.get_modes(), f64["modes"])
+            leg["energy_rel_diff_vs_fp64_gpu"] = abs(energies[-1] - f64["energies"][-1]) / abs(f64["energies"][-1])
+            leg["energy_max_rel_change_per_step"] = max((e1 - e0) / abs(e0) for e0, e1 in zip(energies, energies[1:]))
+            sv.close()
+            ladder[prec] = leg
+        ladder["note"] = ("tensor-core precisions beside the headline's hi + lo split: bf16 = one BF16 term per "
+                          "factor value (1 product per K step), split3 = hi + mid + lo (6 products); timed on the "
+                          "steps after the warm-up, errors as in accuracy")
+    out["ladder"] = ladder
     # side legs: the plain FP64 form under the same rules; both forms with the stall rule off
     side = {}
     for key, prec, o in (("fp64_same_rules", "fp64", over), ("mixed_stall_off", "mixed", dict(als_stall_tol=0.0)),
@@ -500,10 +535,10 @@ def single_line(w, res, args, pk, pk_kind, world, headline=True):
             "als_stalled_per_step": [s["als_stalled"] for s in res["stats"]],
             "half_sweeps_per_s": sum(s["als_sweeps"] for s in res["stats"]) * w.dim / (total_ms / 1e3),
             "phase_us_per_half_sweep": res["phase_us_per_half_sweep"], "roofline": roof,
-            "accuracy": res["accuracy"]}
+            "accuracy": res["accuracy"], "precision_ladder": res.get("ladder", {})}
     ph = res["phase_us_per_half_sweep"]
-    if args.precision == "mixed" and ph.get("contract"):
-        cr = contraction_roof_us(w, res["mk_mean"], pk)
+    if args.precision != "fp64" and ph.get("contract"):
+        cr = contraction_roof_us(w, res["mk_mean"], pk, args.precision)
         line["contraction_roofline"] = {
             "phase_us": ph["contract"], "roof_us": cr["roof_us"], "bound": cr["bound"],
             "frac": cr["roof_us"] / ph["contract"], "tensor_us": cr["tensor_us"], "alu_us": cr["alu_us"],
@@ -754,8 +789,7 @@ def main_batch(args, rank, world, local_rank):
     line = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3-split/f32-acc; solves, Gram products, energy FP64-accurate" if args.precision == "mixed"
-            else "f64", "data": "synthetic", "config": f["config"],
+            "dtype": dtype_of(args.precision), "data": "synthetic", "config": f["config"],
             "instance_steps_per_s": f["instance_steps_per_s"], "dof_updates_per_s": f["dof_updates_per_s"],
             "sweeps_per_instance_step": f["sweeps_per_instance_step"], "modes_per_instance": f["modes_per_instance"],
             "roofline": {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
@@ -789,8 +823,11 @@ def workload_config(w, args):
 
 
 def dtype_of(precision):
-    return ("bf16x3-split/f32-acc contraction; solves, Gram products, convergence test and energy "
-            "FP64-accurate (double-float, FP64 energy)" if precision == "mixed" else "f64")
+    rest = "; solves, Gram products, convergence test double-float (48-bit), energy FP64"
+    return {"mixed": "bf16 hi+lo split (3 products)/f32-acc contraction" + rest,
+            "bf16": "bf16 (1 product)/f32-acc contraction" + rest,
+            "split3": "bf16 hi+mid+lo split (6 products)/f32-acc contraction" + rest,
+            "fp64": "f64 contraction and energy" + rest}[precision]
 
 
 def main():
@@ -799,7 +836,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     ap.add_argument("--workload", default="c3")
     ap.add_argument("--stall", type=float, default=STALL_DEFAULT,
                     help="stall rule of the fixed-point sweeps (als_stall_tol) for every leg; 0: off")

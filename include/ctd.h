@@ -46,11 +46,17 @@ typedef enum {
   CTD_ERR_UNSUPPORTED = -7          /* valid request this build does not implement           */
 } ctd_status;
 
-/* Arithmetic of the full-grid nonlinear contraction (all other parts are FP64-accurate). */
+/* Arithmetic of the full-grid nonlinear contraction (all other parts are FP64-accurate).
+ * The tensor-core forms rebuild u^k per 128 x 128 tile on tcgen05 tensor cores (FP32
+ * accumulation in TMEM), fuse the cubic w(u) into the tile epilogue and sum a tile's columns
+ * in FP32, the tiles of a row in FP64.  They differ in how many BF16 terms carry each factor
+ * value a (relative error of a reconstructed value, against sum_m |prod_d a_m,d|): */
 enum {
-  CTD_PREC_FP64 = 0,      /* w(u^k) materialised once per step in FP64, FP64 contraction  */
-  CTD_PREC_SPLIT_BF16 = 1 /* u^k rebuilt per tile on tcgen05 tensor cores from hi/lo BF16
-                             modes (3 products, FP32 accumulation), cubic fused, FP32 sums */
+  CTD_PREC_FP64 = 0,        /* w(u^k) materialised once per step in FP64, FP64 contraction  */
+  CTD_PREC_SPLIT_BF16 = 1,  /* a = hi + lo, 3 products (hi hi, hi lo, lo hi): about 2^-15    */
+  CTD_PREC_BF16 = 2,        /* a = hi, one product: about 2^-8                               */
+  CTD_PREC_SPLIT3_BF16 = 3  /* a = hi + mid + lo, 6 products (every pair of order <= 2):
+                               about 2^-22                                                  */
 };
 
 typedef struct {
@@ -123,6 +129,8 @@ typedef struct {
   int not_converged;        /* 1 if some mode ended without meeting tol_als (I_max or stall) */
   int status;               /* ctd_status of the step                                       */
   int als_stalled;          /* modes whose sweeps the stall rule ended (als_stall_tol)      */
+  int als_sweeps_committed; /* sweeps of the committed modes (als_sweeps less those of a mode
+                               that the enrichment test discarded)                          */
 } ctd_step_stats;
 
 typedef struct ctd_ctx* ctd_handle;
@@ -231,8 +239,8 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
 ctd_status ctd_probe_solve(ctd_handle h, int x, double alpha1, double alpha2,
                            const double* q, double* y);
 
-/* Grid values of the current field u^k rebuilt on the tensor cores (CTD_PREC_SPLIT_BF16
- * handles only): out[i * ncols_pad + c] for the n_pad[x] x ncols_pad tile grid of direction
+/* Grid values of the current field u^k rebuilt on the tensor cores (handles of a tensor-core
+ * precision only): out[i * ncols_pad + c] for the n_pad[x] x ncols_pad tile grid of direction
  * x (rows: nodes of x padded to 128; columns: nodes of the other dimension (2D) or the
  * other dimensions' index pairs (3D, last one padded to 128)), FP32.  scratch: device
  * buffer of at least the output size.  Synchronises.  Sets the handle's trial factors to

@@ -148,8 +148,9 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
     dd.KB = cv.take<float2>(static_cast<size_t>(pl.Mcap) * n);
     dd.v = cv.take<float2>(n);
     dd.vold = cv.take<float2>(n);
-    dd.op = (c.precision == CTD_PREC_SPLIT_BF16)
-                ? cv.take<__nv_bfloat16>(static_cast<size_t>(pl.n_pad[d]) * 2 * pl.Kpad) : nullptr;
+    dd.op = (c.precision != CTD_PREC_FP64)
+                ? cv.take<__nv_bfloat16>(static_cast<size_t>(pl.n_pad[d]) * ctd::tc_nimg(c.precision) * pl.Kpad)
+                : nullptr;
     kc_store[d] = cv.take<float2>(static_cast<size_t>(n + 1) * w);
     x.Af[d] = cv.take<double>(static_cast<size_t>(pl.Mcap) * n);
     dd.nq = pl.nq[d];
@@ -175,9 +176,10 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   p.rpart = cv.take<double>(pl.rpart_len);
   x.rpart_tc = cv.take<double>(std::max<size_t>(1, pl.rpart_tc_len));
   for (int k = 0; k < 3; ++k) x.kr[k] = nullptr;
-  if (c.precision == CTD_PREC_SPLIT_BF16 && D == 3)
+  if (c.precision != CTD_PREC_FP64 && D == 3)
     for (int k = 0; k < 3; ++k)
-      x.kr[k] = cv.take<__nv_bfloat16>(static_cast<size_t>(pl.dirs[k].ncols_pad) * 2 * pl.Kpad);
+      x.kr[k] = cv.take<__nv_bfloat16>(static_cast<size_t>(pl.dirs[k].ncols_pad) * ctd::tc_nimg(c.precision) *
+                                       pl.Kpad);
   for (int k = 0; k < D; ++k) x.dirs[k] = pl.dirs[k];
   p.Q = cv.take<float2>(ctd::kMaxN);
   size_t crf = 0;
@@ -232,7 +234,9 @@ ctd_status validate(const ctd_config* c) {
   if (!(c->tol_als >= 0.0) || !(c->tol_enrich >= 0.0)) return CTD_ERR_ARG;
   if (!(c->als_stall_tol >= 0.0) || !std::isfinite(c->als_stall_tol)) return CTD_ERR_ARG;
   if (c->fixed_als_iters < 0 || c->fixed_modes < 0 || c->fixed_modes > c->M_max) return CTD_ERR_ARG;
-  if (c->precision != CTD_PREC_FP64 && c->precision != CTD_PREC_SPLIT_BF16) return CTD_ERR_ARG;
+  if (c->precision != CTD_PREC_FP64 && c->precision != CTD_PREC_SPLIT_BF16 && c->precision != CTD_PREC_BF16 &&
+      c->precision != CTD_PREC_SPLIT3_BF16)
+    return CTD_ERR_ARG;
   if (c->grid_ctas > kGridMax) return CTD_ERR_ARG;
   if (!(c->reduced_tol >= 0.0) || !std::isfinite(c->reduced_tol)) return CTD_ERR_ARG;
   if (c->reduced_tol > 0.0 && c->dim != 2) return CTD_ERR_UNSUPPORTED;
@@ -595,8 +599,8 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     else P.solver_mode = 2;
     const size_t used = P.solver_mode == 3 ? chf : (P.solver_mode == 0 ? crf : l0f);
     size_t need = fixed + ctd::step_arena_bytes(n_max, used, P.solver_mode) + 1024;
-    if (cfg->precision == CTD_PREC_SPLIT_BF16) {
-      const int chunks = 2 * h->plan.Kpad / ctd::kTcChunkElems;
+    if (cfg->precision != CTD_PREC_FP64) {
+      const int chunks = ctd::tc_nimg(cfg->precision) * h->plan.Kpad / ctd::kTcChunkElems;
       int stages = 4;
       for (; stages >= 1; --stages) {
         size_t tcb = 0;
@@ -616,7 +620,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     }
     // the tensor-core path allocates all 512 TMEM columns of the SM: more than half the shared
     // memory keeps it at one CTA per SM, so no CTA waits for another's columns
-    if (cfg->precision == CTD_PREC_SPLIT_BF16) need = std::max(need, static_cast<size_t>(optin) / 2 + 1024);
+    if (cfg->precision != CTD_PREC_FP64) need = std::max(need, static_cast<size_t>(optin) / 2 + 1024);
     P.smem_bytes = static_cast<int>(need);
   }
   InstState st{};
@@ -695,6 +699,7 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
         o.capped = rec[k].capped;
         o.not_converged = rec[k].not_converged;
         o.als_stalled = rec[k].als_stalled;
+        o.als_sweeps_committed = rec[k].als_sweeps_committed;
         o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
         if (o.status < 0) worst = static_cast<ctd_status>(o.status);
         else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -781,6 +786,7 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
           o.capped = rec[k].capped;
           o.not_converged = rec[k].not_converged;
           o.als_stalled = rec[k].als_stalled;
+          o.als_sweeps_committed = rec[k].als_sweeps_committed;
           o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
           if (o.status < 0) worst = static_cast<ctd_status>(o.status);
           else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -933,7 +939,7 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
 
 ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch, size_t scratch_bytes) {
   if (!h || !out || x < 0 || x >= h->cfg.dim) return CTD_ERR_ARG;
-  if (h->cfg.precision != CTD_PREC_SPLIT_BF16) return fail(h, CTD_ERR_UNSUPPORTED, "tensor-core path only");
+  if (h->cfg.precision == CTD_PREC_FP64) return fail(h, CTD_ERR_UNSUPPORTED, "tensor-core path only");
   if (!h->has_modes) return fail(h, CTD_ERR_STATE, "no field set");
   const ctd::TcDir& td = h->plan.dirs[x];
   const size_t need = static_cast<size_t>(h->plan.n_pad[x]) * td.ncols_pad * sizeof(float);
@@ -959,7 +965,7 @@ ctd_status ctd_probe_reconstruct(ctd_handle h, int x, float* out, void* scratch,
 
 ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out) {
   if (!h || !out || x < 0 || x >= h->cfg.dim) return CTD_ERR_ARG;
-  if (h->cfg.precision != CTD_PREC_SPLIT_BF16) return fail(h, CTD_ERR_UNSUPPORTED, "tensor-core path only");
+  if (h->cfg.precision == CTD_PREC_FP64) return fail(h, CTD_ERR_UNSUPPORTED, "tensor-core path only");
   const ctd::TcDir& td = h->plan.dirs[x];
   const size_t need = static_cast<size_t>(h->plan.n_pad[x]) * td.ncols_pad * sizeof(float);
   if (need > CTD_RECONSTRUCT_STATIC_BYTES) {

@@ -66,6 +66,7 @@ struct StepStatsDev {
   int not_converged;
   int status;
   int als_stalled;
+  int als_sweeps_committed;
 };
 
 struct StepParams {

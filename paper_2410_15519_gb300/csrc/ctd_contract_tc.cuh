@@ -31,16 +31,25 @@ constexpr int kTcAcc = 4;              // TMEM accumulators in flight (MMAs run 
 constexpr int kTcAccCols = kTcAcc * kTcN;   // TMEM columns allocated: all 512 of the SM
 
 // Tile-image operand layout.  Rows come in blocks of 128; a block holds KS = Kpad / 16 K steps,
-// each a hi and a lo image of 4 KB: 16 groups of 8 rows (256 bytes apart), each group two core
-// matrices of 8 rows x 8 columns (128 contiguous bytes, the second holding columns 8..15).
+// each `nimg` images of 4 KB (the BF16 terms of the split: hi, or hi and lo, or hi, mid and
+// lo): 16 groups of 8 rows (256 bytes apart), each group two core matrices of 8 rows x 8
+// columns (128 contiguous bytes, the second holding columns 8..15).
 constexpr int kTcImgElems = kTcM * 16;                  // elements of one image
 constexpr uint32_t kTcImgBytes = kTcImgElems * 2;       // 4 KB
-__host__ __device__ inline size_t tc_img_index(long long i, int k, int h, int KS) {
+__host__ __device__ inline size_t tc_img_index(long long i, int k, int h, int KS, int nimg) {
   const long long rb = i >> 7;
   const int r = static_cast<int>(i & 127), g = r >> 3, rr = r & 7;
   const int ks = k >> 4, j = (k >> 3) & 1, e = k & 7;
-  return static_cast<size_t>(((rb * KS + ks) * 2 + h) * kTcImgElems) + g * 128 + j * 64 + rr * 8 + e;
+  return static_cast<size_t>(((rb * KS + ks) * nimg + h) * kTcImgElems) + g * 128 + j * 64 + rr * 8 + e;
 }
+// BF16 terms per operand value for a tensor-core precision (1: BF16, 2: hi + lo, 3: hi + mid +
+// lo) and the products the reconstruction sums: every pair (a, b) of terms of order below the
+// last term's, i.e. all a + b <= nimg - 1 (1, 3 or 6 MMAs per K step).
+__host__ __device__ constexpr int tc_nimg(int precision) { return precision == 2 ? 1 : (precision == 3 ? 3 : 2); }
+__host__ __device__ constexpr int tc_npairs(int nimg) { return nimg * (nimg + 1) / 2; }
+// product p: terms (tc_pair_a(p), tc_pair_b(p)) in the order (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+__host__ __device__ constexpr int tc_pair_a(int p) { return (p == 2 || p == 4) ? 1 : (p == 5 ? 2 : 0); }
+__host__ __device__ constexpr int tc_pair_b(int p) { return (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0); }
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -227,7 +236,7 @@ struct TcDir {
 // hi and of the lo image); units in image order, grid-stride over all CTAs.
 static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir* dirs, __nv_bfloat16* const* kr, int pb,
                                   int Mk) {
-  const int KS = P.Kpad / 16, ksteps = (Mk + 15) / 16;
+  const int KS = P.Kpad / 16, ksteps = (Mk + 15) / 16, nimg = tc_nimg(P.precision);
   const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
   const long long t0 = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x;
   // unit u -> (row block, K step, group, core matrix, row in group)
@@ -238,16 +247,22 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
     i = (q / ksteps) * 128 + g * 8 + rr;
     k0 = ks * 16 + j * 8;
   };
+  // the BF16 terms of the split: t_0 = bf16(a), t_h = bf16(a - t_0 - .. - t_{h-1}) (each
+  // remainder is exact in FP32)
   auto store = [&](__nv_bfloat16* op, long long i, int k0, const float (&a)[8]) {
-    __align__(16) __nv_bfloat16 hi[8], lo[8];
+    float rem[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      hi[e] = __float2bfloat16_rn(a[e]);
-      lo[e] = __float2bfloat16_rn(a[e] - __bfloat162float(hi[e]));
+    for (int e = 0; e < 8; ++e) rem[e] = a[e];
+    const size_t o = tc_img_index(i, k0, 0, KS, nimg);
+    for (int h = 0; h < nimg; ++h) {
+      __align__(16) __nv_bfloat16 t[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        t[e] = __float2bfloat16_rn(rem[e]);
+        rem[e] -= __bfloat162float(t[e]);
+      }
+      *reinterpret_cast<uint4*>(op + o + static_cast<size_t>(h) * kTcImgElems) = *reinterpret_cast<const uint4*>(t);
     }
-    const size_t o = tc_img_index(i, k0, 0, KS);
-    *reinterpret_cast<uint4*>(op + o) = *reinterpret_cast<const uint4*>(hi);
-    *reinterpret_cast<uint4*>(op + o + kTcImgElems) = *reinterpret_cast<const uint4*>(lo);
   };
   if (ksteps == 0) return;
   // rows: the nodes (nodal rule, factors) or the Gauss points (Gauss rule, factors there)
@@ -384,11 +399,12 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     return __uint_as_float(tile_max[idx]) * on_scale > on_tol;
   };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int chunks = 2 * P.Kpad / kTcChunkElems;
+  const int nimg = tc_nimg(P.precision), npairs = tc_npairs(nimg);
+  const int chunks = nimg * P.Kpad / kTcChunkElems;
   const int ksteps = (Mk + 15) / 16;
   // a block's images of the K steps that hold modes: one contiguous bulk copy
-  const uint32_t load_bytes = 2u * ksteps * kTcImgBytes;
-  const size_t block_elems = static_cast<size_t>(P.Kpad / 16) * 2 * kTcImgElems;
+  const uint32_t load_bytes = static_cast<uint32_t>(nimg) * ksteps * kTcImgBytes;
+  const size_t block_elems = static_cast<size_t>(P.Kpad / 16) * nimg * kTcImgElems;
   const int wl_n = tmid < 0 ? ncols_pad : n_last_pad;
   const int wm_n = tmid < 0 ? 0 : P.d[tmid].nq;
   const TcLayout Ly = tc_layout(chunks, stages, wl_n, wm_n);
@@ -512,14 +528,12 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
           const uint32_t d = tmem_base + static_cast<uint32_t>((2 * ps + j) * kTcN);
           const uint32_t bs = b_base + static_cast<uint32_t>(s) * stage_bytes + j * load_bytes;
           for (int k = 0; k < ksteps; ++k) {
-            const uint32_t hi_off = (2 * k) * kTcImgBytes, lo_off = hi_off + kTcImgBytes;
-            const uint64_t ah = umma_desc_img(a_base + hi_off);
-            const uint64_t al = umma_desc_img(a_base + lo_off);
-            const uint64_t bh = umma_desc_img(bs + hi_off);
-            const uint64_t bl = umma_desc_img(bs + lo_off);
-            tc_mma(d, ah, bh, idesc, k > 0 ? 1u : 0u);
-            tc_mma(d, ah, bl, idesc, 1u);
-            tc_mma(d, al, bh, idesc, 1u);
+            const uint32_t off = static_cast<uint32_t>(k * nimg) * kTcImgBytes;
+            for (int p = 0; p < npairs; ++p) {
+              const uint64_t ad = umma_desc_img(a_base + off + tc_pair_a(p) * kTcImgBytes);
+              const uint64_t bd = umma_desc_img(bs + off + tc_pair_b(p) * kTcImgBytes);
+              tc_mma(d, ad, bd, idesc, (k > 0 || p > 0) ? 1u : 0u);
+            }
           }
         }
         tc_commit(&sh->b_empty[s]);

@@ -321,7 +321,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
   }
   trace_mark(P, tmark, kTrPrologue);
 
-  int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0, n_stalled = 0;
+  int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0, n_stalled = 0, sweeps_discarded = 0;
   double amp0 = 0.0;   // amplitude max|(x)v| of the step's leading mode
   bool stopped = false;
   const int n_modes = P.fixed_modes > 0 ? P.fixed_modes : P.M_max;
@@ -467,8 +467,8 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     sweeps_max = max(sweeps_max, it);
     if (!zero_mode && P.fixed_als == 0 && !(delta <= P.tol_als)) not_conv = 1;
     if (zero_mode) amp = 0.0;
-    if (P.fixed_modes == 0 && amp <= P.tol_enrich) { stopped = true; break; }
-    if (zero_mode) { stopped = true; break; }   // fixed-mode runs cannot commit a zero mode
+    if (P.fixed_modes == 0 && amp <= P.tol_enrich) { stopped = true; sweeps_discarded = it; break; }
+    if (zero_mode) { stopped = true; sweeps_discarded = it; break; }   // fixed-mode runs cannot commit a zero mode
     // commit with equal 2-norms in every factor
     double scale[kMaxDim], target = 1.0;
     for (int c = 0; c < D; ++c) target *= sqrt(norms2[c]);
@@ -495,6 +495,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     r.not_converged = not_conv;
     r.status = 0;
     r.als_stalled = n_stalled;
+    r.als_sweeps_committed = sweeps - sweeps_discarded;
     *P.stats = r;
   }
 }

@@ -799,10 +799,10 @@ __device__ __forceinline__ float cheb_pass_bound(float rho, int its, float kappa
   return 4.f * fmaxf(cheb, kappa * 5.960464477539063e-08f);
 }
 
-// Relative accuracy a solve stops at: 2^-46 of the iterate (the double-float limit) for the
+// Relative accuracy a solve stops at: 2^-48 of the iterate (the double-float limit) for the
 // FP64 path; 2^-34 for the tensor-core path, whose contraction carries FP32 rounding into
 // every right-hand side (2^-34 is 5.8e-11, far below that).
-constexpr float kSolveTolFp64 = 1.4210854715202004e-14f;
+constexpr float kSolveTolFp64 = 3.552713678800501e-15f;
 constexpr float kSolveTolMixed = 5.820766091346741e-11f;
 // Error reduction of a first refinement pass: 2^-22, unless the caller knows its warm start
 // to be closer (then tol over the expected relative change, at most 2^-8)

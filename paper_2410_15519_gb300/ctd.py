@@ -16,7 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libctd.so")
 
 PREC_FP64 = 0
-PREC_SPLIT_BF16 = 1
+PREC_SPLIT_BF16 = 1        # tensor cores, factors as hi + lo BF16 (3 products)
+PREC_BF16 = 2              # tensor cores, factors as one BF16 term (1 product)
+PREC_SPLIT3_BF16 = 3       # tensor cores, factors as hi + mid + lo BF16 (6 products)
 NONLINEAR_GRID = 0         # nonlinear term as the full nodal integral (Eq. KxxMxx)
 NONLINEAR_SEPARATED = 1    # separated form (Eq. MxySep) for steps with M_k <= 16
 QUAD_NODAL = 0             # mass-type integrals with the nodal rule (M = diag(omega))
@@ -43,7 +45,7 @@ class Config(ctypes.Structure):
 class StepStats(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("als_sweeps_max", ctypes.c_int),
                 ("capped", ctypes.c_int), ("not_converged", ctypes.c_int), ("status", ctypes.c_int),
-                ("als_stalled", ctypes.c_int)]
+                ("als_stalled", ctypes.c_int), ("als_sweeps_committed", ctypes.c_int)]
 
 
 class CTDError(RuntimeError):
@@ -210,7 +212,8 @@ def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True,
     for i in range(count):
         out.append([dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
                          capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
-                         als_stalled=r.als_stalled)
+                         als_stalled=r.als_stalled,
+                         als_sweeps_committed=r.als_sweeps_committed)
                     for r in rec[i * nsteps:(i + 1) * nsteps]])
     return out
 
@@ -273,7 +276,8 @@ class Solver:
         _check(self.lib, self.h, st, "ctd_step")
         return [dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
                      capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
-                         als_stalled=r.als_stalled) for r in rec]
+                         als_stalled=r.als_stalled,
+                         als_sweeps_committed=r.als_sweeps_committed) for r in rec]
 
     def energy(self) -> float:
         e = ctypes.c_double(0.0)

@@ -1,6 +1,6 @@
 // Host checks of two index tables of the step kernel:
-//  * tc_img_index (tensor-core contraction): per 128-row block and 16-wide K step a hi and a
-//    lo image of 128 x 16 BF16.  The map must be a bijection onto the images, and inside an
+//  * tc_img_index (tensor-core contraction): per 128-row block and 16-wide K step one image
+//    of 128 x 16 BF16 per term of the split (1 to 3).  The map must be a bijection onto the images, and inside an
 //    image it must be the canonical K-major layout without swizzle that the shared-memory
 //    descriptors declare: 8 x 8 core matrices with rows 16 bytes apart, the second core
 //    matrix along K 128 bytes after the first (leading byte offset) and the next group of 8
@@ -22,21 +22,21 @@ static void fail(const char* what, long long a, long long b, long long c) {
   ++failures;
 }
 
-static void check_images(int nrb, int KS) {
+static void check_images(int nrb, int KS, int nimg) {
   using namespace ctd;
-  const size_t total = static_cast<size_t>(nrb) * KS * 2 * kTcImgElems;
+  const size_t total = static_cast<size_t>(nrb) * KS * nimg * kTcImgElems;
   std::vector<int> seen(total, 0);
   for (long long i = 0; i < 128LL * nrb; ++i)
     for (int k = 0; k < 16 * KS; ++k)
-      for (int h = 0; h < 2; ++h) {
-        const size_t idx = tc_img_index(i, k, h, KS);
+      for (int h = 0; h < nimg; ++h) {
+        const size_t idx = tc_img_index(i, k, h, KS, nimg);
         if (idx >= total) {
           fail("range", i, k, static_cast<long long>(idx));
           continue;
         }
         ++seen[idx];
-        // image of (row block, K step, hi/lo), then the byte offset inside it
-        const size_t img = static_cast<size_t>(((i >> 7) * KS + (k >> 4)) * 2 + h);
+        // image of (row block, K step, BF16 term), then the byte offset inside it
+        const size_t img = static_cast<size_t>(((i >> 7) * KS + (k >> 4)) * nimg + h);
         const long long off = 2LL * static_cast<long long>(idx - img * kTcImgElems);
         const int r = static_cast<int>(i & 127), kk = k & 15;
         const long long want = (r >> 3) * 256LL + (kk >> 3) * 128LL + (r & 7) * 16LL + (kk & 7) * 2LL;
@@ -77,7 +77,22 @@ int main() {
   const int blocks[] = {1, 2, 3};
   const int ksteps[] = {1, 2, 3, 5};
   for (int nrb : blocks)
-    for (int KS : ksteps) check_images(nrb, KS);
+    for (int KS : ksteps)
+      for (int nimg = 1; nimg <= 3; ++nimg) check_images(nrb, KS, nimg);
+  // the products of the tensor-core precisions: every pair of term orders summing to at most
+  // nimg - 1, each once, the leading product first
+  using namespace ctd;
+  for (int nimg = 1; nimg <= 3; ++nimg) {
+    int seen[3][3] = {};
+    for (int p = 0; p < tc_npairs(nimg); ++p) {
+      const int a = tc_pair_a(p), b = tc_pair_b(p);
+      if (a + b > nimg - 1) fail("pair order", nimg, a, b);
+      ++seen[a][b];
+    }
+    for (int a = 0; a < nimg; ++a)
+      for (int b = 0; a + b < nimg; ++b)
+        if (seen[a][b] != 1) fail("pair", nimg, a, b);
+  }
   check_sep_table();
   if (failures) {
     std::printf("%d failures\n", failures);

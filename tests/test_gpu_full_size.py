@@ -56,6 +56,7 @@ def test_c1_first_step_matches_oracle(lib, c1_oracle, prec, tol):
         # side that has cancelled to that level, which magnifies the last-bit difference of
         # FP64 and the 48-bit double-float solves.  The field above is unaffected (1e-12).
         assert st_g["modes"] == st_o["modes"]
+        assert st_g["als_sweeps_committed"] == sum(st_o["als_iters"][:st_o["modes"]])
         assert abs(st_g["als_sweeps"] - sum(st_o["als_iters"])) <= 1
 
 
@@ -125,7 +126,10 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
     # The full 3D configurations: the split-BF16 tensor-core form against the plain FP64 form
     # on the GPU (the oracle cannot hold these grids).
     # (1) Same schedule (fixed mode count and sweeps, the strict-parity mode): the fields differ
-    #     only by the arithmetic, within the mixed-precision bar 1e-5.
+    #     only by the arithmetic.  The three-term split (hi + mid + lo) is within the
+    #     mixed-precision bar 1e-5 on both; the two-term split on c3 too, while on c2, where
+    #     the tanh interface mode puts u = +-1 over most of the domain (w ~ 0 but |w'| = 2),
+    #     its 2^-15 reconstruction error leaves 1e-4.
     # (2) Free running under the same stop rules: the greedy decisions may differ where a mode's
     #     amplitude sits at the enrichment threshold tol_enrich = 1e-4, so the fields agree to
     #     that truncation level; the energy decreases in both.
@@ -133,7 +137,7 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
     A0 = workloads.initial_modes(w)
 
     def run(prec, nsteps, **over):
-        p = lib.PREC_FP64 if prec == "fp64" else lib.PREC_SPLIT_BF16
+        p = {"fp64": lib.PREC_FP64, "mixed": lib.PREC_SPLIT_BF16, "split3": lib.PREC_SPLIT3_BF16}[prec]
         s = lib.Solver(lib.config_from_workload(w, precision=p, **over))
         s.set_initial_modes(A0)
         E = [s.energy()]
@@ -147,10 +151,11 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
 
     fixed = dict(fixed_modes=12, fixed_als_iters=6)
     G64, E64, _ = run("fp64", 1, **fixed)
-    Gmx, Emx, _ = run("mixed", 1, **fixed)
-    assert G64[0].shape[1] == Gmx[0].shape[1] == 12
-    assert field_rel_l2(Gmx, G64) < 1e-5
-    assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1])
+    for prec, bar in (("split3", 1e-5), ("mixed", 1e-5 if name == "c3" else 2e-4)):
+        Gmx, Emx, _ = run(prec, 1, **fixed)
+        assert G64[0].shape[1] == Gmx[0].shape[1] == 12
+        assert field_rel_l2(Gmx, G64) < bar, prec
+        assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1]), prec
     G64, E64, s64 = run("fp64", 2, als_stall_tol=1e-6)
     Gmx, Emx, smx = run("mixed", 2, als_stall_tol=1e-6)
     assert all(r["status"] >= 0 for r in s64 + smx)

@@ -328,3 +328,42 @@ def test_separated_form_falls_back_above_the_mode_limit():
     prob.separated_max_modes = 4
     assert ctd.nonlinear_operator(prob, ops, A)[0] == "separated"
     assert ctd.nonlinear_operator(prob, ops, [a[:, :0] for a in A])[0] == "grid"   # u^k = 0
+
+
+def test_stalled_3d_case_amplifies_last_bit_perturbations():
+    # Conditioning of the 3D case whose modes stall at I_max (the GPU parity test of the same
+    # case): perturbing every banded solve of the oracle by one unit in the last place moves its
+    # own field after three steps by far more than one unit -- the near-neutral sweep map carries
+    # the perturbation over 50 sweeps -- yet stays below 1e-12, the FP64 parity bar.
+    w = workloads.preset("c0", dim=3, n=(14, 11, 17), length=(1.0, 1.0, 1.0), eps=0.08, M_max=10, ic_rank=3)
+    prob = ctd.Problem(dim=w.dim, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa,
+                       a0=w.a0, alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+                       tol_enrich=w.tol_enrich, seed=w.seed)
+    ops = ctd.build_operators(prob)
+    orig = ctd.banded_spd_solve
+
+    def run(seed):
+        rng = np.random.default_rng(seed) if seed is not None else None
+
+        def solve(A, rhs):
+            x = orig(A, rhs)
+            return x if rng is None else x * (1.0 + 2.0 ** -52 * rng.uniform(-1.0, 1.0, size=x.shape))
+
+        ctd.banded_spd_solve = solve
+        try:
+            A = workloads.initial_modes(w)
+            hist = []
+            for k in range(3):
+                A, st = ctd.step(prob, ops, A, k)
+                hist.append(st["als_iters"])
+            return A, hist
+        finally:
+            ctd.banded_spd_solve = orig
+
+    A0, h0 = run(None)
+    errs = []
+    for seed in range(3):
+        A1, h1 = run(seed)
+        assert h1 == h0
+        errs.append(ctd.rel_l2_between(A1, A0))
+    assert max(errs) > 1e-14 and max(errs) < 1e-12, errs
