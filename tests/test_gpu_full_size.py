@@ -125,14 +125,15 @@ def field_rel_l2(A, B):
 def test_3d_whole_steps_mixed_vs_fp64(lib, name):
     # The full 3D configurations: the split-BF16 tensor-core form against the plain FP64 form
     # on the GPU (the oracle cannot hold these grids).
-    # (1) Same schedule (fixed mode count and sweeps, the strict-parity mode): the fields differ
-    #     only by the arithmetic.  The three-term split (hi + mid + lo) is within the
-    #     mixed-precision bar 1e-5 on both; the two-term split on c3 too, while on c2, where
-    #     the tanh interface mode puts u = +-1 over most of the domain (w ~ 0 but |w'| = 2),
-    #     its 2^-15 reconstruction error leaves 1e-4.
+    # (1) The same mode count (fixed_modes), every mode swept to its stop rules: the fields
+    #     differ by the arithmetic alone, within the mixed-precision bar 1e-5, for the hi + lo
+    #     and the hi + mid + lo splits.  (A fixed, unconverged sweep count is no measure of the
+    #     arithmetic: with 6 sweeps per mode the oracle's own c2 step moves by 1e-4 under a 1e-7
+    #     perturbation of its nonlinear term, tests/test_oracle_step.py.)
     # (2) Free running under the same stop rules: the greedy decisions may differ where a mode's
-    #     amplitude sits at the enrichment threshold tol_enrich = 1e-4, so the fields agree to
-    #     that truncation level; the energy decreases in both.
+    #     amplitude sits at the enrichment threshold tol_enrich = 1e-4 (the oracle's own c2 step
+    #     changes its mode count under a 1e-7 perturbation), so the fields agree to that
+    #     truncation level; the energy decreases in both.
     w = workloads.preset(name)
     A0 = workloads.initial_modes(w)
 
@@ -149,12 +150,12 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
         s.close()
         return G, E, st
 
-    fixed = dict(fixed_modes=12, fixed_als_iters=6)
+    fixed = dict(fixed_modes=12, als_stall_tol=1e-6)
     G64, E64, _ = run("fp64", 1, **fixed)
-    for prec, bar in (("split3", 1e-5), ("mixed", 1e-5 if name == "c3" else 2e-4)):
+    for prec in ("mixed", "split3"):
         Gmx, Emx, _ = run(prec, 1, **fixed)
         assert G64[0].shape[1] == Gmx[0].shape[1] == 12
-        assert field_rel_l2(Gmx, G64) < bar, prec
+        assert field_rel_l2(Gmx, G64) < 1e-5, prec
         assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1]), prec
     G64, E64, s64 = run("fp64", 2, als_stall_tol=1e-6)
     Gmx, Emx, smx = run("mixed", 2, als_stall_tol=1e-6)
