@@ -152,6 +152,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without the wait: the registers are valid only after tmem_wait_ld_tie on them
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+// Wait for this thread's outstanding TMEM loads; the registers are tied to the wait, so that no
+// use of them is scheduled before it (only the first of several waits in a row waits)
+__device__ __forceinline__ void tmem_wait_ld_tie(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
 // Shared-memory matrix descriptor of one tile image: K-major, no swizzle, core matrices
 // adjacent in K 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart (stride
 // byte offset).
@@ -577,13 +601,15 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");   // the epilogue warps only
     const uint32_t lane_base = tmem_base + (static_cast<uint32_t>((warp & 3) * 32) << 16);
-    double acc = 0.0;   // FP32 within a tile, FP64 across the tiles of a row block
+    // FP32 within a tile, double-float (two FP32 words, exact products) across the tiles of a
+    // row block: hundreds of tiles whose sums cancel would lose the FP32 sum's digits
+    dfloat acc = {0.f, 0.f};
     int cur_rb = -1;
     auto flush = [&](int rbf) {
       const int row = rbf * kTcM + r;
       if (!dump && row < nx) {
         const int j = cta - tile_owner(T, G, static_cast<long long>(rbf) * ntc);
-        rpart_tc[static_cast<size_t>(row) * cmax + j] = acc;
+        rpart_tc[static_cast<size_t>(row) * cmax + j] = static_cast<double>(acc.hi) + static_cast<double>(acc.lo);
       }
     };
     int rb = t0 / ntc, cb = t0 - rb * ntc;
@@ -592,7 +618,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       g = 1;
       if (rb != cur_rb) {
         if (cur_rb >= 0) flush(cur_rb);
-        acc = 0.0;
+        acc = {0.f, 0.f};
         cur_rb = rb;
       }
       if (!active(t)) continue;
@@ -614,30 +640,43 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
           wt = wl + (col0 - jm * n_last_pad);
           wscale = wm[jm];
         }
-        // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
-        // instruction; four interleaved sums (columns 0, 1, 2, 3 mod 4)
-        float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
-        const float2 m1 = make_float2(-1.f, -1.f);
+        // The tile row's 128 accumulator columns: four TMEM loads issued back to back, one wait
+        // (the load latency is exposed once per tile, not once per 32 columns)
         const uint32_t acol = static_cast<uint32_t>((2 * ps + j) * kTcN);
+        uint32_t vr[kTcN / 32][32];
+#pragma unroll
+        for (int q = 0; q < kTcN / 32; ++q) tmem_ld32_async(lane_base + acol + static_cast<uint32_t>(q * 32), vr[q]);
+#pragma unroll
+        for (int q = 0; q < kTcN / 32; ++q) tmem_wait_ld_tie(vr[q]);
+        if (dump) {
+          const int row = rb * kTcM + r;
+          for (int q = 0; q < kTcN / 32; ++q)
+            for (int c = 0; c < 32; ++c)
+              dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = __uint_as_float(vr[q][c]);
+        }
+        // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
+        // instruction; four interleaved packed sums
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float4* w4 = reinterpret_cast<const float4*>(wt);
 #pragma unroll
         for (int q = 0; q < kTcN / 32; ++q) {
-          float v[32];
-          tmem_ld32(lane_base + acol + static_cast<uint32_t>(q * 32), v);
-          if (dump) {
-            const int row = rb * kTcM + r;
-            for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = v[c];
-          }
-          const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float4 ww = w4[c];
-            const float2 u01 = make_float2(v[4 * c], v[4 * c + 1]), u23 = make_float2(v[4 * c + 2], v[4 * c + 3]);
-            a01 = __ffma2_rn(__fmul2_rn(u01, __ffma2_rn(u01, u01, m1)), make_float2(ww.x, ww.y), a01);
-            a23 = __ffma2_rn(__fmul2_rn(u23, __ffma2_rn(u23, u23, m1)), make_float2(ww.z, ww.w), a23);
+          for (int c = 0; c < 8; c += 2) {
+            const float4 wa = w4[q * 8 + c], wb = w4[q * 8 + c + 1];
+            const float2 u0 = make_float2(__uint_as_float(vr[q][4 * c]), __uint_as_float(vr[q][4 * c + 1]));
+            const float2 u1 = make_float2(__uint_as_float(vr[q][4 * c + 2]), __uint_as_float(vr[q][4 * c + 3]));
+            const float2 u2 = make_float2(__uint_as_float(vr[q][4 * c + 4]), __uint_as_float(vr[q][4 * c + 5]));
+            const float2 u3 = make_float2(__uint_as_float(vr[q][4 * c + 6]), __uint_as_float(vr[q][4 * c + 7]));
+            a0 = __ffma2_rn(__fmul2_rn(u0, __ffma2_rn(u0, u0, m1)), make_float2(wa.x, wa.y), a0);
+            a1 = __ffma2_rn(__fmul2_rn(u1, __ffma2_rn(u1, u1, m1)), make_float2(wa.z, wa.w), a1);
+            a2 = __ffma2_rn(__fmul2_rn(u2, __ffma2_rn(u2, u2, m1)), make_float2(wb.x, wb.y), a2);
+            a3 = __ffma2_rn(__fmul2_rn(u3, __ffma2_rn(u3, u3, m1)), make_float2(wb.z, wb.w), a3);
           }
         }
-        const float at = (a01.x + a01.y) + (a23.x + a23.y);
-        acc = fma(static_cast<double>(wscale), static_cast<double>(at), acc);
+        const float at = ((a0.x + a0.y) + (a1.x + a1.y)) + ((a2.x + a2.y) + (a3.x + a3.y));
+        const float pr = wscale * at;
+        acc = df_add(acc, dfloat{pr, __fmaf_rn(wscale, at, -pr)});
       }
       tc_fence_before();
       mbar_arrive(&sh->acc_empty[ps]);
