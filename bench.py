@@ -421,6 +421,10 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
     hs = sum(s["als_sweeps"] for s in st_tr) * w.dim
     out["phase_us_per_half_sweep"] = {k: 1e6 * v / max(1, hs) for k, v in tr.items()
                                       if k in ("gram_contract", "gram", "contract", "rhs", "solve", "converge")}
+    if tr.get("tc_tiles", 0) > 0:
+        # the tensor-core contraction's roles on the traced (last) CTA, SM cycles per tile
+        out["contraction_role_cycles_per_tile"] = {
+            k[3:-7]: v / tr["tc_tiles"] for k, v in tr.items() if k.startswith("tc_") and k.endswith("_cycles")}
     if headline:
         # end to end through the C ABI with host buffers: H2D of u^k, step, D2H of u^{k+1}
         n_e2e = min(steps, args.e2e_steps)
@@ -535,7 +539,8 @@ def single_line(w, res, args, pk, pk_kind, world, headline=True):
             "als_sweeps_per_step": [s["als_sweeps"] for s in res["stats"]],
             "als_stalled_per_step": [s["als_stalled"] for s in res["stats"]],
             "half_sweeps_per_s": sum(s["als_sweeps"] for s in res["stats"]) * w.dim / (total_ms / 1e3),
-            "phase_us_per_half_sweep": res["phase_us_per_half_sweep"], "roofline": roof,
+            "phase_us_per_half_sweep": res["phase_us_per_half_sweep"],
+            "contraction_role_cycles_per_tile": res.get("contraction_role_cycles_per_tile"), "roofline": roof,
             "accuracy": res["accuracy"], "precision_ladder": res.get("ladder", {})}
     ph = res["phase_us_per_half_sweep"]
     if args.precision != "fp64" and ph.get("contract"):

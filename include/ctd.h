@@ -272,8 +272,11 @@ ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out);
  * 5 convergence test, 6 mode commit; inside the banded solve: 8 set-up, 9 first pass,
  * 10 refinement, 11 refinement passes (a count, in units of 1e-9), 14 double-float
  * residuals, 15 inner FP32 solves; 12 Gram products, 13 contraction (timed on the last CTA,
- * whose tile share is a full one; every other slot on CTA 0).  Also counts
- * ctd_probe_solve.  Synchronises. */
+ * whose tile share is a full one; every other slot on CTA 0); tensor-core contraction roles on
+ * that last CTA, in SM clock cycles (read as seconds x 1e9): 16 producer waiting for a free
+ * stage, 17 MMA issuer waiting for operands, 18 MMA issuer waiting for a free accumulator,
+ * 19 MMA issue, 20 epilogue (its first warp) waiting for an accumulator, 21 epilogue work,
+ * 22 tiles contracted (a count).  Also counts ctd_probe_solve.  Synchronises. */
 ctd_status ctd_probe_trace(ctd_handle h, int enable, double* seconds, int nslots);
 
 #ifdef __cplusplus

@@ -114,7 +114,12 @@ struct StepParams {
 // phases accumulated in StepParams::trace (each includes its closing grid barrier)
 enum TracePhase { kTrPrologue = 0, kTrInit, kTrGramContract, kTrRhs, kTrSolve, kTrConverge, kTrCommit,
                   kTrSolveFactor = 8, kTrSolveFirst, kTrSolveRefine, kTrSolvePasses, kTrGram, kTrContract,
-                  kTrSolveResidual, kTrSolveInner, kTrSlots = 16 };
+                  kTrSolveResidual, kTrSolveInner,
+                  // tensor-core contraction roles on the traced CTA, SM clock cycles: producer waiting
+                  // for a free stage, MMA issuer waiting for operands / for a free accumulator and
+                  // issuing, epilogue waiting for an accumulator and working, tiles contracted
+                  kTrTcProdWait = 16, kTrTcMmaWaitB, kTrTcMmaWaitAcc, kTrTcMmaIssue, kTrTcEpiWait, kTrTcEpiWork,
+                  kTrTcTiles, kTrSlots = 24 };
 
 // ------------------------------------------------------------------ time & barrier
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -152,30 +152,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// The same load without the wait: the registers are valid only after tmem_wait_ld_tie on them
-__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-// Wait for this thread's outstanding TMEM loads; the registers are tied to the wait, so that no
-// use of them is scheduled before it (only the first of several waits in a row waits)
-__device__ __forceinline__ void tmem_wait_ld_tie(uint32_t (&r)[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-               :
-               : "memory");
-}
-
 // Shared-memory matrix descriptor of one tile image: K-major, no swizzle, core matrices
 // adjacent in K 128 bytes apart (leading byte offset), 8-row groups 256 bytes apart (stride
 // byte offset).
@@ -441,6 +417,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   const int t0 = tile_lo(T, G, cta), t1 = tile_lo(T, G, cta + 1);
   const unsigned long long lim = P.wait_ns;
   const uint32_t stage_bytes = static_cast<uint32_t>(chunks) * kTcChunkBytes;
+  // role timing (SM cycles) on the traced CTA: the last one, whose tile share is a full one
+  unsigned long long* const tr = (P.trace && cta == G - 1) ? P.trace : nullptr;
+  long long t_wait = 0, t_wait2 = 0, t_work = 0;
 
   if (threadIdx.x == 0) {
     mbar_init(&sh->a_full, 1);
@@ -503,7 +482,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         ++a_loads;
         cur_rb = rb;
       }
+      const long long c0 = tr ? clock64() : 0;
       if (gi >= stages && !warp_wait(&sh->b_empty[s], (round - 1) & 1, lim, st, abort_flag, 22)) { ok = false; break; }
+      if (tr) t_wait += clock64() - c0;
       if (lane == 0) {
         mbar_expect_tx(&sh->b_full[s], g * load_bytes);
         for (int j = 0; j < g; ++j)
@@ -515,6 +496,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       if (++s == stages) { s = 0; ++round; }
     }
     if (!ok && lane == 0) sh->abort = 1;
+    if (tr && lane == 0) atomicAdd(tr + kTrTcProdWait, static_cast<unsigned long long>(t_wait));
   } else if (warp == 1) {
     // ---------------- MMA issuer
     const uint32_t idesc = umma_idesc_bf16();
@@ -531,12 +513,16 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         ++a_uses;
         cur_rb = rb;
       }
+      const long long c0 = tr ? clock64() : 0;
       if (!warp_wait(&sh->b_full[s], round & 1, lim, st, abort_flag, 24)) { ok = false; break; }
+      const long long c1 = tr ? clock64() : 0;
       const int ps = gi & 1;   // accumulator pair
       if (gi >= 2 && !warp_wait(&sh->acc_empty[ps], ((gi >> 1) - 1) & 1, lim, st, abort_flag, 25)) {
         ok = false;
         break;
       }
+      const long long c2 = tr ? clock64() : 0;
+      if (tr) { t_wait += c1 - c0; t_wait2 += c2 - c1; }
       tc_fence_after();
       // is this the row block's last contracted group (then its A block is released)?
       bool last_in_rb;
@@ -565,9 +551,16 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         if (last_in_rb) tc_commit(&sh->a_empty);
       }
       __syncwarp();
+      if (tr) t_work += clock64() - c2;
       ++gi;
       n_g = gi;
       if (++s == stages) { s = 0; ++round; }
+    }
+    if (tr && lane == 0) {
+      atomicAdd(tr + kTrTcMmaWaitB, static_cast<unsigned long long>(t_wait));
+      atomicAdd(tr + kTrTcMmaWaitAcc, static_cast<unsigned long long>(t_wait2));
+      atomicAdd(tr + kTrTcMmaIssue, static_cast<unsigned long long>(t_work));
+      atomicAdd(tr + kTrTcTiles, static_cast<unsigned long long>(t1 - t0));
     }
     if (!ok) {
       if (lane == 0) sh->abort = 1;
@@ -626,7 +619,9 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       const int ps = gi & 1;
       // each lane leaves its wait on its own; the TMEM loads below are warp-collective
       // (.sync.aligned), so the warp reconverges (and agrees on the outcome) first
+      const long long c0 = tr ? clock64() : 0;
       if (!warp_wait(&sh->acc_full[ps], (gi >> 1) & 1, lim, st, abort_flag, 28)) { ok = false; break; }
+      const long long c1 = tr ? clock64() : 0;
       ++gi;
       tc_fence_after();
       for (int j = 0; j < g; ++j) {
@@ -640,49 +635,42 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
           wt = wl + (col0 - jm * n_last_pad);
           wscale = wm[jm];
         }
-        // The tile row's 128 accumulator columns: four TMEM loads issued back to back, one wait
-        // (the load latency is exposed once per tile, not once per 32 columns)
-        const uint32_t acol = static_cast<uint32_t>((2 * ps + j) * kTcN);
-        uint32_t vr[kTcN / 32][32];
-#pragma unroll
-        for (int q = 0; q < kTcN / 32; ++q) tmem_ld32_async(lane_base + acol + static_cast<uint32_t>(q * 32), vr[q]);
-#pragma unroll
-        for (int q = 0; q < kTcN / 32; ++q) tmem_wait_ld_tie(vr[q]);
-        if (dump) {
-          const int row = rb * kTcM + r;
-          for (int q = 0; q < kTcN / 32; ++q)
-            for (int c = 0; c < 32; ++c)
-              dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = __uint_as_float(vr[q][c]);
-        }
         // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
-        // instruction; four interleaved packed sums
-        float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+        // instruction; four interleaved sums (columns 0, 1, 2, 3 mod 4)
+        float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
         const float2 m1 = make_float2(-1.f, -1.f);
-        const float4* w4 = reinterpret_cast<const float4*>(wt);
+        const uint32_t acol = static_cast<uint32_t>((2 * ps + j) * kTcN);
 #pragma unroll
         for (int q = 0; q < kTcN / 32; ++q) {
+          float v[32];
+          tmem_ld32(lane_base + acol + static_cast<uint32_t>(q * 32), v);
+          if (dump) {
+            const int row = rb * kTcM + r;
+            for (int c = 0; c < 32; ++c) dump[static_cast<size_t>(row) * ncols_pad + col0 + q * 32 + c] = v[c];
+          }
+          const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
 #pragma unroll
-          for (int c = 0; c < 8; c += 2) {
-            const float4 wa = w4[q * 8 + c], wb = w4[q * 8 + c + 1];
-            const float2 u0 = make_float2(__uint_as_float(vr[q][4 * c]), __uint_as_float(vr[q][4 * c + 1]));
-            const float2 u1 = make_float2(__uint_as_float(vr[q][4 * c + 2]), __uint_as_float(vr[q][4 * c + 3]));
-            const float2 u2 = make_float2(__uint_as_float(vr[q][4 * c + 4]), __uint_as_float(vr[q][4 * c + 5]));
-            const float2 u3 = make_float2(__uint_as_float(vr[q][4 * c + 6]), __uint_as_float(vr[q][4 * c + 7]));
-            a0 = __ffma2_rn(__fmul2_rn(u0, __ffma2_rn(u0, u0, m1)), make_float2(wa.x, wa.y), a0);
-            a1 = __ffma2_rn(__fmul2_rn(u1, __ffma2_rn(u1, u1, m1)), make_float2(wa.z, wa.w), a1);
-            a2 = __ffma2_rn(__fmul2_rn(u2, __ffma2_rn(u2, u2, m1)), make_float2(wb.x, wb.y), a2);
-            a3 = __ffma2_rn(__fmul2_rn(u3, __ffma2_rn(u3, u3, m1)), make_float2(wb.z, wb.w), a3);
+          for (int c = 0; c < 8; ++c) {
+            const float4 ww = w4[c];
+            const float2 u01 = make_float2(v[4 * c], v[4 * c + 1]), u23 = make_float2(v[4 * c + 2], v[4 * c + 3]);
+            a01 = __ffma2_rn(__fmul2_rn(u01, __ffma2_rn(u01, u01, m1)), make_float2(ww.x, ww.y), a01);
+            a23 = __ffma2_rn(__fmul2_rn(u23, __ffma2_rn(u23, u23, m1)), make_float2(ww.z, ww.w), a23);
           }
         }
-        const float at = ((a0.x + a0.y) + (a1.x + a1.y)) + ((a2.x + a2.y) + (a3.x + a3.y));
+        const float at = (a01.x + a01.y) + (a23.x + a23.y);
         const float pr = wscale * at;
         acc = df_add(acc, dfloat{pr, __fmaf_rn(wscale, at, -pr)});
       }
       tc_fence_before();
       mbar_arrive(&sh->acc_empty[ps]);
+      if (tr) { t_wait += c1 - c0; t_work += clock64() - c1; }
     }
     if (ok && cur_rb >= 0) flush(cur_rb);
     if (!ok) sh->abort = 1;
+    if (tr && warp == 4 && lane == 0) {
+      atomicAdd(tr + kTrTcEpiWait, static_cast<unsigned long long>(t_wait));
+      atomicAdd(tr + kTrTcEpiWork, static_cast<unsigned long long>(t_work));
+    }
   }
   __syncthreads();
   return !(*abort_flag);

@@ -341,12 +341,16 @@ class Solver:
     def trace(self, enable: bool = True) -> dict:
         """Seconds per step-kernel phase accumulated since the last call; (re)starts or stops
         accumulation."""
-        out = np.zeros(16)
-        _check(self.lib, self.h, self.lib.ctd_probe_trace(self.h, 1 if enable else 0, out.ctypes.data, 16),
+        out = np.zeros(24)
+        _check(self.lib, self.h, self.lib.ctd_probe_trace(self.h, 1 if enable else 0, out.ctypes.data, 24),
                "probe_trace")
         d = dict(zip(self.TRACE_PHASES, out[:len(self.TRACE_PHASES)].tolist()))
         d.update(solve_factor=out[8], solve_first=out[9], solve_refine=out[10], solve_passes=out[11] * 1e9,
                  gram=out[12], contract=out[13], solve_residual=out[14], solve_inner=out[15])
+        # tensor-core contraction roles on the traced CTA, in SM clock cycles
+        for k, name in enumerate(("tc_producer_wait", "tc_mma_wait_operands", "tc_mma_wait_accumulator",
+                                  "tc_mma_issue", "tc_epilogue_wait", "tc_epilogue_work", "tc_tiles")):
+            d[name + ("" if name == "tc_tiles" else "_cycles")] = out[16 + k] * 1e9
         return d
 
     def probe_solve(self, x: int, alpha1: float, alpha2: float, q: np.ndarray) -> np.ndarray:
