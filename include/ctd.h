@@ -116,6 +116,23 @@ typedef struct {
                                quad_q (n[d] - 1) <= 12288 for every direction
                                (CTD_ERR_UNSUPPORTED otherwise); ctd_step_batch refuses it.   */
   int quad_q;               /* Gauss points per element (CTD_QUAD_GAUSS)                     */
+  int actd_Mc;              /* > 0: adaptive CTD (Section 3.3, "Adaptivity") with critical mode
+                               count M_c = actd_Mc: each step runs the greedy loop with the mode
+                               budget min(M_max, M_c + 1); a step that commits an (M_c + 1)-th
+                               mode discards its separated result and is solved instead on the
+                               full tensor-product C-FEM space by fast diagonalisation (the
+                               generalised eigenpairs K_d V_d = M_d V_d Lambda_d of every
+                               dimension, computed at ctd_create), and the field is then held as
+                               the full-grid array of its nodal values; the next step runs CTD
+                               from that array (its right-hand side c_t M u^k - int N~ L w(u^k)
+                               is one full-grid term, its modes start from the SplitMix64
+                               vectors).  0: off.  Requires CTD_PREC_FP64, the nodal rule, the
+                               grid nonlinear form and reduced_tol 0 (CTD_ERR_UNSUPPORTED
+                               otherwise); ctd_step_batch refuses it.  Uses cuBLAS (FP64 GEMMs
+                               of the transforms) and cuSOLVER (the eigenpairs, at create), whose
+                               handles allocate their own device memory: the exception to the
+                               no-allocation convention above.  ctd_step synchronises after
+                               every step to read the switch decision.                        */
 } ctd_config;
 
 enum { CTD_NONLINEAR_GRID = 0, CTD_NONLINEAR_SEPARATED = 1 };
@@ -131,6 +148,8 @@ typedef struct {
   int als_stalled;          /* modes whose sweeps the stall rule ended (als_stall_tol)      */
   int als_sweeps_committed; /* sweeps of the committed modes (als_sweeps less those of a mode
                                that the enrichment test discarded)                          */
+  int actd_switched;        /* 1 if the step was solved on the full grid (actd_Mc > 0); then
+                               modes is the count the greedy loop reached (M_c + 1)          */
 } ctd_step_stats;
 
 typedef struct ctd_ctx* ctd_handle;
@@ -182,9 +201,16 @@ ctd_status ctd_energy(ctd_handle h, double* energy);
 
 /* Copy the current field's factors out: *rank receives M; if M <= capacity, factor d is
  * written column-major into modes_out[d] (n[d] x capacity leading dimension n[d]).
- * Returns CTD_ERR_ARG with *rank set if capacity < M.  Synchronises. */
+ * Returns CTD_ERR_ARG with *rank set if capacity < M.  A field held on the full grid (after an
+ * adaptive-CTD full-grid step) has no factors: CTD_ERR_STATE (read it with ctd_get_field).
+ * Synchronises. */
 ctd_status ctd_get_modes(ctd_handle h, int capacity, int* rank, double* const* modes_out,
                          int on_device);
+
+/* Full-grid nodal values of the current field (row-major, n[0] x n[1] (x n[2]) doubles, host
+ * or device pointer by on_device): rebuilt from the factors, or copied from the full-grid
+ * array an adaptive-CTD step left (actd_Mc > 0).  Synchronises. */
+ctd_status ctd_get_field(ctd_handle h, double* out, int on_device);
 
 /* Release the handle (not the caller's workspace).  Waits for queued work. */
 void ctd_destroy(ctd_handle h);

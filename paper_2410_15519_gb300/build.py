@@ -18,7 +18,14 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctd.so")
 
-SOURCES = ["cfem_host.cpp", "ctd_kernels.cu", "ctd_kernels_sep.cu", "ctd_api.cu"]
+SOURCES = ["cfem_host.cpp", "ctd_kernels.cu", "ctd_kernels_sep.cu", "ctd_actd.cu", "ctd_api.cu"]
+# cuBLAS and cuSOLVER serve the adaptive-CTD full-grid step (FP64 GEMMs, eigenpairs at create)
+LIBS = ["-lcublas", "-lcusolver"]
+
+
+def _cuda_lib_dirs():
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
+    return [d for d in (os.path.join(root, "lib64"), os.path.join(root, "lib")) if os.path.isdir(d)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -59,7 +66,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+    rpath = [f"-Xlinker=-rpath,{d}" for d in _cuda_lib_dirs()]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, *LIBS, *rpath]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

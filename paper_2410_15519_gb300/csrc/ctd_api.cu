@@ -13,6 +13,7 @@
 
 #include "ctd.h"
 #include "cfem_host.h"
+#include "ctd_actd.h"
 #include "ctd_kernels.h"
 
 using ctd::Dim;
@@ -128,7 +129,7 @@ Plan make_plan(const ctd_config& c, int grid) {
 // Lay out every workspace piece; fills P and X pointers when base != null.
 size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Extra* X,
              float2** kc_store, float2** mc_store, double** energy_part, double** energy_gram,
-             StepStatsDev** stats) {
+             StepStatsDev** stats, ctd::ActdState* actd) {
   Carver cv(base);
   StepParams p{};
   Extra x{};
@@ -188,6 +189,23 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   p.solver = cv.take<float>(crf);
   p.xsol_g = cv.take<float2>(ctd::kMaxN);
   p.W = (c.precision == CTD_PREC_FP64) ? cv.take<double>(static_cast<size_t>(pl.N)) : nullptr;
+  p.U = nullptr;
+  if (c.actd_Mc > 0) {
+    // adaptive CTD: the full-grid field, a full-grid scratch, eigenpairs, eigensolver scratch
+    ctd::ActdState a;
+    p.U = cv.take<double>(static_cast<size_t>(pl.N));
+    a.Y = cv.take<double>(static_cast<size_t>(pl.N));
+    int nm = 0;
+    for (int d = 0; d < D; ++d) {
+      a.V[d] = cv.take<double>(static_cast<size_t>(pl.n[d]) * pl.n[d]);
+      a.lam[d] = cv.take<double>(pl.n[d]);
+      nm = std::max(nm, pl.n[d]);
+    }
+    a.work_len = ctd::actd_work_doubles(nm);
+    a.work = cv.take<double>(a.work_len);
+    a.info = cv.take<int>(64);
+    if (actd) *actd = a;
+  }
   p.barrier = cv.take<unsigned>(64);
   p.tile_max = cv.take<unsigned>(static_cast<size_t>(pl.n_pad[0] / ctd::kTcM) * (pl.n_pad[1] / ctd::kTcN));
   p.trace = cv.take<unsigned long long>(ctd::kTrSlots);
@@ -244,6 +262,10 @@ ctd_status validate(const ctd_config* c) {
   if (c->nonlinear_form == CTD_NONLINEAR_SEPARATED && (c->reduced_tol > 0.0 || c->M_max > ctd::kMaxSepModes))
     return CTD_ERR_ARG;
   if (c->quad_rule != CTD_QUAD_NODAL && c->quad_rule != CTD_QUAD_GAUSS) return CTD_ERR_ARG;
+  if (c->actd_Mc < 0) return CTD_ERR_ARG;
+  if (c->actd_Mc > 0 && (c->precision != CTD_PREC_FP64 || c->quad_rule != CTD_QUAD_NODAL ||
+                         c->nonlinear_form != CTD_NONLINEAR_GRID || c->reduced_tol > 0.0))
+    return CTD_ERR_UNSUPPORTED;
   if (c->quad_rule == CTD_QUAD_GAUSS) {
     if (c->quad_q < 1 || c->quad_q > ctd::kMaxGaussPoints) return CTD_ERR_ARG;
     if (c->nonlinear_form != CTD_NONLINEAR_GRID || c->reduced_tol > 0.0) return CTD_ERR_UNSUPPORTED;
@@ -303,6 +325,7 @@ struct ctd_ctx {
   std::vector<double> gphi[3];   // Gauss rule: shape function values at the points [nq][2s+2]
   std::vector<int> gcol0[3];     // and their first nodes
   std::vector<double> gwq[3];    // and the weights of the points
+  ctd::ActdState actd;           // adaptive CTD: library handles, eigenpairs, scratch
   double* energy_part;
   double* energy_gram;
   StepStatsDev* stats_dev;
@@ -375,7 +398,7 @@ ctd_status ctd_workspace_size(const ctd_config* cfg, size_t* bytes) {
   // every grid size 1..kGridMax fits (rpart_tc depends on the split of tiles over CTAs)
   for (int g : {1, 2, 4, 8, 16, 32, 64, 128, 132, 144, 148, 152, 160, 256, kGridMax}) {
     const Plan pl = make_plan(*cfg, g);
-    best = std::max(best, carve(*cfg, pl, nullptr, nullptr, nullptr, kc, mc, &ep, &eg, &sd));
+    best = std::max(best, carve(*cfg, pl, nullptr, nullptr, nullptr, kc, mc, &ep, &eg, &sd, nullptr));
   }
   *bytes = best + static_cast<size_t>(2) * kGridMax * ctd::kMaxN * sizeof(float);
   return CTD_OK;
@@ -431,7 +454,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   h->grid = grid;
   h->plan = make_plan(*cfg, grid);
   carve(*cfg, h->plan, workspace, &h->P, &h->X, h->kc_store, h->mc_store, &h->energy_part, &h->energy_gram,
-        &h->stats_dev);
+        &h->stats_dev, &h->actd);
   h->P.vgrid = grid;   // each CTA sets its own rank in its shared-memory copy
   h->P.vrank = 0;
 
@@ -439,6 +462,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   Extra& X = h->X;
   P.dim = cfg->dim;
   P.quad = h->plan.quad;
+  P.actd_Mc = cfg->actd_Mc;
   P.quad_q = h->plan.quad ? cfg->quad_q : 1;
   P.Mcap = h->plan.Mcap;
   P.Kpad = h->plan.Kpad;
@@ -623,6 +647,23 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     if (cfg->precision != CTD_PREC_FP64) need = std::max(need, static_cast<size_t>(optin) / 2 + 1024);
     P.smem_bytes = static_cast<int>(need);
   }
+  if (cfg->actd_Mc > 0) {
+    // the omega and band uploads above read host vectors that live in the handle
+    const double* kb[3] = {nullptr, nullptr, nullptr};
+    const double* om[3] = {nullptr, nullptr, nullptr};
+    for (int d = 0; d < cfg->dim; ++d) {
+      kb[d] = h->kband[d].data();
+      om[d] = h->omega[d].data();
+    }
+    const char* msg = "";
+    const int rc = ctd::actd_setup(h->actd, P, kb, om, h->stream, &msg);
+    if (rc != 0) {
+      ctd_status s = fail(h, static_cast<ctd_status>(rc), msg);
+      ctd::actd_release(h->actd);
+      delete h;
+      return s;
+    }
+  }
   InstState st{};
   CTD_CUDA(h, cudaMemcpyAsync(P.st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
   CTD_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -675,13 +716,36 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
   ctd_status worst = CTD_OK;
   std::vector<StepStatsDev> rec;
   int done = 0;
+  // adaptive CTD: one step at a time, the switch decision read back after each
+  const bool actd = h->P.actd_Mc > 0;
   while (done < nsteps) {
-    const int batch = std::min(nsteps - done, kStatsCap);
+    const int batch = actd ? 1 : std::min(nsteps - done, kStatsCap);
     for (int k = 0; k < batch; ++k) {
       h->P.stats = h->stats_dev + k;
       CTD_CUDA(h, cudaMemsetAsync(h->P.barrier, 0, sizeof(unsigned), h->stream));
       CTD_CUDA(h, h->P.nl_form == CTD_NONLINEAR_SEPARATED ? ctd::launch_step_sep(h->P, h->X, h->grid, h->stream)
                                                          : ctd::launch_step(h->P, h->X, h->grid, h->stream));
+    }
+    if (actd) {
+      InstState st;
+      ctd_status rs = read_state(h, &st);
+      if (rs != CTD_OK) return rs;
+      if (st.status) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "device status %d at wait %d", st.status, st.err_info);
+        return fail(h, status_from_bits(st.status), buf);
+      }
+      if (st.switched) {
+        // the step needs more than M_c modes: solve it on the full grid from u^k
+        const char* msg = "";
+        const int rc = ctd::actd_cfe_step(h->actd, h->P, st.grid, st.bank, st.Mk, h->stream, &msg);
+        if (rc != 0) return fail(h, static_cast<ctd_status>(rc), msg);
+        st.grid = 1;
+        st.Mk = 0;
+        st.switched = 0;
+        CTD_CUDA(h, cudaMemcpyAsync(h->P.st, &st, sizeof(st), cudaMemcpyHostToDevice, h->stream));
+        CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+      }
     }
     if (stats) {
       rec.resize(batch);
@@ -700,6 +764,7 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
         o.not_converged = rec[k].not_converged;
         o.als_stalled = rec[k].als_stalled;
         o.als_sweeps_committed = rec[k].als_sweeps_committed;
+        o.actd_switched = rec[k].actd_switched;
         o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
         if (o.status < 0) worst = static_cast<ctd_status>(o.status);
         else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -739,6 +804,7 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
     if (h->P.nl_form != CTD_NONLINEAR_GRID)
       return fail(h, CTD_ERR_UNSUPPORTED, "batched steps integrate the nonlinear term over the grid only");
     if (h->P.quad) return fail(h, CTD_ERR_UNSUPPORTED, "batched steps take the nodal rule only");
+    if (h->P.actd_Mc > 0) return fail(h, CTD_ERR_UNSUPPORTED, "batched steps do not switch to the full grid");
   }
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   // one entry per instance; the largest instances start first
@@ -787,6 +853,7 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
           o.not_converged = rec[k].not_converged;
           o.als_stalled = rec[k].als_stalled;
           o.als_sweeps_committed = rec[k].als_sweeps_committed;
+          o.actd_switched = rec[k].actd_switched;
           o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
           if (o.status < 0) worst = static_cast<ctd_status>(o.status);
           else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -809,10 +876,21 @@ ctd_status ctd_energy(ctd_handle h, double* energy) {
   if (rs != CTD_OK) return rs;
   if (st.status) return fail(h, status_from_bits(st.status), "device status set");
   const int Mk = st.Mk, D = h->cfg.dim;
-  CTD_CUDA(h, ctd::launch_convert_modes(h->P, h->X, st.bank, Mk, h->stream));
   int sms = 0;
   CTD_CUDA(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int eg = std::min(1024, 4 * sms);
+  if (st.grid) {
+    // adaptive CTD: the field is the full-grid array
+    CTD_CUDA(h, ctd::launch_energy_grid(h->P, h->P.U, h->energy_part, eg, h->stream));
+    std::vector<double> part(eg);
+    CTD_CUDA(h, cudaMemcpyAsync(part.data(), h->energy_part, sizeof(double) * eg, cudaMemcpyDeviceToHost, h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    double e = 0.0;
+    for (int g = 0; g < eg; ++g) e += part[g];
+    *energy = e;
+    return CTD_OK;
+  }
+  CTD_CUDA(h, ctd::launch_convert_modes(h->P, h->X, st.bank, Mk, h->stream));
   CTD_CUDA(h, ctd::launch_energy_bulk(h->P, h->X, Mk, h->energy_part, eg, h->stream));
   CTD_CUDA(h, ctd::launch_energy_gram(h->P, h->X, Mk, h->energy_gram, h->stream));
   std::vector<double> part(eg), gram(static_cast<size_t>(D) * 2 * Mk * Mk);
@@ -842,6 +920,10 @@ ctd_status ctd_get_modes(ctd_handle h, int capacity, int* rank, double* const* m
   InstState st;
   ctd_status rs = read_state(h, &st);
   if (rs != CTD_OK) return rs;
+  if (st.grid) {
+    *rank = 0;
+    return fail(h, CTD_ERR_STATE, "the field is held on the full grid (read it with ctd_get_field)");
+  }
   *rank = st.Mk;
   if (capacity < st.Mk) return fail(h, CTD_ERR_ARG, "capacity below rank");
   if (st.Mk == 0) return CTD_OK;
@@ -864,9 +946,57 @@ ctd_status ctd_get_modes(ctd_handle h, int capacity, int* rank, double* const* m
   return CTD_OK;
 }
 
+ctd_status ctd_get_field(ctd_handle h, double* out, int on_device) {
+  if (!h || !out) return CTD_ERR_ARG;
+  if (!h->has_modes) return fail(h, CTD_ERR_STATE, "no field set");
+  InstState st;
+  ctd_status rs = read_state(h, &st);
+  if (rs != CTD_OK) return rs;
+  size_t nodes = 1;   // the field's values at the nodes (also under the Gauss rule)
+  for (int d = 0; d < h->cfg.dim; ++d) nodes *= static_cast<size_t>(h->cfg.n[d]);
+  if (st.grid) {
+    CTD_CUDA(h, cudaMemcpyAsync(out, h->P.U, sizeof(double) * nodes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CTD_OK;
+  }
+  if (on_device) {
+    CTD_CUDA(h, ctd::launch_field_from_modes(h->P, st.bank, st.Mk, out, h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    return CTD_OK;
+  }
+  // host output: rebuild from the factors on the host
+  const int D = h->cfg.dim, Mk = st.Mk;
+  std::vector<std::vector<double>> f(D);
+  for (int d = 0; d < D; ++d) {
+    const int n = h->cfg.n[d];
+    std::vector<float2> tmp(static_cast<size_t>(Mk) * n);
+    if (Mk)
+      CTD_CUDA(h, cudaMemcpyAsync(tmp.data(), h->P.d[d].bank[st.bank], sizeof(float2) * tmp.size(),
+                                  cudaMemcpyDeviceToHost, h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    f[d].resize(tmp.size());
+    for (size_t t = 0; t < tmp.size(); ++t) f[d][t] = static_cast<double>(tmp[t].x) + static_cast<double>(tmp[t].y);
+  }
+  const int n0 = h->cfg.n[0], n1 = h->cfg.n[1], n2 = D == 3 ? h->cfg.n[2] : 1;
+  for (int i = 0; i < n0; ++i)
+    for (int j = 0; j < n1; ++j)
+      for (int l = 0; l < n2; ++l) {
+        double u = 0.0;
+        for (int m = 0; m < Mk; ++m) {
+          double t = f[0][static_cast<size_t>(m) * n0 + i] * f[1][static_cast<size_t>(m) * n1 + j];
+          if (D == 3) t *= f[2][static_cast<size_t>(m) * n2 + l];
+          u += t;
+        }
+        out[(static_cast<size_t>(i) * n1 + j) * n2 + l] = u;
+      }
+  return CTD_OK;
+}
+
 void ctd_destroy(ctd_handle h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  ctd::actd_release(h->actd);
   delete h;
 }
 

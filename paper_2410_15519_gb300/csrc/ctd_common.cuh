@@ -56,6 +56,8 @@ struct InstState {
   long long step;          // index of the next step (SplitMix64 key)
   int status;              // kErr* bits
   int err_info;            // where a wait gave up (phase id)
+  int grid;                // 1: u^k is held as the full-grid array U (after an adaptive-CTD step)
+  int switched;            // 1: the last step reached M_c + 1 modes; the host solves it on the grid
 };
 
 struct StepStatsDev {
@@ -67,6 +69,7 @@ struct StepStatsDev {
   int status;
   int als_stalled;
   int als_sweeps_committed;
+  int actd_switched;
 };
 
 struct StepParams {
@@ -76,6 +79,8 @@ struct StepParams {
   int Kpad;                // padded mode count of the tensor-core operands (multiple of 64)
   int precision;           // 0 FP64, 1 split BF16 tensor cores
   int quad;                // 0 nodal rule (M = diag(omega)), 1 Gauss rule (consistent mass)
+  int actd_Mc;             // > 0: adaptive CTD critical mode count (budget M_c + 1)
+  double* U;               // [N] full-grid field of the adaptive-CTD grid state (FP64)
   int quad_q;              // Gauss points per element
   double c_t, c_k, L, a0;
   float2 ct_df, ck_df, L_df;   // the same constants as double-float (converted on the host)

@@ -290,7 +290,8 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     convert_prev_modes(P, X, pb, Mk);
     if (P.quad) gauss_prologue(P, X, pb, Mk);
     if (!sync_all(P, epoch, 1)) return;
-    if (P.quad) materialise_w_gauss(P, Mk);
+    if (st0.grid) materialise_w_grid(P);   // adaptive CTD: u^k held on the full grid
+    else if (P.quad) materialise_w_gauss(P, Mk);
     else materialise_w(P, X, Mk);
   } else {
     if (P.quad) {
@@ -324,7 +325,9 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
   int M = 0, sweeps = 0, sweeps_max = 0, not_conv = 0, n_stalled = 0, sweeps_discarded = 0;
   double amp0 = 0.0;   // amplitude max|(x)v| of the step's leading mode
   bool stopped = false;
-  const int n_modes = P.fixed_modes > 0 ? P.fixed_modes : P.M_max;
+  // adaptive CTD: a budget of M_c + 1 modes; committing the last one means M > M_c
+  const int n_modes = P.fixed_modes > 0 ? P.fixed_modes
+                                        : (P.actd_Mc > 0 && P.actd_Mc < P.M_max ? P.actd_Mc + 1 : P.M_max);
   const int n_it = P.fixed_als > 0 ? P.fixed_als : P.I_max;
   for (int m = 0; m < n_modes; ++m) {
     init_mode(P, m, pb, Mk, st0.step);
@@ -481,9 +484,18 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
   }
   // ---- epilogue
   if (P.vrank == 0 && threadIdx.x == 0) {
+    // adaptive CTD: M > M_c discards the separated result; u^k stays for the host's full-grid
+    // step, which replaces it
+    const bool switched = P.actd_Mc > 0 && P.fixed_modes == 0 && M > P.actd_Mc;
     InstState s = st0;
-    s.Mk = M;
-    s.bank = cb;
+    if (switched) {
+      s.switched = 1;
+    } else {
+      s.Mk = M;
+      s.bank = cb;
+      s.grid = 0;
+      s.switched = 0;
+    }
     s.step = st0.step + 1;
     s.status = P.st->status;
     *P.st = s;
@@ -491,7 +503,8 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     r.modes = M;
     r.als_sweeps = sweeps;
     r.als_sweeps_max = sweeps_max;
-    r.capped = (P.fixed_modes == 0 && !stopped) ? 1 : 0;
+    r.capped = (P.fixed_modes == 0 && !stopped && !switched) ? 1 : 0;
+    r.actd_switched = switched ? 1 : 0;
     r.not_converged = not_conv;
     r.status = 0;
     r.als_stalled = n_stalled;

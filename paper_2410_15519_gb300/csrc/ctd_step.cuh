@@ -718,6 +718,20 @@ static __device__ __noinline__ void materialise_w_gauss(const StepParams& P, int
   }
 }
 
+// Adaptive CTD, step from the full-grid field U (nodal rule): the whole right-hand side from
+// u^k, c_t M u^k - int N~ L w(u^k), is one full-grid term; W = w(U) - (c_t / L) U makes the
+// contraction's -L omega R carry both parts (the step has no factors of u^k).
+static __device__ __noinline__ void materialise_w_grid(const StepParams& P) {
+  const int D = P.dim;
+  const long long N = static_cast<long long>(P.d[0].n) * P.d[1].n * (D == 3 ? P.d[2].n : 1);
+  const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
+  const double r = P.c_t / P.L;
+  for (long long p = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x; p < N; p += stride) {
+    const double u = P.U[p];
+    __stcs(P.W + p, 4.0 * P.a0 * (u * u * u - u) - r * u);
+  }
+}
+
 // Reduced integration domain on the materialised grid (FP64 path, 2D): every 128 x 128 node
 // block whose largest |W| is not above reduced_tol is set to zero.  Blocks are split over
 // the CTAs; each CTA reads its block, reduces the maximum in a fixed order, then zeroes it.

@@ -39,13 +39,15 @@ class Config(ctypes.Structure):
                 ("fixed_modes", ctypes.c_int), ("seed", ctypes.c_ulonglong),
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int),
                 ("reduced_tol", ctypes.c_double), ("nonlinear_form", ctypes.c_int),
-                ("als_stall_tol", ctypes.c_double), ("quad_rule", ctypes.c_int), ("quad_q", ctypes.c_int)]
+                ("als_stall_tol", ctypes.c_double), ("quad_rule", ctypes.c_int), ("quad_q", ctypes.c_int),
+                ("actd_Mc", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("als_sweeps_max", ctypes.c_int),
                 ("capped", ctypes.c_int), ("not_converged", ctypes.c_int), ("status", ctypes.c_int),
-                ("als_stalled", ctypes.c_int), ("als_sweeps_committed", ctypes.c_int)]
+                ("als_stalled", ctypes.c_int), ("als_sweeps_committed", ctypes.c_int),
+                ("actd_switched", ctypes.c_int)]
 
 
 class CTDError(RuntimeError):
@@ -73,6 +75,7 @@ def load() -> ctypes.CDLL:
     lib.ctd_step.argtypes = [vp, i, ctypes.POINTER(StepStats)]
     lib.ctd_energy.argtypes = [vp, ctypes.POINTER(d)]
     lib.ctd_get_modes.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(vp), i]
+    lib.ctd_get_field.argtypes = [vp, vp, i]
     lib.ctd_destroy.argtypes = [vp]
     lib.ctd_destroy.restype = None
     lib.ctd_last_error.argtypes = [vp]
@@ -89,7 +92,7 @@ def load() -> ctypes.CDLL:
     lib.ctd_batch_workspace_size.argtypes = [i, ctypes.POINTER(sz)]
     lib.ctd_step_batch.argtypes = [ctypes.POINTER(vp), i, i, vp, sz, vp, ctypes.POINTER(StepStats)]
     for f in ("ctd_workspace_size", "ctd_create", "ctd_set_initial_modes", "ctd_step", "ctd_energy",
-              "ctd_get_modes", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve", "ctd_probe_trace",
+              "ctd_get_modes", "ctd_get_field", "ctd_probe_cfem", "ctd_probe_contract", "ctd_probe_solve", "ctd_probe_trace",
               "ctd_probe_reconstruct", "ctd_probe_reconstruct_noalloc", "ctd_batch_workspace_size",
               "ctd_step_batch"):
         getattr(lib, f).restype = ctypes.c_int
@@ -100,7 +103,7 @@ def load() -> ctypes.CDLL:
 def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
                 precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
                 grid_ctas=0, reduced_tol=0.0, nonlinear_form=0, als_stall_tol=0.0, quad_rule=0,
-                quad_q=0) -> Config:
+                quad_q=0, actd_Mc=0) -> Config:
     c = Config()
     c.dim = dim
     for k in range(3):
@@ -116,6 +119,7 @@ def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, 
     c.nonlinear_form = int(nonlinear_form)
     c.als_stall_tol = float(als_stall_tol)
     c.quad_rule, c.quad_q = int(quad_rule), int(quad_q)
+    c.actd_Mc = int(actd_Mc)
     return c
 
 
@@ -213,7 +217,8 @@ def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True,
         out.append([dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
                          capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
                          als_stalled=r.als_stalled,
-                         als_sweeps_committed=r.als_sweeps_committed)
+                         als_sweeps_committed=r.als_sweeps_committed,
+                         actd_switched=bool(r.actd_switched))
                     for r in rec[i * nsteps:(i + 1) * nsteps]])
     return out
 
@@ -277,7 +282,8 @@ class Solver:
         return [dict(modes=r.modes, als_sweeps=r.als_sweeps, als_sweeps_max=r.als_sweeps_max,
                      capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
                          als_stalled=r.als_stalled,
-                         als_sweeps_committed=r.als_sweeps_committed) for r in rec]
+                         als_sweeps_committed=r.als_sweeps_committed,
+                         actd_switched=bool(r.actd_switched)) for r in rec]
 
     def energy(self) -> float:
         e = ctypes.c_double(0.0)
@@ -307,6 +313,13 @@ class Solver:
         if device:
             return [t.t() for t in outs]
         return [np.ascontiguousarray(t) for t in outs]
+
+    def get_field(self) -> np.ndarray:
+        """Full-grid nodal values of the current field (host array, n[0] x n[1] (x n[2]))."""
+        shape = tuple(self.cfg.n[d] for d in range(self.cfg.dim))
+        out = np.zeros(shape)
+        _check(self.lib, self.h, self.lib.ctd_get_field(self.h, out.ctypes.data, 0), "ctd_get_field")
+        return out
 
     def probe_contract(self, x: int, v: Sequence[np.ndarray]) -> np.ndarray:
         ptrs = (ctypes.c_void_p * 3)()
