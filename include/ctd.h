@@ -215,7 +215,8 @@ ctd_status ctd_get_field(ctd_handle h, double* out, int on_device);
 /* Release the handle (not the caller's workspace).  Waits for queued work. */
 void ctd_destroy(ctd_handle h);
 
-/* Message of the last failing call on h (static text for h == NULL). */
+/* Message of the last failing call on h; for h == NULL, that of the last ctd_create on this
+ * thread that failed after validating its arguments (else static text). */
 const char* ctd_last_error(ctd_handle h);
 const char* ctd_status_string(int status);
 

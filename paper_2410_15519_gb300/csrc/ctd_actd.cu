@@ -135,8 +135,9 @@ __global__ void energy_grid_kernel(const StepParams P, double kappa, const doubl
 }  // namespace
 
 size_t actd_work_doubles(int n) {
-  // the symmetric eigensolver with vectors needs about 1 + 6 n + 2 n^2 doubles
-  return 2 * static_cast<size_t>(n) * n + 64 * static_cast<size_t>(n) + 65536;
+  // the symmetric eigensolver with vectors needs about 1 + 6 n + 2 n^2 doubles, and a blocked
+  // implementation more for small n: a floor of 4 Mi doubles (32 MiB)
+  return 2 * static_cast<size_t>(n) * n + 64 * static_cast<size_t>(n) + (static_cast<size_t>(1) << 22);
 }
 
 int actd_setup(ActdState& a, const StepParams& P, const double* const* kband_host, const double* const* omega_host,

@@ -336,6 +336,9 @@ struct ctd_ctx {
   std::string err;
 };
 
+// message of the last ctd_create that failed after its checks (ctd_last_error(NULL)), per thread
+static thread_local std::string g_create_err;
+
 static ctd_status fail(ctd_ctx* h, ctd_status s, const std::string& msg) {
   if (h) h->err = msg;
   return s;
@@ -382,7 +385,7 @@ extern "C" {
 const char* ctd_status_string(int status) { return status_text(status); }
 
 const char* ctd_last_error(ctd_handle h) {
-  if (!h) return "no handle";
+  if (!h) return g_create_err.empty() ? "no handle" : g_create_err.c_str();
   return h->err.c_str();
 }
 
@@ -659,6 +662,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     const int rc = ctd::actd_setup(h->actd, P, kb, om, h->stream, &msg);
     if (rc != 0) {
       ctd_status s = fail(h, static_cast<ctd_status>(rc), msg);
+      g_create_err = msg;
       ctd::actd_release(h->actd);
       delete h;
       return s;

