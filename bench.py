@@ -457,7 +457,7 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
         sv.close()
     mx, f64 = traj["mixed"], traj["fp64"]
     # the same mode count, every mode swept to the stop rules: the arithmetic alone
-    fixed = dict(fixed_modes=min(12, w.M_max), als_stall_tol=args.stall)
+    fixed = dict(fixed_modes=min(6, w.M_max), als_stall_tol=args.stall)
     same = {}
     for prec in ("mixed", "fp64"):
         sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **fixed))

@@ -125,7 +125,7 @@ def field_rel_l2(A, B):
 def test_3d_whole_steps_mixed_vs_fp64(lib, name):
     # The full 3D configurations: the split-BF16 tensor-core form against the plain FP64 form
     # on the GPU (the oracle cannot hold these grids).
-    # (1) The same mode count (fixed_modes), every mode swept to its stop rules: the fields
+    # (1) The same mode count (fixed_modes = 6), every mode swept to its stop rules: the fields
     #     differ by the arithmetic alone, within the mixed-precision bar 1e-5, for the hi + lo
     #     and the hi + mid + lo splits.  (A fixed, unconverged sweep count is no measure of the
     #     arithmetic: with 6 sweeps per mode the oracle's own c2 step moves by 1e-4 under a 1e-7
@@ -150,17 +150,15 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
         s.close()
         return G, E, st
 
-    fixed = dict(fixed_modes=12, als_stall_tol=1e-6)
+    # Six modes: forcing more than the workload's leading modes commits trailing modes of
+    # amplitude ~1e-5 whose direction is ill-determined (on c2 a twelfth mode moves the field by
+    # 5e-5 between arithmetics whatever the contraction's precision).
+    fixed = dict(fixed_modes=6, als_stall_tol=1e-6)
     G64, E64, _ = run("fp64", 1, **fixed)
-    # c3: within the mixed-precision bar.  c2 (the tanh interface workload) at 512^3: every
-    # tensor-core precision, the one-term BF16 included, lands 5.7e-5 from the FP64 path, so the
-    # gap does not come from the contraction's precision (at 128^3 each is within 1.4e-7 of the
-    # oracle: test_interface_workload_steps_match_oracle); checked at the truncation level.
-    bar = 1e-5 if name == "c3" else w.tol_enrich
     for prec in ("mixed", "split3"):
         Gmx, Emx, _ = run(prec, 1, **fixed)
-        assert G64[0].shape[1] == Gmx[0].shape[1] == 12
-        assert field_rel_l2(Gmx, G64) < bar, prec
+        assert G64[0].shape[1] == Gmx[0].shape[1] == 6
+        assert field_rel_l2(Gmx, G64) < 1e-5, prec
         assert abs(Emx[-1] - E64[-1]) < 1e-5 * abs(E64[-1]), prec
     G64, E64, s64 = run("fp64", 2, als_stall_tol=1e-6)
     Gmx, Emx, smx = run("mixed", 2, als_stall_tol=1e-6)
@@ -174,18 +172,18 @@ def test_3d_whole_steps_mixed_vs_fp64(lib, name):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-7), ("mixed", 1e-6), ("split3", 1e-6)])
 def test_interface_workload_steps_match_oracle(lib, prec, tol):
     # The tanh interface workload's parameters (eps = 0.02, s = p = 2, rank 6 + tanh mode) on a
-    # 128^3 grid, where the oracle holds the grid: one step with 12 modes, each swept to the same
+    # 128^3 grid, where the oracle holds the grid: one step with 6 modes, each swept to the same
     # stop rules, against the oracle's step.  The stall rule makes the mode stops, hence the
-    # field, depend on the arithmetic's rounding floor at the 1e-8 level (FP64 lands 2.9e-8 from
-    # the oracle), so the bars sit above it; the mixed forms stay two decades under 1e-5.
+    # field, depend on the arithmetic's rounding floor (the bars sit above it); the mixed forms
+    # stay an order under the mixed-precision bar 1e-5.
     w = workloads.preset("c2", n=(128, 128, 128))
     A0 = workloads.initial_modes(w)
     prob = oracle_problem(w)
-    prob.fixed_modes, prob.als_stall_tol = 12, 1e-6
+    prob.fixed_modes, prob.als_stall_tol = 6, 1e-6
     ops = octd.build_operators(prob)
     A, _ = octd.step(prob, ops, A0, 0)
     p = {"fp64": lib.PREC_FP64, "mixed": lib.PREC_SPLIT_BF16, "split3": lib.PREC_SPLIT3_BF16}[prec]
-    s = lib.Solver(lib.config_from_workload(w, precision=p, fixed_modes=12, als_stall_tol=1e-6))
+    s = lib.Solver(lib.config_from_workload(w, precision=p, fixed_modes=6, als_stall_tol=1e-6))
     s.set_initial_modes(A0)
     s.step(1)
     G = s.get_modes()
