@@ -81,9 +81,10 @@ typedef struct {
   double wait_limit_s;      /* limit of each grid-wide wait; <= 0 means 1 second            */
   int grid_ctas;            /* persistent CTAs; <= 0 means one per SM                       */
   double reduced_tol;       /* > 0: reduced integration domain of the nonlinear term
-                               (Section 3.3): a 128 x 128 node block drops out of M_xy for
-                               the step when max |w(u^k)| over its nodes <= reduced_tol;
-                               0: the whole domain.  2D only (CTD_ERR_UNSUPPORTED in 3D)   */
+                               (Section 3.3): a block of 128 nodes per dimension (128 x 128
+                               in 2D, 128^3 in 3D) drops out of M_xy for the step when
+                               max |w(u^k)| over its nodes <= reduced_tol; 0: the whole
+                               domain.  Nodal rule only                                      */
   int nonlinear_form;       /* CTD_NONLINEAR_GRID: M_xy as the full nodal integral over the
                                grid (Eq. KxxMxx), tile by tile.  CTD_NONLINEAR_SEPARATED: the
                                separated form of Eq. MxySep, with the exact decomposition of

@@ -207,7 +207,9 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
     if (actd) *actd = a;
   }
   p.barrier = cv.take<unsigned>(64);
-  p.tile_max = cv.take<unsigned>(static_cast<size_t>(pl.n_pad[0] / ctd::kTcM) * (pl.n_pad[1] / ctd::kTcN));
+  size_t nblocks = 1;   // reduced domain: 128-node blocks per dimension
+  for (int d = 0; d < D; ++d) nblocks *= static_cast<size_t>(pl.n_pad[d] / ctd::kTcM);
+  p.tile_max = cv.take<unsigned>(nblocks);
   p.trace = cv.take<unsigned long long>(ctd::kTrSlots);
   p.st = cv.take<InstState>(1);
   x.maxpart = cv.take<double>(static_cast<size_t>(ctd::kMaxDim) * Gs);
@@ -257,7 +259,6 @@ ctd_status validate(const ctd_config* c) {
     return CTD_ERR_ARG;
   if (c->grid_ctas > kGridMax) return CTD_ERR_ARG;
   if (!(c->reduced_tol >= 0.0) || !std::isfinite(c->reduced_tol)) return CTD_ERR_ARG;
-  if (c->reduced_tol > 0.0 && c->dim != 2) return CTD_ERR_UNSUPPORTED;
   if (c->nonlinear_form != CTD_NONLINEAR_GRID && c->nonlinear_form != CTD_NONLINEAR_SEPARATED) return CTD_ERR_ARG;
   if (c->nonlinear_form == CTD_NONLINEAR_SEPARATED && (c->reduced_tol > 0.0 || c->M_max > ctd::kMaxSepModes))
     return CTD_ERR_ARG;
@@ -648,6 +649,16 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
     // the tensor-core path allocates all 512 TMEM columns of the SM: more than half the shared
     // memory keeps it at one CTA per SM, so no CTA waits for another's columns
     if (cfg->precision != CTD_PREC_FP64) need = std::max(need, static_cast<size_t>(optin) / 2 + 1024);
+    if (cfg->precision != CTD_PREC_FP64 && cfg->reduced_tol > 0.0) {
+      // block classification stages every dimension's factor rows of a block
+      const size_t cls = fixed + 1024 + static_cast<size_t>(cfg->dim) * h->plan.Mcap * ctd::kTcM * sizeof(float) + 1024;
+      if (cls > static_cast<size_t>(optin)) {
+        ctd_status s = fail(h, CTD_ERR_UNSUPPORTED, "reduced-domain classification exceeds shared memory");
+        delete h;
+        return s;
+      }
+      need = std::max(need, cls);
+    }
     P.smem_bytes = static_cast<int>(need);
   }
   if (cfg->actd_Mc > 0) {

@@ -392,10 +392,22 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
   const int ntc = td.ntc, nrb = td.nrb, tmid = td.mid, cmax = td.cmax, n_last_pad = td.n_last_pad;
   const int ncols_pad = td.ncols_pad, nx = P.d[x].nq;
   InstState* const st = P.st;
+  // Reduced domain: the 128-node block of every dimension that tile t lies in (in 3D a tile is
+  // 128 rows of x by 128 nodes of the last dimension at one node of the middle one), blocks
+  // numbered row-major over dimensions 0, 1 (, 2)
+  const int nb1 = (P.d[1].n + kTcM - 1) / kTcM, nb2 = P.dim == 3 ? (P.d[2].n + kTcM - 1) / kTcM : 1;
   auto active = [=](int t) -> bool {
     if (!tile_max) return true;
     const int rb = t / ntc, cb = t - rb * ntc;
-    const int idx = x == 0 ? t : cb * nrb + rb;
+    int idx;
+    if (tmid < 0) {
+      idx = x == 0 ? t : cb * nrb + rb;
+    } else {
+      const int col0 = cb * kTcN, jm = col0 / n_last_pad;
+      const int bm = jm / kTcM, bl = (col0 - jm * n_last_pad) / kTcN;
+      auto blk = [&](int d) { return d == x ? rb : (d == tmid ? bm : bl); };
+      idx = (blk(0) * nb1 + blk(1)) * nb2 + blk(2);
+    }
     return __uint_as_float(tile_max[idx]) * on_scale > on_tol;
   };
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -732,24 +732,50 @@ static __device__ __noinline__ void materialise_w_grid(const StepParams& P) {
   }
 }
 
-// Reduced integration domain on the materialised grid (FP64 path, 2D): every 128 x 128 node
-// block whose largest |W| is not above reduced_tol is set to zero.  Blocks are split over
-// the CTAs; each CTA reads its block, reduces the maximum in a fixed order, then zeroes it.
+// Reduced integration domain: the grid is cut into blocks of 128 nodes per dimension (the
+// tensor-core tile edge; a 3D tile of direction x lies inside one block), numbered row-major
+// over the blocks of dimensions 0, 1 (, 2).
+struct RdBlocks {
+  int n[3], nb[3];
+  __device__ explicit RdBlocks(const StepParams& P) {
+    for (int d = 0; d < 3; ++d) {
+      n[d] = d < P.dim ? P.d[d].n : 1;
+      nb[d] = d < P.dim ? (n[d] + kTcM - 1) / kTcM : 1;
+    }
+  }
+  __device__ int count() const { return nb[0] * nb[1] * nb[2]; }
+  // block blk: node ranges [lo[d], hi[d])
+  __device__ void range(int blk, int (&lo)[3], int (&hi)[3]) const {
+    int b[3];
+    b[2] = blk % nb[2];
+    b[1] = (blk / nb[2]) % nb[1];
+    b[0] = blk / (nb[2] * nb[1]);
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = b[d] * kTcM;
+      hi[d] = min(n[d], lo[d] + kTcM);
+      if (nb[d] == 1 && n[d] == 1) { lo[d] = 0; hi[d] = 1; }
+    }
+  }
+};
+
+// FP64 path: every block whose largest |W| is not above reduced_tol is set to zero.  Blocks are
+// split over the CTAs; each CTA reads its block, reduces the maximum in a fixed order, then
+// zeroes it.
 static __device__ __noinline__ void reduce_domain_fp64(const StepParams& P) {
-  const int n0 = P.d[0].n, n1 = P.d[1].n;
-  const int nb0 = (n0 + kTcM - 1) / kTcM, nb1 = (n1 + kTcN - 1) / kTcN;
+  const RdBlocks B(P);
   double* W = P.W;
   __shared__ double s_red[kWarps];
   __shared__ int s_keep;
-  for (int blk = P.vrank; blk < nb0 * nb1; blk += P.vgrid) {
-    const int b0 = blk / nb1, b1 = blk - b0 * nb1;
-    const int r0 = b0 * kTcM, r1 = min(n0, r0 + kTcM), c0 = b1 * kTcN, c1 = min(n1, c0 + kTcN);
-    const int w = c1 - c0, cnt = (r1 - r0) * w;
+  for (int blk = P.vrank; blk < B.count(); blk += P.vgrid) {
+    int lo[3], hi[3];
+    B.range(blk, lo, hi);
+    const int w1 = hi[1] - lo[1], w2 = hi[2] - lo[2], cnt = (hi[0] - lo[0]) * w1 * w2;
+    auto at = [&](int e) -> size_t {
+      const int l = lo[2] + e % w2, j = lo[1] + (e / w2) % w1, i = lo[0] + e / (w2 * w1);
+      return (static_cast<size_t>(i) * B.n[1] + j) * B.n[2] + l;
+    };
     double mx = 0.0;
-    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-      const int r = r0 + e / w, c = c0 + e % w;
-      mx = fmax(mx, fabs(W[static_cast<size_t>(r) * n1 + c]));
-    }
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) mx = fmax(mx, fabs(W[at(e)]));
     mx = warp_max(mx);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -760,43 +786,43 @@ static __device__ __noinline__ void reduce_domain_fp64(const StepParams& P) {
     }
     __syncthreads();
     if (!s_keep)
-      for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const int r = r0 + e / w, c = c0 + e % w;
-        W[static_cast<size_t>(r) * n1 + c] = 0.0;
-      }
+      for (int e = threadIdx.x; e < cnt; e += blockDim.x) W[at(e)] = 0.0;
     __syncthreads();
   }
 }
 
-// Reduced integration domain, tensor-core path (2D): max |u(u^2 - 1)| of u^k over every
-// 128 x 128 node block, from the FP32 parts of the factors (the arithmetic of the tiles it
-// gates), into P.tile_max (float bits).  Blocks are split over the CTAs; a block's factor
-// rows are staged in shared memory (sh: 2 * 128 * Mk floats).
+// Tensor-core path: max |u(u^2 - 1)| of u^k over every block, from the FP32 parts of the
+// factors (the arithmetic of the tiles it gates), into P.tile_max (float bits).  Blocks are
+// split over the CTAs; a block's factor rows are staged in shared memory (sh: D * 128 * Mk
+// floats).
 static __device__ __noinline__ void classify_tiles(const StepParams& P, int pb, int Mk, float* sh) {
-  const Dim& d0 = P.d[0];
-  const Dim& d1 = P.d[1];
-  const int n0 = d0.n, n1 = d1.n;
-  const int nb0 = (n0 + kTcM - 1) / kTcM, nb1 = (n1 + kTcN - 1) / kTcN;
-  float* sa = sh;              // [Mk][128] rows of the block, dimension 0
-  float* sb = sh + Mk * kTcM;  // [Mk][128] columns of the block, dimension 1
+  const RdBlocks B(P);
+  const int D = P.dim;
+  float* sf[3] = {sh, sh + Mk * kTcM, sh + 2 * Mk * kTcM};   // [Mk][128] per dimension
   __shared__ float s_red[kWarps];
-  for (int blk = P.vrank; blk < nb0 * nb1; blk += P.vgrid) {
-    const int b0 = blk / nb1, b1 = blk - b0 * nb1;
+  for (int blk = P.vrank; blk < B.count(); blk += P.vgrid) {
+    int lo[3], hi[3];
+    B.range(blk, lo, hi);
     __syncthreads();
-    for (int e = threadIdx.x; e < Mk * kTcM; e += blockDim.x) {
-      const int m = e / kTcM, r = e - m * kTcM;
-      const int i = b0 * kTcM + r, j = b1 * kTcN + r;
-      const float2 a = i < n0 ? d0.bank[pb][static_cast<size_t>(m) * n0 + i] : make_float2(0.f, 0.f);
-      const float2 b = j < n1 ? d1.bank[pb][static_cast<size_t>(m) * n1 + j] : make_float2(0.f, 0.f);
-      sa[e] = a.x + a.y;
-      sb[e] = b.x + b.y;
+    for (int d = 0; d < D; ++d) {
+      const Dim& dd = P.d[d];
+      for (int e = threadIdx.x; e < Mk * kTcM; e += blockDim.x) {
+        const int m = e / kTcM, r = e - m * kTcM, i = lo[d] + r;
+        const float2 a = i < hi[d] ? dd.bank[pb][static_cast<size_t>(m) * dd.n + i] : make_float2(0.f, 0.f);
+        sf[d][e] = a.x + a.y;
+      }
     }
     __syncthreads();
+    const int w1 = hi[1] - lo[1], w2 = hi[2] - lo[2], cnt = (hi[0] - lo[0]) * w1 * w2;
     float mx = 0.f;
-    for (int e = threadIdx.x; e < kTcM * kTcN; e += blockDim.x) {
-      const int r = e / kTcN, c = e - r * kTcN;
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int l = e % w2, j = (e / w2) % w1, i = e / (w2 * w1);
       float u = 0.f;
-      for (int m = 0; m < Mk; ++m) u = __fmaf_rn(sa[m * kTcM + r], sb[m * kTcM + c], u);
+      if (D == 2) {
+        for (int m = 0; m < Mk; ++m) u = __fmaf_rn(sf[0][m * kTcM + i], sf[1][m * kTcM + j], u);
+      } else {
+        for (int m = 0; m < Mk; ++m) u = __fmaf_rn(sf[0][m * kTcM + i] * sf[1][m * kTcM + j], sf[2][m * kTcM + l], u);
+      }
       mx = fmaxf(mx, fabsf(u * __fmaf_rn(u, u, -1.f)));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));

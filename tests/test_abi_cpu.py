@@ -155,7 +155,7 @@ def test_calls_without_a_handle_fail_cleanly(ctd):
     (dict(quad_rule=2, quad_q=5), -1),                                 # unknown rule: CTD_ERR_ARG
     (dict(quad_rule=1, quad_q=0), -1), (dict(quad_rule=1, quad_q=17), -1),
     (dict(quad_rule=1, quad_q=5, nonlinear_form=1, M_max=8), -7),      # separated form: CTD_ERR_UNSUPPORTED
-    (dict(quad_rule=1, quad_q=5, reduced_tol=1e-3), -7),               # reduced domain
+    (dict(quad_rule=1, quad_q=5, reduced_tol=1e-3), -7),               # reduced domain (nodal rule only)
     (dict(quad_rule=1, quad_q=5, n=(4096, 64)), -7),                   # 20475 points beside direction 1
     (dict(quad_rule=1, quad_q=2, n=(4096, 4096)), 0), (dict(quad_rule=1, quad_q=5), 0),
     (dict(als_stall_tol=-1.0), -1), (dict(als_stall_tol=1e-6), 0),

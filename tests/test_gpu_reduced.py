@@ -1,7 +1,8 @@
 """Reduced integration domain (Section 3.3) on the GPU against the oracle with the same
-reading (128 x 128 node blocks dropped while max |w(u^k)| <= reduced_tol): a straight
-interface across a 640 x 300 grid leaves one block row of five in the domain.  FP64 path
-within 1e-12, split-BF16 path within 1e-5 (u and energy).
+reading (blocks of 128 nodes per dimension dropped while max |w(u^k)| <= reduced_tol): a
+straight interface across a 640 x 300 grid leaves one block row of five in the domain, and in
+3D an interface normal to each axis leaves one block of three.  FP64 path within 1e-12,
+split-BF16 path within 1e-5 (u and energy).
 
 The energy of a sharp interface is a sum of terms much larger than itself (the stiffness
 products of the nearly constant regions cancel), so its FP64 evaluation, in either program,
@@ -74,8 +75,40 @@ def test_reduced_domain_matches_oracle(lib, prec, tol):
     s.close()
 
 
-def test_reduced_domain_3d_is_refused(lib):
-    w = workloads.preset("c0", dim=3, n=(16, 16, 16), length=(1.0, 1.0, 1.0))
-    with pytest.raises(lib.CTDError) as ei:
-        lib.Solver(lib.config_from_workload(w, reduced_tol=1e-4))
-    assert ei.value.status == -7
+def interface_modes(n, axis, eps):
+    """u = tanh((x_axis - 1/2) / (sqrt(2) eps)): one separated mode, the interface normal to `axis`."""
+    out = []
+    for d in range(3):
+        x = np.linspace(0.0, 1.0, n[d])
+        f = np.tanh((x - 0.5) / (np.sqrt(2.0) * eps)) if d == axis else np.ones(n[d])
+        out.append(f[:, None])
+    return out
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+@pytest.mark.parametrize("axis,n", [(0, (384, 24, 20)), (1, (20, 384, 24)), (2, (20, 24, 384))])
+def test_reduced_domain_3d_matches_oracle(lib, prec, tol, axis, n):
+    # an interface normal to each axis in turn: of the three 128-node blocks along that axis
+    # only the middle one stays in the domain; the others (u = +-1, w ~ 1e-10) drop out
+    w = workloads.preset("c0", dim=3, n=n, length=(1.0, 1.0, 1.0), s=2, p=2, eps=0.01, dt=1e-3, M_max=10)
+    red = 1e-4
+    cfg = lib.config_from_workload(w, precision=lib.PREC_FP64 if prec == "fp64" else lib.PREC_SPLIT_BF16,
+                                   reduced_tol=red)
+    s = lib.Solver(cfg)
+    A = interface_modes(n, axis, w.eps)
+    s.set_initial_modes(A)
+    prob = octd.Problem(dim=3, n=w.n, length=w.length, s=w.s, p=w.p, a=w.a, L=w.L, kappa=w.kappa, a0=w.a0,
+                        alpha=w.alpha, dt=w.dt, M_max=w.M_max, I_max=w.I_max, tol_als=w.tol_als,
+                        tol_enrich=w.tol_enrich, seed=w.seed, reduced_tol=red)
+    ops = octd.build_operators(prob)
+    kept = octd.reduced_domain_mask(prob, octd.w_of_u(octd.reconstruct(A), prob.a0))
+    assert abs(kept.mean() - 1.0 / 3.0) < 1e-12
+    for k in range(3):
+        A, so = octd.step(prob, ops, A, k)
+        sg = s.step(1)[0]
+        assert sg["modes"] == so["modes"], (k, sg, so)
+        assert octd.rel_l2_between(s.get_modes(), A) < tol, (k, octd.rel_l2_between(s.get_modes(), A))
+        eo = octd.energy(prob, ops, A)
+        tol_e = tol + 4.0 * energy_condition(prob, ops, A) * 2.0 ** -53
+        assert abs(s.energy() - eo) / abs(eo) < tol_e, (k, abs(s.energy() - eo) / abs(eo), tol_e)
+    s.close()
