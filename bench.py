@@ -442,6 +442,9 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
         out["e2e"] = dict(steps=n_e2e, seconds=time.perf_counter() - t0, h2d=bi / max(1, n_e2e),
                           d2h=bo / max(1, n_e2e))
     solver.close()
+    if getattr(args, "quick", False):
+        out["accuracy"], out["first_step_modes"], out["side"], out["ladder"] = {}, {}, {}, {}
+        return out
     # accuracy: both arithmetics from the initial condition under the same rules
     traj = {}
     for prec in ("mixed", "fp64"):
@@ -852,6 +855,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--oracle-budget", type=float, default=25.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline timing, phase trace and end-to-end run only (no accuracy, side or ladder legs); "
+                         "for profiler captures")
     args = ap.parse_args()
     args.extras = [] if args.extras in ("", "none") else args.extras.split(",")
 

@@ -649,7 +649,7 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
         }
         // w(u)/(4 a0) = u (u^2 - 1) and the weighted row sum, two columns per FP32x2
         // instruction; four interleaved sums (columns 0, 1, 2, 3 mod 4)
-        float2 a01 = make_float2(0.f, 0.f), a23 = make_float2(0.f, 0.f);
+        float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
         const float2 m1 = make_float2(-1.f, -1.f);
         const uint32_t acol = static_cast<uint32_t>((2 * ps + j) * kTcN);
 #pragma unroll
@@ -662,14 +662,19 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
           }
           const float4* w4 = reinterpret_cast<const float4*>(wt + q * 32);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float4 ww = w4[c];
+          for (int c = 0; c < 8; c += 2) {
+            const float4 wa = w4[c], wb = w4[c + 1];
             const float2 u01 = make_float2(v[4 * c], v[4 * c + 1]), u23 = make_float2(v[4 * c + 2], v[4 * c + 3]);
-            a01 = __ffma2_rn(__fmul2_rn(u01, __ffma2_rn(u01, u01, m1)), make_float2(ww.x, ww.y), a01);
-            a23 = __ffma2_rn(__fmul2_rn(u23, __ffma2_rn(u23, u23, m1)), make_float2(ww.z, ww.w), a23);
+            const float2 u45 = make_float2(v[4 * c + 4], v[4 * c + 5]), u67 = make_float2(v[4 * c + 6], v[4 * c + 7]);
+            // w u (u^2 - 1): the weight product and u^2 - 1 are independent, so each column pair
+            // has a chain of two dependent operations before its accumulator
+            a01 = __ffma2_rn(__fmul2_rn(u01, make_float2(wa.x, wa.y)), __ffma2_rn(u01, u01, m1), a01);
+            a23 = __ffma2_rn(__fmul2_rn(u23, make_float2(wa.z, wa.w)), __ffma2_rn(u23, u23, m1), a23);
+            b01 = __ffma2_rn(__fmul2_rn(u45, make_float2(wb.x, wb.y)), __ffma2_rn(u45, u45, m1), b01);
+            b23 = __ffma2_rn(__fmul2_rn(u67, make_float2(wb.z, wb.w)), __ffma2_rn(u67, u67, m1), b23);
           }
         }
-        const float at = (a01.x + a01.y) + (a23.x + a23.y);
+        const float at = ((a01.x + a01.y) + (a23.x + a23.y)) + ((b01.x + b01.y) + (b23.x + b23.y));
         const float pr = wscale * at;
         acc = df_add(acc, dfloat{pr, __fmaf_rn(wscale, at, -pr)});
       }
