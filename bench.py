@@ -425,23 +425,30 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
         # the tensor-core contraction's roles on the traced (last) CTA, SM cycles per tile
         out["contraction_role_cycles_per_tile"] = {
             k[3:-7]: v / tr["tc_tiles"] for k, v in tr.items() if k.startswith("tc_") and k.endswith("_cycles")}
+    solver.close()
     if headline:
-        # end to end through the C ABI with host buffers: H2D of u^k, step, D2H of u^{k+1}
+        # End to end through the C ABI with host buffers, on the same steps as the first timed
+        # ones (a fresh solver from the initial condition, the same warm-up): every step the H2D
+        # copy of u^k's factors, the step, the D2H read of u^{k+1}'s factors.
         n_e2e = min(steps, args.e2e_steps)
+        solver = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, args.precision), **over))
+        solver.set_initial_modes(workloads.initial_modes(w))
+        solver.step(args.warmup, stats=False)
         modes_host = solver.get_modes()
         bi = bo = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(n_e2e):
             bi += sum(m.nbytes for m in modes_host)
-            solver.set_initial_modes(modes_host, first_step=args.warmup + steps + 2 + k)
+            solver.set_initial_modes(modes_host, first_step=args.warmup + k)
             solver.step(1)
             modes_host = solver.get_modes()
             bo += sum(m.nbytes for m in modes_host)
         torch.cuda.synchronize()
         out["e2e"] = dict(steps=n_e2e, seconds=time.perf_counter() - t0, h2d=bi / max(1, n_e2e),
-                          d2h=bo / max(1, n_e2e))
-    solver.close()
+                          d2h=bo / max(1, n_e2e),
+                          device_ms_same_steps=sum(times_ms[:n_e2e]))
+        solver.close()
     if getattr(args, "quick", False):
         out["accuracy"], out["first_step_modes"], out["side"], out["ladder"] = {}, {}, {}, {}
         return out
@@ -904,7 +911,12 @@ def main():
     line.update(fields)
     line.update({"clocks": res["clocks"], "gpu_launches": args.steps,
                  "e2e": {"value": world * e2e["steps"] / e2e["seconds"], "unit": UNIT,
-                         "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"])}})
+                         "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"]),
+                         "steps": e2e["steps"],
+                         "device_value_same_steps": e2e["steps"] / (e2e["device_ms_same_steps"] / 1e3),
+                         "note": "the first timed steps again from the initial condition through the C ABI "
+                                 "with host factor buffers (H2D of u^k, step, D2H of u^{k+1} each step); "
+                                 "device_value_same_steps: the device-timed rate of those same steps"}})
     extra_out = {}
     for name, val in extras.items():
         if name == "c4":
