@@ -240,9 +240,11 @@ ctd_status ctd_probe_cfem(const ctd_config* cfg, int d, double* omega, double* k
  *                            zero past the support of the point's element (nodes e-s .. e+1+s);
  *   mband[n[d]][2b+1]        the mass Phi^T diag(omega) Phi in the layout of ctd_probe_cfem's
  *                            kband (b = 2s+1); for q >= 5 the exact consistent mass;
- *   mass_bounds[2]           lo <= lambda <= hi for every eigenvalue of diag(M)^-1 M (the
- *                            bounds of a Chebyshev solve preconditioned by diag(M)): banded
- *                            Cholesky tests of M - lo diag(M) and hi diag(M) - M, widened by 1e-6.
+ *   mass_bounds[2]           bounds lo, hi on the eigenvalues of diag(M)^-1 M (those of a
+ *                            Chebyshev solve preconditioned by diag(M)), found by FP64 banded
+ *                            Cholesky tests of M - lo diag(M) and hi diag(M) - M and then widened
+ *                            by a 1e-6 relative margin; they enclose the spectrum numerically, with
+ *                            no proof that the margin covers the tests' rounding errors.
  * Any output may be NULL; the caller owns every buffer.  CTD_ERR_ARG for an invalid
  * configuration, d or q, or a mass that is not positive definite.  A handle created with
  * quad_rule = CTD_QUAD_GAUSS uses the same operators in every step. */
