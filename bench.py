@@ -223,12 +223,19 @@ def replica_units(steps: int, world: int) -> int:
 
 
 # --------------------------------------------------------------------------- rooflines
-def half_sweep_roof_s(w, precision: str, Mk: int, pk: dict) -> dict:
+def epilogue_ops(cube: bool) -> float:
+    """FP32 operations per grid point of the contraction epilogue: the direct form's
+    u*u - 1, times (u c_j), into the row sum (3); the cube form's v*v, times v into the row
+    sum (2)."""
+    return 2.0 if cube else 3.0
+
+
+def half_sweep_roof_s(w, precision: str, Mk: int, pk: dict, cube: bool = False) -> dict:
     """Roofline time of one half-sweep's nonlinear contraction over the whole grid (the only
     term of the step that grows with the grid): the largest of
       tensor: 2 K_eff N flops at the BF16 burst peak (K_eff = 3 Mk for the split product),
-      alu:    3 FP32 operations per grid point in the fused epilogue (u*u - 1, times u, into the
-              weighted row sum) on 152 x 128 FP32 lanes at the maximum SM clock,
+      alu:    the epilogue's FP32 operations per grid point (3 direct, 2 cube form) on
+              152 x 128 FP32 lanes at the maximum SM clock,
       hbm:    the operands' bytes (factor rows, K_eff BF16 values each) at the copy bandwidth;
     FP64 path: one FP64 multiply-add per grid point on the FP64 pipe, or the 8 N bytes of the
     materialised w(u^k) grid from HBM, whichever is slower."""
@@ -239,7 +246,7 @@ def half_sweep_roof_s(w, precision: str, Mk: int, pk: dict) -> dict:
         return {"fp64": t_f, "hbm": t_b}
     keff = PRODUCTS[precision] * Mk
     t_tensor = 2.0 * keff * N / (pk["bf16_tflops"] * 1e12)
-    t_alu = 3.0 * N / (alu_peak_tops(pk) * 1e12)
+    t_alu = epilogue_ops(cube) * N / (alu_peak_tops(pk) * 1e12)
     t_hbm = 2.0 * keff * sum(w.n) / (pk["hbm_gbs"] * 1e9)
     return {"tensor": t_tensor, "alu": t_alu, "hbm": t_hbm}
 
@@ -251,16 +258,18 @@ def step_roofline(w, precision, ranks_in, stats, times_ms, pk, pk_kind, traffic)
     roof = {}
     for mk, st in zip(ranks_in, stats):
         hs = st["als_sweeps"] * w.dim
-        for k, v in half_sweep_roof_s(w, precision, mk, pk).items():
+        for k, v in half_sweep_roof_s(w, precision, mk, pk, st.get("cube_form", False)).items():
             roof[k] = roof.get(k, 0.0) + hs * v
     t = sum(times_ms) / 1e3
     bound = max(roof, key=roof.get)
     N = float(w.grid_points)
     hs_all = sum(st["als_sweeps"] for st in stats) * w.dim
     if bound == "alu":
-        achieved, peak, unit = 3.0 * N * hs_all / t / 1e12, alu_peak_tops(pk), "TFLOP/s"
-        peak_kind = ("FP32 lane operations (3 per grid point and half-sweep), peak = 152 SMs x 128 lanes x "
-                     f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz, derived from unit counts and the maximum clock")
+        ops = sum(epilogue_ops(st.get("cube_form", False)) * st["als_sweeps"] * w.dim for st in stats)
+        achieved, peak, unit = ops * N / t / 1e12, alu_peak_tops(pk), "TFLOP/s"
+        peak_kind = ("FP32 lane operations (per grid point and half-sweep: 3 in the direct form, 2 in the cube "
+                     f"form), peak = 152 SMs x 128 lanes x {pk.get('sm_max_mhz', 2070.0):.0f} MHz, derived from "
+                     "unit counts and the maximum clock")
     elif bound == "tensor":
         flops = sum(2.0 * PRODUCTS[precision] * mk * N * st["als_sweeps"] * w.dim for mk, st in zip(ranks_in, stats))
         achieved, peak, unit = flops / t / 1e12, pk["bf16_tflops"], "TFLOP/s"
@@ -293,14 +302,15 @@ def last_cta_tile_share(w, G: int = SMS) -> float:
     return (T - lo) / T
 
 
-def contraction_roof_us(w, Mk: float, pk: dict, precision: str = "mixed") -> dict:
+def contraction_roof_us(w, Mk: float, pk: dict, precision: str = "mixed", cube: bool = False) -> dict:
     """Roofline time of the last CTA's share of one half-sweep's tensor-core contraction (the
     phase is timed on that CTA): the larger of the split reconstruction on the tensor cores
     (2 * 3Mk flops per grid point at one SM's share of the BF16 burst peak) and the fused
-    epilogue on the FP32 pipes (3 operations per grid point on 128 lanes at the maximum clock)."""
+    epilogue on the FP32 pipes (3 or 2 operations per grid point on 128 lanes at the maximum
+    clock)."""
     n_cta = float(w.grid_points) * last_cta_tile_share(w)
     t_tensor = 2.0 * PRODUCTS[precision] * Mk * n_cta / (pk["bf16_tflops"] * 1e12 / SMS)
-    t_alu = 3.0 * n_cta / (128 * pk.get("sm_max_mhz", 2070.0) * 1e6)
+    t_alu = epilogue_ops(cube) * n_cta / (128 * pk.get("sm_max_mhz", 2070.0) * 1e6)
     bound = "tensor" if t_tensor >= t_alu else "alu"
     return {"roof_us": 1e6 * max(t_tensor, t_alu), "bound": bound, "tensor_us": 1e6 * t_tensor, "alu_us": 1e6 * t_alu,
             "grid_points": n_cta}
@@ -495,17 +505,20 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
     # the precision ladder of the tensor-core contraction beside the headline's two-term split
     ladder = {}
     if args.precision == "mixed":
-        for prec in ("bf16", "split3"):
-            s3, t3, st3, _, _ = timed_run(ctd, torch, w, prec, plan["side_steps"], args.warmup, flush, over=over)
+        for name, prec, form in (("bf16", "bf16", {}), ("split3", "split3", {}),
+                                 ("split_direct_form", "mixed", dict(contraction_form=ctd.CONTRACT_DIRECT))):
+            s3, t3, st3, _, _ = timed_run(ctd, torch, w, prec, plan["side_steps"], args.warmup, flush,
+                                          over=dict(over, **form))
             s3.close()
             leg = leg_summary(t3, st3, w)
-            sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **fixed))
+            leg["cube_steps"] = sum(1 for x in st3 if x.get("cube_form"))
+            sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **fixed, **form))
             sv.set_initial_modes(workloads.initial_modes(w))
             sv.step(1)
             leg["same_schedule_u_rel_l2_vs_fp64_gpu"] = field_rel_l2(sv.get_modes(), same["fp64"][0])
             leg["same_schedule_energy_rel_diff"] = abs(sv.energy() - same["fp64"][1]) / abs(same["fp64"][1])
             sv.close()
-            sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **over))
+            sv = ctd.Solver(ctd.config_from_workload(w, precision=prec_code(ctd, prec), **over, **form))
             sv.set_initial_modes(workloads.initial_modes(w))
             energies = [sv.energy()]
             for k in range(plan["err_steps"]):
@@ -515,10 +528,12 @@ def run_single(ctd, torch, w, args, flush, local_rank, headline=True):
             leg["energy_rel_diff_vs_fp64_gpu"] = abs(energies[-1] - f64["energies"][-1]) / abs(f64["energies"][-1])
             leg["energy_max_rel_change_per_step"] = max((e1 - e0) / abs(e0) for e0, e1 in zip(energies, energies[1:]))
             sv.close()
-            ladder[prec] = leg
+            ladder[name] = leg
         ladder["note"] = ("tensor-core precisions beside the headline's hi + lo split: bf16 = one BF16 term per "
-                          "factor value (1 product per K step), split3 = hi + mid + lo (6 products); timed on the "
-                          "steps after the warm-up, errors as in accuracy")
+                          "factor value (1 product per K step), split3 = hi + mid + lo (6 products), "
+                          "split_direct_form = the headline's split with the direct epilogue forced; each in the "
+                          "automatic contraction form unless named; timed on the steps after the warm-up, errors "
+                          "as in accuracy")
     out["ladder"] = ladder
     # side legs: the plain FP64 form under the same rules; both forms with the stall rule off
     side = {}
@@ -553,15 +568,21 @@ def single_line(w, res, args, pk, pk_kind, world, headline=True):
             "contraction_role_cycles_per_tile": res.get("contraction_role_cycles_per_tile"), "roofline": roof,
             "accuracy": res["accuracy"], "precision_ladder": res.get("ladder", {})}
     ph = res["phase_us_per_half_sweep"]
+    cube_steps = sum(1 for s in res["stats"] if s.get("cube_form"))
+    line["contraction_form"] = {"cube_steps": cube_steps, "direct_steps": len(res["stats"]) - cube_steps,
+                                "note": "tensor-core epilogue per timed step: cube = v^3 with cbrt(c)-scaled "
+                                        "columns and the exact linear part, chosen where sum_m prod_d max|a| <= "
+                                        "0.6; direct = c u (u^2 - 1)"}
     if args.precision != "fp64" and ph.get("contract"):
-        cr = contraction_roof_us(w, res["mk_mean"], pk, args.precision)
+        cr = contraction_roof_us(w, res["mk_mean"], pk, args.precision, cube_steps * 2 > len(res["stats"]))
         line["contraction_roofline"] = {
             "phase_us": ph["contract"], "roof_us": cr["roof_us"], "bound": cr["bound"],
             "frac": cr["roof_us"] / ph["contract"], "tensor_us": cr["tensor_us"], "alu_us": cr["alu_us"],
             "grid_points_of_cta": cr["grid_points"],
             "note": "the last CTA's share of one half-sweep's tensor-core contraction (phase entry to its last "
                     "tile), global-timer trace; roof = max(split MMA at one SM's share of the BF16 burst peak, "
-                    "3 FP32 operations per grid point on 128 lanes at the maximum clock)"}
+                    "the epilogue's FP32 operations per grid point (3 direct, 2 cube form) on 128 lanes at the "
+                    "maximum clock)"}
     side = dict(res["side"])
     lead = {}
     f = side.get("fp64_same_rules")

@@ -134,10 +134,29 @@ typedef struct {
                                handles allocate their own device memory: the exception to the
                                no-allocation convention above.  ctd_step synchronises after
                                every step to read the switch decision.                        */
+  int contraction_form;     /* tensor-core precisions only: how a tile's epilogue forms the
+                               weighted sum sum_j c_j w(u_ij) of Eq. KxxMxx (c_j the quadrature
+                               weight times the fixed factors of the other dimensions).
+                               CTD_CONTRACT_DIRECT: from the reconstructed u, c_j u (u^2 - 1),
+                               three FP32 operations per point and c_j read per column.
+                               CTD_CONTRACT_CUBE: the column operand is rebuilt every half-sweep
+                               with its rows scaled by cbrt(c_j), so that the tensor cores yield
+                               v = cbrt(c_j) u and the epilogue sums v^3 = c_j u^3 (two
+                               operations per point, no weights); the linear part sum_j c_j u_ij
+                               = sum_m a_m,i H_m is added exactly from the Gram products H of the
+                               right-hand side.  Exact algebra; its rounding is smaller than the
+                               direct form's where |u| is small and larger near |u| = 1, where
+                               u^3 and u cancel.
+                               CTD_CONTRACT_AUTO (0, the default): the cube form for a step whose
+                               field satisfies the bound sum_m prod_d max_i |a_m,d(i)| <= 0.6
+                               (then |u^3| <= 0.36 |u| everywhere), else the direct form.  The
+                               reduced integration domain and the probes that dump u always use
+                               the direct form.  Ignored by CTD_PREC_FP64.                     */
 } ctd_config;
 
 enum { CTD_NONLINEAR_GRID = 0, CTD_NONLINEAR_SEPARATED = 1 };
 enum { CTD_QUAD_NODAL = 0, CTD_QUAD_GAUSS = 1 };
+enum { CTD_CONTRACT_AUTO = 0, CTD_CONTRACT_DIRECT = 1, CTD_CONTRACT_CUBE = 2 };
 
 typedef struct {
   int modes;                /* M of u^{k+1}                                                  */
@@ -151,6 +170,8 @@ typedef struct {
                                that the enrichment test discarded)                          */
   int actd_switched;        /* 1 if the step was solved on the full grid (actd_Mc > 0); then
                                modes is the count the greedy loop reached (M_c + 1)          */
+  int cube_form;            /* 1 if the step's tensor-core contractions used the cube form
+                               (contraction_form), 0 otherwise                               */
 } ctd_step_stats;
 
 typedef struct ctd_ctx* ctd_handle;
@@ -299,7 +320,8 @@ ctd_status ctd_probe_reconstruct_noalloc(ctd_handle h, int x, float* out);
  * seconds[0 .. nslots) (may be NULL), resets the counters, and turns accumulation on
  * (enable != 0) or off.  Slots: 0 prologue (nonlinear-term preparation), 1 mode start,
  * 2 Gram products + nonlinear contraction, 3 right-hand sides, 4 banded solve,
- * 5 convergence test, 6 mode commit; inside the banded solve: 8 set-up, 9 first pass,
+ * 5 convergence test, 6 mode commit, 7 the cube form's scaled column operand (per
+ * half-sweep, contraction_form); inside the banded solve: 8 set-up, 9 first pass,
  * 10 refinement, 11 refinement passes (a count, in units of 1e-9), 14 double-float
  * residuals, 15 inner FP32 solves; 12 Gram products, 13 contraction (timed on the last CTA,
  * whose tile share is a full one; every other slot on CTA 0); tensor-core contraction roles on

@@ -174,11 +174,13 @@ size_t carve(const ctd_config& c, const Plan& pl, void* base, StepParams* P, Ext
   const int spd = ctd::slots_per_dim(pl.Mcap, pl.sep_q);
   const int nslots = std::max((D - 1) * spd, D * 6);
   p.gram = cv.take<float2>(static_cast<size_t>(nslots) * Gs);
-  p.rpart = cv.take<double>(pl.rpart_len);
+  p.rpart = cv.take<double>(std::max(pl.rpart_len, static_cast<size_t>(nmax)));   // also the probe's linear part
   x.rpart_tc = cv.take<double>(std::max<size_t>(1, pl.rpart_tc_len));
   for (int k = 0; k < 3; ++k) x.kr[k] = nullptr;
-  if (c.precision != CTD_PREC_FP64 && D == 3)
-    for (int k = 0; k < 3; ++k)
+  // column operands per direction: the 3D Khatri-Rao products, and the cube form's scaled
+  // operand (2D and 3D)
+  if (c.precision != CTD_PREC_FP64)
+    for (int k = 0; k < D; ++k)
       x.kr[k] = cv.take<__nv_bfloat16>(static_cast<size_t>(pl.dirs[k].ncols_pad) * ctd::tc_nimg(c.precision) *
                                        pl.Kpad);
   for (int k = 0; k < D; ++k) x.dirs[k] = pl.dirs[k];
@@ -264,6 +266,7 @@ ctd_status validate(const ctd_config* c) {
     return CTD_ERR_ARG;
   if (c->quad_rule != CTD_QUAD_NODAL && c->quad_rule != CTD_QUAD_GAUSS) return CTD_ERR_ARG;
   if (c->actd_Mc < 0) return CTD_ERR_ARG;
+  if (c->contraction_form < CTD_CONTRACT_AUTO || c->contraction_form > CTD_CONTRACT_CUBE) return CTD_ERR_ARG;
   if (c->actd_Mc > 0 && (c->precision != CTD_PREC_FP64 || c->quad_rule != CTD_QUAD_NODAL ||
                          c->nonlinear_form != CTD_NONLINEAR_GRID || c->reduced_tol > 0.0))
     return CTD_ERR_UNSUPPORTED;
@@ -490,6 +493,7 @@ ctd_status ctd_create(const ctd_config* cfg, void* workspace, size_t workspace_b
   P.reduced_tol = cfg->reduced_tol;
   P.nl_form = cfg->nonlinear_form;
   P.sep_q = h->plan.sep_q;
+  P.contraction_form = cfg->contraction_form;
   P.I_max = cfg->I_max;
   P.M_max = cfg->M_max;
   P.fixed_als = cfg->fixed_als_iters;
@@ -780,6 +784,7 @@ ctd_status ctd_step(ctd_handle h, int nsteps, ctd_step_stats* stats) {
         o.als_stalled = rec[k].als_stalled;
         o.als_sweeps_committed = rec[k].als_sweeps_committed;
         o.actd_switched = rec[k].actd_switched;
+        o.cube_form = rec[k].cube_form;
         o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
         if (o.status < 0) worst = static_cast<ctd_status>(o.status);
         else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -869,6 +874,7 @@ ctd_status ctd_step_batch(const ctd_handle* handles, int count, int nsteps, void
           o.als_stalled = rec[k].als_stalled;
           o.als_sweeps_committed = rec[k].als_sweeps_committed;
           o.actd_switched = rec[k].actd_switched;
+          o.cube_form = rec[k].cube_form;
           o.status = es != CTD_OK ? es : (o.capped ? CTD_STATUS_CAPPED : (o.not_converged ? CTD_STATUS_ALS_NOT_CONVERGED : CTD_OK));
           if (o.status < 0) worst = static_cast<ctd_status>(o.status);
           else if (worst >= 0 && o.status > worst) worst = static_cast<ctd_status>(o.status);
@@ -1074,6 +1080,20 @@ ctd_status ctd_probe_contract(ctd_handle h, int x, const double* const* v, doubl
       }
   } else {
     for (int i = 0; i < n; ++i) out[i] = rq[i];
+  }
+  if (h->cfg.precision != CTD_PREC_FP64) {
+    // tensor-core partials: without the factor 4 a0, and in the cube form without the linear
+    // part, which the probe kernel left in P.rpart
+    int cube = 0;
+    CTD_CUDA(h, cudaMemcpyAsync(&cube, h->X.ctrl + 2, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (cube) {
+      std::vector<double> lin(n);
+      CTD_CUDA(h, cudaMemcpyAsync(lin.data(), h->P.rpart, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+      CTD_CUDA(h, cudaStreamSynchronize(h->stream));
+      for (int i = 0; i < n; ++i) out[i] -= lin[i];
+    }
+    for (int i = 0; i < n; ++i) out[i] *= 4.0 * h->cfg.a0;
   }
   InstState st;
   ctd_status rs = read_state(h, &st);

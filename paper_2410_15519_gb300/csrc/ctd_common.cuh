@@ -70,6 +70,7 @@ struct StepStatsDev {
   int als_stalled;
   int als_sweeps_committed;
   int actd_switched;
+  int cube_form;
 };
 
 struct StepParams {
@@ -111,6 +112,7 @@ struct StepParams {
   int nl_form;             // 0: nonlinear term as the full nodal integral (Eq. KxxMxx); 1: the
                            // separated form (Eq. MxySep) for steps with M_k <= kMaxSepModes
   int sep_q;               // Gram slots per dimension reserved for the separated form (0 if off)
+  int contraction_form;    // tensor-core epilogue: 0 automatic, 1 direct, 2 cube (see ctd_contract_tc.cuh)
   int vgrid, vrank;        // CTAs working on this instance and this CTA's rank among them: the
                            // launch grid for a single instance, 1 and 0 in a batched launch
                            // (set by each CTA in its shared-memory copy)
@@ -118,6 +120,7 @@ struct StepParams {
 
 // phases accumulated in StepParams::trace (each includes its closing grid barrier)
 enum TracePhase { kTrPrologue = 0, kTrInit, kTrGramContract, kTrRhs, kTrSolve, kTrConverge, kTrCommit,
+                  kTrScale,   // the cube form's scaled column operand (per half-sweep)
                   kTrSolveFactor = 8, kTrSolveFirst, kTrSolveRefine, kTrSolvePasses, kTrGram, kTrContract,
                   kTrSolveResidual, kTrSolveInner,
                   // tensor-core contraction roles on the traced CTA, SM clock cycles: producer waiting

@@ -147,7 +147,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  // The load writes r[] asynchronously, when the wait completes: r[] pass through the wait
+  // as read-write operands, so that the compiler neither reads them before it nor reuses
+  // their registers in between (a late write would clobber whatever it put there).
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -235,7 +245,7 @@ struct TcDir {
 // written.  One unit = 8 consecutive K columns of one row (one 16-byte core-matrix row of the
 // hi and of the lo image); units in image order, grid-stride over all CTAs.
 static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir* dirs, __nv_bfloat16* const* kr, int pb,
-                                  int Mk) {
+                                  int Mk, bool build_kr = true) {
   const int KS = P.Kpad / 16, ksteps = (Mk + 15) / 16, nimg = tc_nimg(P.precision);
   const long long stride = static_cast<long long>(P.vgrid) * blockDim.x;
   const long long t0 = static_cast<long long>(P.vrank) * blockDim.x + threadIdx.x;
@@ -289,7 +299,7 @@ static __device__ __noinline__ void tc_prepare(const StepParams& P, const TcDir*
       store(dd.op, i, k0, a);
     }
   }
-  if (P.dim != 3) return;
+  if (P.dim != 3 || !build_kr) return;
   for (int x = 0; x < 3; ++x) {
     const TcDir& td = dirs[x];
     const Dim& dm = P.d[td.mid];
@@ -336,7 +346,7 @@ __device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, in
             const float2 ph = dd.phi[static_cast<size_t>(r) * kPhiW + k], vv = dd.v[j0 + k];
             acc = __fmaf_rn(ph.x + ph.y, vv.x + vv.y, acc);
           }
-        v = s * static_cast<float>(dd.wq[r]) * acc;
+        v = static_cast<float>(dd.wq[r]) * acc;
       }
       w[r] = v;
     }
@@ -353,7 +363,130 @@ __device__ inline void tc_weights(const StepParams& P, const KCompressed& kc, in
 #pragma unroll
     for (int g = 0; g < kGroup; ++g) {
       const int i = i0 + g * nthr;
-      if (i < hi) w[i] = i < dd.n ? s * kc_omega(kc, i).x * (x[g].x + x[g].y) : 0.f;
+      if (i < hi) w[i] = i < dd.n ? kc_omega(kc, i).x * (x[g].x + x[g].y) : 0.f;
+    }
+  }
+}
+
+// Cube form of the contraction (ctd_config.contraction_form).  With c_j the column weight of
+// column j (the product of the other dimensions' tc_weights), the column operand's row j is
+// scaled by cbrt(c_j) (the real cube root, sign kept), so that the tensor cores yield
+// v_ij = cbrt(c_j) u_ij and the epilogue sums v^3 = c_j u_ij^3 with no weights.  The linear
+// part sum_j c_j u_ij = sum_m a_m,i H_m (H_m the product of the Gram sums h_d,m = c_d . a_m,d)
+// is subtracted exactly in the right-hand side.  The bound below selects the form per step
+// in automatic mode: at |u| <= 0.6, |u^3| <= 0.36 |u|, so the cube sum cancels little against
+// the linear part, and the split's rounding enters through 3 u^2 instead of |3 u^2 - 1|.
+constexpr float kCubeMaxAmp = 0.6f;
+
+// sum_m prod_d max_i |a_m,d(i)| over u^k's factors (at the nodes, or at the Gauss points),
+// a bound of max |u^k| over the grid.  Every CTA computes it alike (exact maxima, then one
+// thread's fixed-order sum), so all CTAs take the same decision.  s: dim * Mk floats of shared
+// memory.
+static __device__ __noinline__ float tc_amp_bound(const StepParams& P, int pb, int Mk, float* s) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = warp; t < P.dim * Mk; t += nw) {
+    const int d = t / Mk, m = t - d * Mk;
+    const Dim& dd = P.d[d];
+    const float2* src = (P.quad ? dd.Aq : dd.bank[pb]) + static_cast<size_t>(m) * dd.nq;
+    float mx = 0.f;
+    for (int i = lane; i < dd.nq; i += 32) {
+      const float2 v = src[i];
+      mx = fmaxf(mx, fabsf(v.x + v.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s[t] = mx;
+  }
+  __syncthreads();
+  float B = 0.f;
+  for (int m = 0; m < Mk; ++m) {
+    float p = 1.f;
+    for (int d = 0; d < P.dim; ++d) p *= s[d * Mk + m];
+    B += p;
+  }
+  __syncthreads();
+  return B;
+}
+
+// The cube form's column operand of direction x, written to `out` in the tile-image layout of
+// tc_prepare: row j of the other dimension (2D), or row (j, l) = j n_last_pad + l of the middle
+// and last dimensions (3D), times cbrt of its column weight.  The scale vectors are staged in
+// shared memory s (ncols_pad floats in 2D; n_last_pad + nq_mid in 3D); the (row block, K step)
+// pieces are spread over all warps of all CTAs.
+static __device__ __noinline__ void tc_prepare_scaled(const StepParams& P, const KCompressed* kc, const TcDir& td,
+                                                      __nv_bfloat16* out, int pb, int Mk, float* s) {
+  const int KS = P.Kpad / 16, ksteps = (Mk + 15) / 16, nimg = tc_nimg(P.precision);
+  if (ksteps == 0) return;
+  const bool three = td.mid >= 0;
+  const int nl = three ? td.n_last_pad : td.ncols_pad;
+  const int nm = three ? P.d[td.mid].nq : 0;
+  float* sl = s;
+  float* sm = s + nl;
+  tc_weights(P, kc[td.last], td.last, sl, nl, 0, nl, threadIdx.x, blockDim.x);
+  if (three) tc_weights(P, kc[td.mid], td.mid, sm, nm, 0, nm, threadIdx.x, blockDim.x);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nl + nm; i += blockDim.x) s[i] = cbrtf(s[i]);
+  __syncthreads();
+  auto src_of = [&](const Dim& dd) { return P.quad ? dd.Aq : dd.bank[pb]; };
+  const Dim& dl = P.d[td.last];
+  const float2* fl = src_of(dl);
+  const float2* fm = three ? src_of(P.d[td.mid]) : nullptr;
+  // one warp per (128-row block, K step); in 3D a block lies at one middle index j (n_last_pad
+  // is a multiple of 128).  Lane: row rr = lane & 7 of each 8-row group, K half cm, and every
+  // other group starting at gg; its eight K columns' middle factor is loaded once per block.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int rr = lane & 7, cm = (lane >> 3) & 1, gg = lane >> 4;
+  const int nblk = td.ncols_pad / kTcM, work = nblk * ksteps;
+  for (int wi = P.vrank * nw + warp; wi < work; wi += P.vgrid * nw) {
+    const int blk = wi / ksteps, ks = wi - blk * ksteps;
+    const int row0 = blk * kTcM;
+    int j = 0, l0 = row0;
+    if (three) {
+      j = row0 / td.n_last_pad;
+      l0 = row0 - j * td.n_last_pad;
+    }
+    const int k0 = ks * 16 + cm * 8;
+    float fk[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      fk[e] = 0.f;
+      if (k < Mk) {
+        fk[e] = 1.f;
+        if (three) {
+          const float2 vm = fm[static_cast<size_t>(k) * nm + j];
+          fk[e] = sm[j] * (vm.x + vm.y);
+        }
+      }
+    }
+    // every load of the block first (64 per lane in flight), then the products and stores: the
+    // stores could alias the loads for the compiler, which would otherwise keep them in order
+    float2 vl[8][8];
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int l = l0 + (gg + 2 * it) * 8 + rr;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        vl[it][e] = (l < dl.nq && k0 + e < Mk) ? fl[static_cast<size_t>(k0 + e) * dl.nq + l] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int g = gg + 2 * it, l = l0 + g * 8 + rr;
+      const float sc = l < dl.nq ? sl[l] : 0.f;
+      float a[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a[e] = sc * fk[e] * (vl[it][e].x + vl[it][e].y);
+      // the BF16 terms of the split, as in tc_prepare
+      const size_t o = tc_img_index(row0 + g * 8 + rr, k0, 0, KS, nimg);
+      for (int h = 0; h < nimg; ++h) {
+        __align__(16) __nv_bfloat16 t[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          t[e] = __float2bfloat16_rn(a[e]);
+          a[e] -= __bfloat162float(t[e]);
+        }
+        *reinterpret_cast<uint4*>(out + o + static_cast<size_t>(h) * kTcImgElems) = *reinterpret_cast<const uint4*>(t);
+      }
     }
   }
 }
@@ -385,7 +518,8 @@ __host__ __device__ inline TcLayout tc_layout(int chunks, int stages, int wlast_
 static __device__ __noinline__ bool tc_contract(const StepParams& P, const KCompressed* kc, const TcDir& td,
                                    const __nv_bfloat16* Pop, const __nv_bfloat16* Qop, int x, int Mk, int stages,
                                    unsigned char* base, uint32_t tmem_base, double* rpart_tc, float* dump,
-                                   const unsigned* tile_max = nullptr, float on_scale = 0.f, float on_tol = 0.f) {
+                                   const unsigned* tile_max = nullptr, float on_scale = 0.f, float on_tol = 0.f,
+                                   bool cube = false) {
   const int G = P.vgrid, cta = P.vrank;
   // Parameters the role loops use, in registers: P and td live in shared memory, and every
   // asm statement below (waits, MMAs, commits) is a memory clobber that would reload them.
@@ -590,7 +724,8 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
     const int r = (warp - 4) * 32 + lane;
     // column weights of the fixed factors (in 2D only those of this CTA's column blocks),
     // formed by the epilogue's 128 threads while the first copies and MMAs are in flight
-    if (tmid >= 0) {
+    if (cube) {
+    } else if (tmid >= 0) {
       tc_weights(P, kc[td.last], td.last, wl, wl_n, 0, wl_n, r, 128);
       tc_weights(P, kc[tmid], tmid, wm, wm_n, 0, wm_n, r, 128);
     } else if (t1 - t0 >= ntc) {
@@ -636,7 +771,28 @@ static __device__ __noinline__ bool tc_contract(const StepParams& P, const KComp
       const long long c1 = tr ? clock64() : 0;
       ++gi;
       tc_fence_after();
-      for (int j = 0; j < g; ++j) {
+      for (int j = 0; j < g && cube; ++j) {
+        // cube form: v^3 = c_j u^3, two columns per FP32x2 instruction, four interleaved sums
+        float2 a01 = make_float2(0.f, 0.f), a23 = a01, b01 = a01, b23 = a01;
+        const uint32_t acol = static_cast<uint32_t>((2 * ps + j) * kTcN);
+#pragma unroll
+        for (int q = 0; q < kTcN / 32; ++q) {
+          float v[32];
+          tmem_ld32(lane_base + acol + static_cast<uint32_t>(q * 32), v);
+#pragma unroll
+          for (int c = 0; c < 32; c += 8) {
+            const float2 u01 = make_float2(v[c], v[c + 1]), u23 = make_float2(v[c + 2], v[c + 3]);
+            const float2 u45 = make_float2(v[c + 4], v[c + 5]), u67 = make_float2(v[c + 6], v[c + 7]);
+            a01 = __ffma2_rn(__fmul2_rn(u01, u01), u01, a01);
+            a23 = __ffma2_rn(__fmul2_rn(u23, u23), u23, a23);
+            b01 = __ffma2_rn(__fmul2_rn(u45, u45), u45, b01);
+            b23 = __ffma2_rn(__fmul2_rn(u67, u67), u67, b23);
+          }
+        }
+        const float at = ((a01.x + a01.y) + (a23.x + a23.y)) + ((b01.x + b01.y) + (b23.x + b23.y));
+        acc = df_add(acc, dfloat{at, 0.f});
+      }
+      for (int j = 0; j < g && !cube; ++j) {
         const int col0 = (cb + j) * kTcN;
         const float* wt;
         float wscale = 1.f;

@@ -285,6 +285,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
 
   // ---- prologue: the nonlinear term's data for this step (none for the separated form,
   // whose 1D sums are Gram slots)
+  bool cube = false;
   if constexpr (kSepTU) {
   } else if (P.precision == 0) {
     convert_prev_modes(P, X, pb, Mk);
@@ -298,7 +299,13 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
       gauss_prologue(P, X, pb, Mk);
       if (!sync_all(P, epoch, 1)) return;
     }
-    tc_prepare(P, X.dirs, X.kr, pb, Mk);
+    // the cube form of the contraction (see tc_amp_bound): the reduced domain drops tiles of
+    // w(u), which the cube form does not hold apart from the linear part, so it keeps the
+    // direct form
+    if (Mk > 0 && P.reduced_tol <= 0.0 && P.contraction_form != 1)
+      cube = P.contraction_form == 2 ||
+             tc_amp_bound(P, pb, Mk, reinterpret_cast<float*>(arena_base(smem_raw))) <= kCubeMaxAmp;
+    tc_prepare(P, X.dirs, X.kr, pb, Mk, !cube);
     fence_proxy_async_global();
     // contraction partial slots start the step at zero (see rhs_rows)
     size_t nslot = 0;
@@ -340,6 +347,13 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     for (it = 1; it <= n_it; ++it) {
       save_old(P);
       for (int x = 0; x < D; ++x) {
+        if (cube) {
+          // cube form: the column operand scaled by the cube roots of the current weights
+          tc_prepare_scaled(P, X.kc, X.dirs[x], X.kr[x], pb, Mk, reinterpret_cast<float*>(arena_base(smem_raw)));
+          fence_proxy_async_global();
+          if (!sync_all(P, epoch, 14)) return;
+          trace_mark(P, tmark, kTrScale);
+        }
         // Phase A: Gram partials of the fixed factors + nonlinear contraction partials
         unsigned long long tsub = (P.trace && P.vrank == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
         gram_partials(P, X, x, Mk, M, pb, cb, ar.gram_rows);
@@ -363,10 +377,10 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
           contract_fp64(P, x, g);
         } else {
           const TcDir& td = X.dirs[x];
-          const __nv_bfloat16* qop = (D == 2) ? P.d[td.last].op : X.kr[x];
+          const __nv_bfloat16* qop = (D == 2 && !cube) ? P.d[td.last].op : X.kr[x];
           if (!tc_contract(P, X.kc, td, P.d[x].op, qop, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base,
                            X.rpart_tc, nullptr, P.reduced_tol > 0.0 ? P.tile_max : nullptr,
-                           static_cast<float>(4.0 * P.a0), static_cast<float>(P.reduced_tol)))
+                           static_cast<float>(4.0 * P.a0), static_cast<float>(P.reduced_tol), cube))
             return;
         }
         if (tr_last) atomicAdd(P.trace + kTrContract, global_ns() - tcon);
@@ -374,7 +388,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
         trace_mark(P, tmark, kTrGramContract);
         // Phase B: coefficients (every CTA, same order) and right-hand-side rows
         build_coefficients(P, x, Mk, M, &sm.coef, ar.gram_rows);
-        rhs_rows(P, X, x, Mk, M, pb, cb, &sm.coef);
+        rhs_rows(P, X, x, Mk, M, pb, cb, &sm.coef, cube);
         if (!sync_all(P, epoch, 4)) return;
         trace_mark(P, tmark, kTrRhs);
         // Phase C: banded solve on CTA 0
@@ -509,6 +523,7 @@ CTD_LOCAL __device__ void step_body(const StepParams& P, const Extra& X, unsigne
     r.status = 0;
     r.als_stalled = n_stalled;
     r.als_sweeps_committed = sweeps - sweeps_discarded;
+    r.cube_form = cube ? 1 : 0;
     *P.stats = r;
   }
 }
@@ -728,13 +743,54 @@ __device__ void probe_contract_body(const StepParams& P, const Extra& X, int x, 
       gauss_prologue(P, X, st0.bank, st0.Mk);
       if (!sync_all(P, epoch, 13)) return;
     }
-    tc_prepare(P, X.dirs, X.kr, st0.bank, st0.Mk);
+    // the step's choice of contraction form (the dump is of u: direct form)
+    const int Mk = st0.Mk, pb = st0.bank;
+    float* fs = reinterpret_cast<float*>(arena_base(smem_raw));
+    bool cube = false;
+    if (!dump && Mk > 0 && P.reduced_tol <= 0.0 && P.contraction_form != 1)
+      cube = P.contraction_form == 2 || tc_amp_bound(P, pb, Mk, fs) <= kCubeMaxAmp;
+    tc_prepare(P, X.dirs, X.kr, pb, Mk, !cube);
+    const TcDir& td = X.dirs[x];
+    if (cube) tc_prepare_scaled(P, X.kc, td, X.kr[x], pb, Mk, fs);
     fence_proxy_async_global();
     if (!sync_all(P, epoch, 11)) return;
-    const TcDir& td = X.dirs[x];
-    const __nv_bfloat16* qop = (P.dim == 2) ? P.d[td.last].op : X.kr[x];
-    tc_contract(P, X.kc, td, P.d[x].op, qop, x, st0.Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart_tc,
-                dump);
+    const __nv_bfloat16* qop = (P.dim == 2 && !cube) ? P.d[td.last].op : X.kr[x];
+    tc_contract(P, X.kc, td, P.d[x].op, qop, x, Mk, X.tc_stages, arena_base(smem_raw), tmem_base, X.rpart_tc,
+                dump, nullptr, 0.f, 0.f, cube);
+    if (P.vrank == 0 && threadIdx.x == 0) X.ctrl[2] = cube ? 1 : 0;
+    if (!cube) return;
+    // the cube form's linear part for the host, lin_i = sum_m A_m,i H_m into P.rpart (A the
+    // factors, or M a under the Gauss rule; H_m the product over the other dimensions of
+    // h_d,m = sum_j omega_j v_j a_m(j), or v . M a_m): FP64, every CTA forms H alike
+    double* sH = reinterpret_cast<double*>(arena_base(smem_raw));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nO = P.dim - 1;
+    __syncthreads();
+    for (int t = warp; t < nO * Mk; t += kWarps) {
+      const int o = t / Mk, m = t - o * Mk, d = o < x ? o : o + 1;
+      const Dim& dd = P.d[d];
+      const float2* a = (P.quad ? dd.MA : dd.bank[pb]) + static_cast<size_t>(m) * dd.n;
+      double acc = 0.0;
+      for (int j = lane; j < dd.n; j += 32) {
+        const float2 vv = dd.v[j], aa = a[j];
+        const double w = P.quad ? 1.0 : dd.omega[j];
+        acc = fma(w * (static_cast<double>(vv.x) + vv.y), static_cast<double>(aa.x) + aa.y, acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) sH[t] = acc;
+    }
+    __syncthreads();
+    const Dim& dx = P.d[x];
+    const float2* A = P.quad ? dx.MA : dx.bank[pb];
+    for (int i = P.vrank * blockDim.x + threadIdx.x; i < dx.n; i += P.vgrid * blockDim.x) {
+      double lin = 0.0;
+      for (int m = 0; m < Mk; ++m) {
+        double H = 1.0;
+        for (int o = 0; o < nO; ++o) H *= sH[o * Mk + m];
+        const float2 am = A[static_cast<size_t>(m) * dx.n + i];
+        lin = fma(static_cast<double>(am.x) + am.y, H, lin);
+      }
+      P.rpart[i] = lin;
+    }
   }
 }
 

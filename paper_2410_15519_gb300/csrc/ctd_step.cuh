@@ -51,7 +51,7 @@ struct Extra {            // per-launch workspace pieces not in StepParams
   int* ctrl;              // [4] solver flags broadcast
   double* rpart_tc;        // [nq][cmax] partial row sums of the tensor-core contraction (one per CTA)
   TcDir dirs[kMaxDim];    // tensor-core geometry per direction
-  __nv_bfloat16* kr[kMaxDim];   // 3D Khatri-Rao operands per direction
+  __nv_bfloat16* kr[kMaxDim];   // column operands per direction: 3D Khatri-Rao, cube form scaled
   int tc_stages;          // B-operand ring depth
   float2* xprev;          // [kMaxDim][kMaxN] last unnormalised solve per direction (warm start)
 };
@@ -364,9 +364,12 @@ __device__ inline double gauss_row_integral(const StepParams& P, const Extra& X,
 
 // Right-hand side rows of this CTA's slice of direction x (Eq. KxQx), written as
 // double-float into P.Q.  R_i (the nonlinear contraction, without L omega_i) comes from the
-// partial buffers.
+// partial buffers; the tensor-core partials lack the factor 4 a0 of w, and with cube (the cube
+// form of the contraction) also the linear part -sum_j c_j u_ij = -sum_m a_m,i H_m (nodal
+// rule; under the Gauss rule its Phi^T integral, sum_m (M a_m)_i H_m), which is added here
+// from the same sums s1 starts with.
 static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X, int x, int Mk, int M, int pb,
-                         int cb, const Coef* c) {
+                         int cb, const Coef* c, bool cube = false) {
   const Dim& dd = P.d[x];
   int lo, hi;
   slice_of(dd.n, P.vgrid, P.vrank, lo, hi);
@@ -396,7 +399,7 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
   for (int i0 = lo; i0 < hi; i0 += groups) {
     const int i = i0 + g;
     const bool live = i < hi;
-    dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f}, s4 = {0.f, 0.f};
+    dfloat s1 = {0.f, 0.f}, s2 = {0.f, 0.f}, s3 = {0.f, 0.f}, s4 = {0.f, 0.f}, s5 = {0.f, 0.f};
     if (live) {
       // Gauss rule: M a and M b of the factors (consistent mass), nodal rule: a and b (the
       // diagonal mass joins below)
@@ -407,6 +410,7 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         s1 = df_fma(s1, ami, h);
         if (sep) s4 = df_add(s4, df_neg(df_mul(ami, h)));   // -u part of w (Eq. MxySep)
       }
+      if (cube) s5 = s1;   // the cube form's linear part: sum_m a_m,i H_m
       // u^3 part of w: sum over multisets of a_m1 a_m2 a_m3 (row i of u^k's factors) T_q
       for (int q = lane; q < nsep; q += tpr) {
         const unsigned e = kSepTable.e[q];
@@ -427,12 +431,17 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
     s2 = group_sum(s2, tpr);
     s3 = group_sum(s3, tpr);
     if (sep) s4 = group_sum(s4, tpr);
+    if (cube) s5 = group_sum(s5, tpr);
     if (live && lane == 0) {
       dfloat R;
       if (sep) {
         R = df_mul(df_of(4.0 * P.a0), s4);
       } else if (P.quad) {
         R = df_of(gauss_row_integral(P, X, x, i));
+        if (P.precision != 0) {
+          if (cube) R = df_add(R, df_neg(s5));
+          R = df_mul(df_of(4.0 * P.a0), R);
+        }
       } else if (P.precision == 0) {
         const double* rp = P.rpart + static_cast<size_t>(i) * C;
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
@@ -463,6 +472,8 @@ static __device__ __noinline__ void rhs_rows(const StepParams& P, const Extra& X
         for (int k = 0; k < 8; ++k) r += part[k];
         for (int k = 8; k < Cr; ++k) r += rp[k];
         R = df_of(r);
+        if (cube) R = df_add(R, df_neg(s5));
+        R = df_mul(df_of(4.0 * P.a0), R);
         for (int k = 0; k < Cr; ++k) rp[k] = 0.0;
       }
       dfloat q;

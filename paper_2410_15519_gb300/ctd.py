@@ -23,6 +23,9 @@ NONLINEAR_GRID = 0         # nonlinear term as the full nodal integral (Eq. KxxM
 NONLINEAR_SEPARATED = 1    # separated form (Eq. MxySep) for steps with M_k <= 16
 QUAD_NODAL = 0             # mass-type integrals with the nodal rule (M = diag(omega))
 QUAD_GAUSS = 1             # Gauss points per element, consistent mass
+CONTRACT_AUTO = 0          # tensor-core epilogue: cube form when the field bound allows it
+CONTRACT_DIRECT = 1        # tensor-core epilogue: c u (u^2 - 1) from the reconstructed u
+CONTRACT_CUBE = 2          # tensor-core epilogue: v^3 with cbrt(c)-scaled columns, exact linear part
 
 STATUS = {0: "CTD_OK", 1: "CTD_STATUS_CAPPED", 2: "CTD_STATUS_ALS_NOT_CONVERGED", -1: "CTD_ERR_ARG",
           -2: "CTD_ERR_WORKSPACE", -3: "CTD_ERR_CUDA", -4: "CTD_ERR_NONFINITE", -5: "CTD_ERR_TIMEOUT",
@@ -40,14 +43,14 @@ class Config(ctypes.Structure):
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int),
                 ("reduced_tol", ctypes.c_double), ("nonlinear_form", ctypes.c_int),
                 ("als_stall_tol", ctypes.c_double), ("quad_rule", ctypes.c_int), ("quad_q", ctypes.c_int),
-                ("actd_Mc", ctypes.c_int)]
+                ("actd_Mc", ctypes.c_int), ("contraction_form", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
     _fields_ = [("modes", ctypes.c_int), ("als_sweeps", ctypes.c_int), ("als_sweeps_max", ctypes.c_int),
                 ("capped", ctypes.c_int), ("not_converged", ctypes.c_int), ("status", ctypes.c_int),
                 ("als_stalled", ctypes.c_int), ("als_sweeps_committed", ctypes.c_int),
-                ("actd_switched", ctypes.c_int)]
+                ("actd_switched", ctypes.c_int), ("cube_form", ctypes.c_int)]
 
 
 class CTDError(RuntimeError):
@@ -103,7 +106,7 @@ def load() -> ctypes.CDLL:
 def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, tol_als, tol_enrich,
                 precision=PREC_FP64, fixed_als_iters=0, fixed_modes=0, seed=0, wait_limit_s=0.0,
                 grid_ctas=0, reduced_tol=0.0, nonlinear_form=0, als_stall_tol=0.0, quad_rule=0,
-                quad_q=0, actd_Mc=0) -> Config:
+                quad_q=0, actd_Mc=0, contraction_form=CONTRACT_AUTO) -> Config:
     c = Config()
     c.dim = dim
     for k in range(3):
@@ -120,6 +123,7 @@ def make_config(dim, n, length, s, p, a, L, kappa, a0, alpha, dt, M_max, I_max, 
     c.als_stall_tol = float(als_stall_tol)
     c.quad_rule, c.quad_q = int(quad_rule), int(quad_q)
     c.actd_Mc = int(actd_Mc)
+    c.contraction_form = int(contraction_form)
     return c
 
 
@@ -222,7 +226,7 @@ def step_batch(solvers: Sequence["Solver"], nsteps: int = 1, stats: bool = True,
                          capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
                          als_stalled=r.als_stalled,
                          als_sweeps_committed=r.als_sweeps_committed,
-                         actd_switched=bool(r.actd_switched))
+                         actd_switched=bool(r.actd_switched), cube_form=bool(r.cube_form))
                     for r in rec[i * nsteps:(i + 1) * nsteps]])
     return out
 
@@ -287,7 +291,7 @@ class Solver:
                      capped=bool(r.capped), not_converged=bool(r.not_converged), status=r.status,
                          als_stalled=r.als_stalled,
                          als_sweeps_committed=r.als_sweeps_committed,
-                         actd_switched=bool(r.actd_switched)) for r in rec]
+                         actd_switched=bool(r.actd_switched), cube_form=bool(r.cube_form)) for r in rec]
 
     def energy(self) -> float:
         e = ctypes.c_double(0.0)
@@ -353,7 +357,7 @@ class Solver:
                "probe_reconstruct_noalloc")
         return out
 
-    TRACE_PHASES = ("prologue", "mode_start", "gram_contract", "rhs", "solve", "converge", "commit")
+    TRACE_PHASES = ("prologue", "mode_start", "gram_contract", "rhs", "solve", "converge", "commit", "scale_operand")
 
     def trace(self, enable: bool = True) -> dict:
         """Seconds per step-kernel phase accumulated since the last call; (re)starts or stops

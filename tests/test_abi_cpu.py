@@ -160,7 +160,10 @@ def test_calls_without_a_handle_fail_cleanly(ctd):
     (dict(quad_rule=1, quad_q=2, n=(4096, 4096)), 0), (dict(quad_rule=1, quad_q=5), 0),
     (dict(als_stall_tol=-1.0), -1), (dict(als_stall_tol=1e-6), 0),
     (dict(actd_Mc=-1), -1), (dict(actd_Mc=3), 0), (dict(actd_Mc=3, precision=1), -7),
-    (dict(actd_Mc=3, quad_rule=1, quad_q=5), -7)])
+    (dict(actd_Mc=3, quad_rule=1, quad_q=5), -7),
+    (dict(contraction_form=-1), -1), (dict(contraction_form=3), -1),   # unknown form: CTD_ERR_ARG
+    (dict(contraction_form=2, precision=1), 0), (dict(contraction_form=1, precision=3), 0),
+    (dict(contraction_form=2), 0)])                                    # ignored by the FP64 path
 def test_gauss_and_stall_configurations(ctd, over, status):
     w = workloads.preset("c0", **({"n": over.pop("n")} if "n" in over else {}))
     cfg = ctd.config_from_workload(w, **over)

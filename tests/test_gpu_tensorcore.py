@@ -125,8 +125,9 @@ def prec_of(lib, name):
 
 
 @pytest.mark.parametrize("name,rbound,cbound", LADDER)
-@pytest.mark.parametrize("n,rank", [((200, 77), 5), ((130, 90), 33)])
+@pytest.mark.parametrize("n,rank", [((200, 77), 5), ((130, 90), 33), ((300, 140), 128)])
 def test_precision_ladder_reconstruction(lib, name, rbound, cbound, n, rank):
+    # rank 128 fills the padded K range (the smallest ring of column stages)
     w = workloads.preset("c0", n=n, M_max=max(rank, 8))
     s = lib.Solver(lib.config_from_workload(w, precision=prec_of(lib, name)))
     A = workloads.cosine_modes(n, (1.0, 1.0), rank, 4, 7, amp=0.9)
